@@ -1,0 +1,271 @@
+"""CPU oracle for the SpMV optimization-selection method (arXiv 1511.02494).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module; the library under
+``paper_1511_02494_gb300`` never does.  It shares no code with the CUDA path.
+
+The arithmetic lives in ``oracle.c`` (plain sequential C, FP64, compiled with
+``-ffp-contract=off``); this module only builds it with gcc, loads it with
+ctypes and marshals numpy arrays.  Each wrapper names the passage of the paper
+it follows.
+
+Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
+every function below is pinned except the profile-rule *thresholds*, which the
+paper never prints ("empirically set", Section 3.2.1): the rule's logic is
+pinned, its default thresholds are parity unpinned.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (host architecture)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Features(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "line_bytes", "l2_bytes",
+                                         "working_set_bytes", "nnz_min", "nnz_max")] + \
+        [(n, C.c_uint64) for n in ("nnz_sum", "nnz_sumsq_lo", "nnz_sumsq_hi")] + \
+        [(n, C.c_int64) for n in ("bw_min", "bw_max")] + \
+        [(n, C.c_uint64) for n in ("bw_sum", "bw_sumsq_lo", "bw_sumsq_hi", "disp_sum",
+                                   "disp_sumsq_lo", "disp_sumsq_hi", "clust_sum",
+                                   "ngroups_sum", "misses_sum")] + \
+        [(n, C.c_double) for n in ("size", "density", "nnz_avg", "nnz_sd", "bw_avg", "bw_sd",
+                                   "disp_avg", "disp_sd", "clustering", "miss_ratio")] + \
+        [("vec", C.c_float * 16)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "vec"}
+        for s in ("nnz_sumsq", "bw_sumsq", "disp_sumsq"):
+            d[s] = (d.pop(s + "_hi") << 64) | d.pop(s + "_lo")
+        d["vec"] = np.array(list(self.vec), dtype=np.float32)
+        return d
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            P = C.c_void_p
+            i64, i32 = C.c_int64, C.c_int32
+            sig = {
+                "orc_spmv": (None, [i64, P, P, P, P, P]),
+                "orc_spmv_ref": (None, [i64, P, P, P, P, i64, P, P, P]),
+                "orc_spmv_lowp": (None, [i64, P, P, i32, P, P, P]),
+                "orc_round_bf16": (C.c_uint16, [C.c_double]),
+                "orc_round_bf16_array": (None, [i64, P, P]),
+                "orc_round_f32_array": (None, [i64, P, P]),
+                "orc_features": (None, [i64, i64, P, P, i64, i64, C.POINTER(Features)]),
+                "orc_profile_class": (i32, [C.c_double] * 6),
+                "orc_class_variant": (i32, [i32]),
+                "orc_static_partition": (None, [i64, P, i64, P]),
+                "orc_row_blocks": (None, [i64, P, i64, i64, P]),
+                "orc_merge_path": (None, [i64, P, i64, i64, P, P]),
+                "orc_compress_u16": (i64, [i64, P, P, P, P]),
+                "orc_mlp_forward_f32": (None, [i32, i32, i32] + [P] * 10),
+                "orc_argmax": (i32, [i32, P, P]),
+                "orc_mlp_loss_grad_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
+                "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _np(a, dtype):
+    """Contiguous numpy view/copy of a torch tensor or array."""
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _csr(A):
+    return (_np(A.rowptr, np.int32), _np(A.colind, np.int32), _np(A.val, np.float64))
+
+
+def spmv(A, x) -> np.ndarray:
+    """Algorithm 1 (Section 2), sequential FP64: y = A x."""
+    rp, ci, v = _csr(A)
+    x = _np(x, np.float64)
+    y = np.empty(A.n_rows, np.float64)
+    _load().orc_spmv(A.n_rows, _p(rp), _p(ci), _p(v), _p(x), _p(y))
+    return y
+
+
+def spmv_ref(A, x, rows=None):
+    """Compensated y and the per-row scale sum_j |a_ij x_j| (Algorithm 1),
+    for all rows or the listed ones."""
+    rp, ci, v = _csr(A)
+    x = _np(x, np.float64)
+    if rows is None:
+        n, r = A.n_rows, None
+    else:
+        r = _np(rows, np.int64)
+        n = r.size
+    y = np.empty(n, np.float64)
+    s = np.empty(n, np.float64)
+    _load().orc_spmv_ref(A.n_rows, _p(rp), _p(ci), _p(v), _p(x), n,
+                         _p(r) if r is not None else None, _p(y), _p(s))
+    return y, s
+
+
+def spmv_lowp(A, x, vkind: int, lowval) -> np.ndarray:
+    """y = A x with float32 (vkind=1) or bfloat16-bit (vkind=2) stored values,
+    FP64 accumulation (compressed-value MB variant, Section 3.3)."""
+    rp, ci, _ = _csr(A)
+    x = _np(x, np.float64)
+    lv = _np(lowval, np.float32 if vkind == 1 else np.uint16)
+    y = np.empty(A.n_rows, np.float64)
+    _load().orc_spmv_lowp(A.n_rows, _p(rp), _p(ci), vkind, _p(lv), _p(x), _p(y))
+    return y
+
+
+def round_bf16(v) -> np.ndarray:
+    """Round-to-nearest-even double -> bfloat16 bit patterns (uint16)."""
+    v = _np(v, np.float64).reshape(-1)
+    out = np.empty(v.size, np.uint16)
+    _load().orc_round_bf16_array(v.size, _p(v), _p(out))
+    return out
+
+
+def round_f32(v) -> np.ndarray:
+    v = _np(v, np.float64).reshape(-1)
+    out = np.empty(v.size, np.float32)
+    _load().orc_round_f32_array(v.size, _p(v), _p(out))
+    return out
+
+
+def features(A, line_bytes: int = 128, l2_bytes: int = 0) -> dict:
+    """Table 1 (Section 3.2.2) features with the exact integer aggregates."""
+    rp, ci, _ = _csr(A)
+    f = Features()
+    _load().orc_features(A.n_rows, A.n_cols, _p(rp), _p(ci), line_bytes, l2_bytes, C.byref(f))
+    return f.as_dict()
+
+
+CML, MB, IMB, CMP = 0, 1, 2, 3
+
+
+def profile_class(s_noxmiss, s_inflate, s_balance, tau=(1.40, 1.15, 1.25)) -> int:
+    """Section 3.2.1 profiling-based classification rule (readings O9-O12)."""
+    return int(_load().orc_profile_class(s_noxmiss, s_inflate, s_balance, *tau))
+
+
+def class_variant(cls: int) -> int:
+    return int(_load().orc_class_variant(cls))
+
+
+def static_partition(A, n_workers: int) -> np.ndarray:
+    """Section 3.2.1 default partition: equal-nonzero contiguous row ranges."""
+    rp = _np(A.rowptr, np.int32)
+    out = np.empty(n_workers + 1, np.int64)
+    _load().orc_static_partition(A.n_rows, _p(rp), n_workers, _p(out))
+    return out
+
+
+def row_blocks(A, block_nnz: int) -> np.ndarray:
+    rp = _np(A.rowptr, np.int32)
+    nb = max(1, -(-A.nnz // block_nnz))
+    out = np.empty(nb + 1, np.int32)
+    _load().orc_row_blocks(A.n_rows, _p(rp), block_nnz, nb, _p(out))
+    return out
+
+
+def merge_path(A, items: int):
+    """Merge-path start coordinates (row, nonzero) of every part."""
+    rp = _np(A.rowptr, np.int32)
+    total = A.n_rows + A.nnz
+    parts = max(1, -(-total // items))
+    rs = np.empty(parts + 1, np.int32)
+    ns = np.empty(parts + 1, np.int32)
+    _load().orc_merge_path(A.n_rows, _p(rp), items, parts, _p(rs), _p(ns))
+    return rs, ns
+
+
+def compress_u16(A):
+    """16-bit column offsets from each row's first column (reading O13)."""
+    rp, ci, _ = _csr(A)
+    base = np.empty(A.n_rows, np.int32)
+    off = np.empty(A.nnz, np.uint16)
+    wide = _load().orc_compress_u16(A.n_rows, _p(rp), _p(ci), _p(base), _p(off))
+    return base, off, int(wide)
+
+
+def mlp_forward_f32(params: dict, v) -> np.ndarray:
+    """Fixed-order fmaf forward of the 16-H1-H2-K selector network."""
+    W1 = _np(params["W1"], np.float32); W2 = _np(params["W2"], np.float32)
+    W3 = _np(params["W3"], np.float32)
+    h1, h2, k = W1.shape[0], W2.shape[0], W3.shape[0]
+    v = _np(v, np.float32).reshape(-1, 16)
+    out = np.empty((v.shape[0], k), np.float32)
+    args = [_np(params[n], np.float32) for n in ("mean", "istd", "W1", "b1", "W2", "b2", "W3", "b3")]
+    for s in range(v.shape[0]):
+        row = np.ascontiguousarray(v[s])
+        res = np.empty(k, np.float32)
+        _load().orc_mlp_forward_f32(h1, h2, k, *[_p(a) for a in args], _p(row), _p(res))
+        out[s] = res
+    return out
+
+
+def argmax(logits) -> tuple[int, float]:
+    lg = _np(logits, np.float32)
+    m = C.c_float()
+    b = _load().orc_argmax(lg.size, _p(lg), C.byref(m))
+    return int(b), float(m.value)
+
+
+def mlp_loss_grad_f64(params: dict, z, labels):
+    """FP64 mean softmax cross-entropy and its gradients (backpropagation)."""
+    P64 = {n: _np(params[n], np.float64) for n in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    h1, h2, k = P64["W1"].shape[0], P64["W2"].shape[0], P64["W3"].shape[0]
+    z = _np(z, np.float64).reshape(-1, 16)
+    lab = _np(labels, np.int32)
+    G = {n: np.empty_like(a) for n, a in P64.items()}
+    loss = _load().orc_mlp_loss_grad_f64(
+        h1, h2, k, z.shape[0], *[_p(P64[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")],
+        _p(z), _p(lab), *[_p(G[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    return float(loss), G
+
+
+def cg(A, b, x0, iters: int, vkind: int = 0, lowval=None, refine: int = 0):
+    """Conjugate gradients in FP64 (optionally low-precision inner SpMV with
+    FP64 residual recomputation every `refine` iterations)."""
+    rp, ci, v = _csr(A)
+    n = A.n_rows
+    bb = _np(b, np.float64)
+    x = _np(x0, np.float64).copy()
+    lv = None
+    if vkind:
+        lv = _np(lowval, np.float32 if vkind == 1 else np.uint16)
+    resid = np.empty(iters + 1, np.float64)
+    r, p, q = (np.empty(n, np.float64) for _ in range(3))
+    _load().orc_cg(n, _p(rp), _p(ci), _p(v), vkind, _p(lv) if lv is not None else None,
+                   refine, _p(bb), _p(x), iters, _p(resid), _p(r), _p(p), _p(q))
+    return x, resid

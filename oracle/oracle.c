@@ -1,0 +1,507 @@
+/*
+ * CPU oracle for the SpMV optimization-selection method of Elafrou, Goumas and
+ * Koziris, "A lightweight optimization selection method for Sparse
+ * Matrix-Vector Multiplication" (arXiv 1511.02494).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, sequential
+ * restatement of what the method computes, used to check the CUDA library.
+ * Only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * may load it.  It shares no code, header or table with the CUDA library.
+ *
+ * Compiled with -O2 -ffp-contract=off: every floating-point operation below
+ * is rounded as written (no fused multiply-add unless fmaf is called).
+ *
+ * Readings of the paper where it is silent or garbled (numbered as in the
+ * design notes):
+ *   O1  Algorithm 1 writes an assignment over an inclusive, 1-based range; the
+ *       product is read as y_i = sum over the half-open 0-based range
+ *       [rowptr_i, rowptr_{i+1}), with y_i = 0 for an empty row.
+ *   O2  bw_i = last column - first column of row i; 0 when nnz_i <= 1.
+ *   O3  distance_i in disp_i = nnz_i / distance_i is span_i = bw_i + 1.
+ *   O4  ngroups_i counts maximal runs of consecutive column indices.
+ *   O5  element j (not the first of its row) is a miss when
+ *       8 * (c_j - c_{j-1}) > line_bytes; the first element of a non-empty
+ *       row always counts as a miss.
+ *   O6  miss_ratio is the literal Table 1 formula (1/N) * sum misses_i.
+ *   O7  standard deviations are population (1/N) deviations.
+ *   O8  size = 1 when bytes(rowptr, colind, val, x, y) <= LLC (here: L2) bytes.
+ *   O9-O12 profile rule: speedups sorted descending (ties broken in the
+ *       fixed order CML, MB, IMB); the first one strictly above its threshold
+ *       names the class; none above -> CMP.  s_inflate = T_inflate / T_base.
+ *   O15 empty rows take part in the row statistics with nnz = bw = 0 and
+ *       disp = clust = 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Section 2): y = A x over CSR, sequential FP64 accumulation in
+ * column order, reading O1.                                                  */
+void orc_spmv(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+              const double *val, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double s = 0.0;
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j)
+            s = s + val[j] * x[colind[j]];
+        y[i] = s;
+    }
+}
+
+/* Neumaier-compensated row sums (the reference of record for tolerances) and
+ * the per-row scale sum_j |a_ij x_j| that the tolerance is relative to.
+ * Only the listed rows are computed (all rows when rows == NULL).            */
+void orc_spmv_ref(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                  const double *val, const double *x, int64_t n_sel,
+                  const int64_t *rows, double *y, double *scale)
+{
+    int64_t n = rows ? n_sel : n_rows;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = rows ? rows[k] : k;
+        double s = 0.0, c = 0.0, a = 0.0;
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+            double p = val[j] * x[colind[j]];
+            double t = s + p;
+            if (fabs(s) >= fabs(p)) c += (s - t) + p;
+            else                    c += (p - t) + s;
+            s = t;
+            a += fabs(p);
+        }
+        y[k] = s + c;
+        scale[k] = a;
+    }
+}
+
+/* Low-precision stored values, FP64 accumulation (the compressed-value
+ * variant of the MB class, Section 3.3 / Table 2).  vkind: 1 = float32,
+ * 2 = bfloat16 bit patterns.                                                  */
+static double bf16_to_double(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+void orc_spmv_lowp(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                   int32_t vkind, const void *val, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double s = 0.0;
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+            double a = vkind == 1 ? (double)((const float *)val)[j]
+                                  : bf16_to_double(((const uint16_t *)val)[j]);
+            s = s + a * x[colind[j]];
+        }
+        y[i] = s;
+    }
+}
+
+/* IEEE round-to-nearest-even of a double to bfloat16 (8 significant bits,
+ * float32 exponent range), done in one rounding step: scale by a power of two
+ * so that one bfloat16 quantum becomes 1, round with nearbyint (ties to even
+ * in the default rounding mode), scale back.                                 */
+uint16_t orc_round_bf16(double v)
+{
+    if (isnan(v)) return 0x7FC0;
+    double a = fabs(v);
+    uint32_t sign = signbit(v) ? 0x8000u : 0u;
+    double q;
+    if (a == 0.0) {
+        q = 0.0;
+    } else {
+        int e;
+        frexp(a, &e);           /* a = m 2^e, m in [0.5, 1): leading bit 2^(e-1) */
+        int qexp = e - 8;       /* quantum for 8 significant bits */
+        if (qexp < -133) qexp = -133;   /* subnormal bfloat16 quantum 2^-133 */
+        q = ldexp(nearbyint(ldexp(a, -qexp)), qexp);
+    }
+    /* largest finite bfloat16: (2 - 2^-7) 2^127 */
+    if (q > ldexp(255.0, 120) || isinf(a)) return (uint16_t)(sign | 0x7F80u);
+    float f = (float)q;         /* exact: q has <= 8 significant bits */
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(sign | ((u >> 16) & 0x7FFFu));
+}
+
+void orc_round_bf16_array(int64_t n, const double *v, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_round_bf16(v[i]);
+}
+
+void orc_round_f32_array(int64_t n, const double *v, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = (float)v[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Table 1 (Section 3.2.2): structural features, as exact integer aggregates
+ * first, then the double formulas.                                           */
+typedef struct {
+    int64_t n_rows, n_cols, nnz, line_bytes, l2_bytes, working_set_bytes;
+    int64_t nnz_min, nnz_max;
+    uint64_t nnz_sum, nnz_sumsq_lo, nnz_sumsq_hi;
+    int64_t bw_min, bw_max;
+    uint64_t bw_sum, bw_sumsq_lo, bw_sumsq_hi;
+    uint64_t disp_sum, disp_sumsq_lo, disp_sumsq_hi; /* q = floor(2^32 nnz_i/span_i) */
+    uint64_t clust_sum;                              /* q = floor(2^32 ngroups_i/nnz_i) */
+    uint64_t ngroups_sum, misses_sum;
+    double size, density, nnz_avg, nnz_sd, bw_avg, bw_sd;
+    double disp_avg, disp_sd, clustering, miss_ratio;
+    float vec[16];
+} orc_features_t;
+
+/* population sd from exact integer sums: sqrt(N*S2 - S1^2) / N */
+static double sd_from_sums(uint64_t n, uint64_t s1, u128 s2)
+{
+    u128 num = (u128)n * s2 - (u128)s1 * (u128)s1;
+    return sqrt((double)num) / (double)n;
+}
+
+static float lg1p(double v) { return (float)log2(1.0 + v); }
+
+void orc_features(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                  const int32_t *colind, int64_t line_bytes, int64_t l2_bytes,
+                  orc_features_t *o)
+{
+    memset(o, 0, sizeof(*o));
+    int64_t nnz = n_rows > 0 ? rowptr[n_rows] : 0;
+    o->n_rows = n_rows; o->n_cols = n_cols; o->nnz = nnz;
+    o->line_bytes = line_bytes; o->l2_bytes = l2_bytes;
+    o->working_set_bytes = 4 * (n_rows + 1) + 12 * nnz + 8 * n_cols + 8 * n_rows;
+
+    u128 nnz_s2 = 0, bw_s2 = 0, disp_s2 = 0;
+    o->nnz_min = INT64_MAX; o->bw_min = INT64_MAX;
+    o->nnz_max = 0; o->bw_max = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t b = rowptr[i], e = rowptr[i + 1];
+        int64_t nz = e - b;
+        int64_t bw = 0, ngroups = 0, misses = 0;
+        uint64_t dq = 0, cq = 0;
+        if (nz > 0) {
+            bw = (int64_t)colind[e - 1] - (int64_t)colind[b];       /* O2 */
+            ngroups = 1; misses = 1;                                /* O4, O5 */
+            for (int64_t j = b + 1; j < e; ++j) {
+                int64_t d = (int64_t)colind[j] - (int64_t)colind[j - 1];
+                if (d != 1) ngroups += 1;
+                if (8 * d > line_bytes) misses += 1;
+            }
+            int64_t span = bw + 1;                                  /* O3 */
+            dq = (uint64_t)((((u128)nz) << 32) / (u128)span);
+            cq = (uint64_t)((((u128)ngroups) << 32) / (u128)nz);
+        }
+        if (nz < o->nnz_min) o->nnz_min = nz;
+        if (nz > o->nnz_max) o->nnz_max = nz;
+        if (bw < o->bw_min) o->bw_min = bw;
+        if (bw > o->bw_max) o->bw_max = bw;
+        o->nnz_sum += (uint64_t)nz;  nnz_s2 += (u128)nz * (u128)nz;
+        o->bw_sum += (uint64_t)bw;   bw_s2 += (u128)bw * (u128)bw;
+        o->disp_sum += dq;           disp_s2 += (u128)dq * (u128)dq;
+        o->clust_sum += cq;
+        o->ngroups_sum += (uint64_t)ngroups;
+        o->misses_sum += (uint64_t)misses;
+    }
+    if (n_rows == 0) { o->nnz_min = 0; o->bw_min = 0; }
+    o->nnz_sumsq_lo = (uint64_t)nnz_s2;  o->nnz_sumsq_hi = (uint64_t)(nnz_s2 >> 64);
+    o->bw_sumsq_lo = (uint64_t)bw_s2;    o->bw_sumsq_hi = (uint64_t)(bw_s2 >> 64);
+    o->disp_sumsq_lo = (uint64_t)disp_s2; o->disp_sumsq_hi = (uint64_t)(disp_s2 >> 64);
+
+    o->size = o->working_set_bytes <= l2_bytes ? 1.0 : 0.0;        /* O8 */
+    if (n_rows > 0 && n_cols > 0)
+        o->density = (double)nnz / ((double)n_rows * (double)n_cols);
+    if (n_rows > 0) {
+        const double q32 = 1.0 / 4294967296.0;
+        double N = (double)n_rows;
+        o->nnz_avg = (double)o->nnz_sum / N;
+        o->nnz_sd = sd_from_sums((uint64_t)n_rows, o->nnz_sum, nnz_s2);
+        o->bw_avg = (double)o->bw_sum / N;
+        o->bw_sd = sd_from_sums((uint64_t)n_rows, o->bw_sum, bw_s2);
+        o->disp_avg = ((double)o->disp_sum / N) * q32;
+        o->disp_sd = sd_from_sums((uint64_t)n_rows, o->disp_sum, disp_s2) * q32;
+        o->clustering = ((double)o->clust_sum / N) * q32;
+        o->miss_ratio = (double)o->misses_sum / N;
+    }
+    /* the 16-entry model input: the 14 Table 1 features (heavy-tailed counts
+     * on a log2(1+v) scale) plus log2 N and log2(1+NNZ)                       */
+    double dens = o->density > 0x1p-64 ? o->density : 0x1p-64;
+    o->vec[0] = (float)o->size;
+    o->vec[1] = (float)log2(dens);
+    o->vec[2] = lg1p((double)o->nnz_min);
+    o->vec[3] = lg1p((double)o->nnz_max);
+    o->vec[4] = lg1p(o->nnz_avg);
+    o->vec[5] = lg1p(o->nnz_sd);
+    o->vec[6] = lg1p((double)o->bw_min);
+    o->vec[7] = lg1p((double)o->bw_max);
+    o->vec[8] = lg1p(o->bw_avg);
+    o->vec[9] = lg1p(o->bw_sd);
+    o->vec[10] = (float)o->disp_avg;
+    o->vec[11] = (float)o->disp_sd;
+    o->vec[12] = (float)o->clustering;
+    o->vec[13] = lg1p(o->miss_ratio);
+    o->vec[14] = lg1p((double)n_rows);
+    o->vec[15] = lg1p((double)nnz);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.2.1 profiling-based classifier, readings O9-O12.
+ * Classes in the fixed tie order: 0 CML, 1 MB, 2 IMB; 3 CMP when no probe's
+ * speedup is strictly above its threshold.  NaN counts as -infinity.          */
+int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
+                          double tau_noxmiss, double tau_inflate, double tau_balance)
+{
+    double s[3] = {s_noxmiss, s_inflate, s_balance};
+    double tau[3] = {tau_noxmiss, tau_inflate, tau_balance};
+    int used[3] = {0, 0, 0};
+    for (int rank = 0; rank < 3; ++rank) {
+        int best = -1;
+        for (int c = 0; c < 3; ++c) {
+            if (used[c]) continue;
+            double v = isnan(s[c]) ? -INFINITY : s[c];
+            double bv = best < 0 ? 0.0 : (isnan(s[best]) ? -INFINITY : s[best]);
+            if (best < 0 || v > bv) best = c;   /* strict: ties keep the lower class */
+        }
+        used[best] = 1;
+        if (!isnan(s[best]) && s[best] > tau[best]) return best;
+    }
+    return 3;
+}
+
+/* Table 2 analogue on the GPU: class -> variant id.  Variant ids:
+ * 0 scalar, 1 sub-warp, 2 stream, 3 merge-path, 4 dynamic, 5 latency,
+ * 6 compressed.  CML -> latency, MB -> compressed, IMB -> merge-path,
+ * CMP -> stream.                                                            */
+int32_t orc_class_variant(int32_t cls)
+{
+    static const int32_t map[4] = {5, 6, 3, 2};
+    return (cls >= 0 && cls < 4) ? map[cls] : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.2.1 default partitioning for the balance benchmark: static 1-D
+ * row partition with (as near as possible) equal nonzeros per worker.
+ * bounds[w] = smallest row i with rowptr[i] >= floor(w * NNZ / W);
+ * bounds[W] = N.  Linear scan.                                               */
+void orc_static_partition(int64_t n_rows, const int32_t *rowptr, int64_t n_workers,
+                          int64_t *bounds)
+{
+    int64_t nnz = n_rows > 0 ? rowptr[n_rows] : 0;
+    int64_t i = 0;
+    for (int64_t w = 0; w < n_workers; ++w) {
+        int64_t target = (w * nnz) / n_workers;
+        while (i < n_rows && rowptr[i] < target) ++i;
+        bounds[w] = i;
+    }
+    bounds[n_workers] = n_rows;
+}
+
+/* Row blocks for the staged (stream) variant: block k owns the rows whose
+ * first nonzero index lies in the window [k B, (k+1) B):
+ * R_k = smallest i with rowptr[i] >= k B, R_{n_blocks} = N.  Linear scan.   */
+void orc_row_blocks(int64_t n_rows, const int32_t *rowptr, int64_t block_nnz,
+                    int64_t n_blocks, int32_t *out)
+{
+    int64_t i = 0;
+    for (int64_t k = 0; k < n_blocks; ++k) {
+        int64_t target = k * block_nnz;
+        while (i < n_rows && rowptr[i] < target) ++i;
+        out[k] = (int32_t)i;
+    }
+    out[n_blocks] = (int32_t)n_rows;
+}
+
+/* Merge-path coordinates for the balanced variant: the path merges the row
+ * ends rowptr[1..N] with the nonzero indices 0..NNZ-1; one step consumes the
+ * end of row i when all of its nonzeros have been consumed
+ * (rowptr[i+1] <= j), otherwise nonzero j.  Part p starts at diagonal
+ * d = min(p * items, N + NNZ).  Brute-force walk.                            */
+void orc_merge_path(int64_t n_rows, const int32_t *rowptr, int64_t items,
+                    int64_t n_parts, int32_t *row_start, int32_t *nz_start)
+{
+    int64_t nnz = n_rows > 0 ? rowptr[n_rows] : 0;
+    int64_t total = n_rows + nnz;
+    int64_t i = 0, j = 0, d = 0;
+    for (int64_t p = 0; p <= n_parts; ++p) {
+        int64_t target = p * items < total ? p * items : total;
+        while (d < target) {
+            if (i < n_rows && (j >= nnz || rowptr[i + 1] <= j)) ++i;
+            else ++j;
+            ++d;
+        }
+        row_start[p] = (int32_t)i;
+        nz_start[p] = (int32_t)j;
+    }
+}
+
+/* MB-class compression (Section 3.3, Table 2: column-index compression),
+ * GPU reading O13: each row stores its first column in rowbase and every
+ * column as a 16-bit offset from it when bw_i < 65536.  Wider rows keep
+ * their 32-bit columns and get rowbase = -1.  Empty rows: rowbase = 0.
+ * Returns the number of wide rows.                                           */
+int64_t orc_compress_u16(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                         int32_t *rowbase, uint16_t *off)
+{
+    int64_t wide = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t b = rowptr[i], e = rowptr[i + 1];
+        if (e == b) { rowbase[i] = 0; continue; }
+        int64_t first = colind[b];
+        if ((int64_t)colind[e - 1] - first >= 65536) {
+            rowbase[i] = -1;
+            ++wide;
+            for (int64_t j = b; j < e; ++j) off[j] = 0;
+        } else {
+            rowbase[i] = (int32_t)first;
+            for (int64_t j = b; j < e; ++j) off[j] = (uint16_t)(colind[j] - first);
+        }
+    }
+    return wide;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned selector: fully connected 16 -> H1 -> H2 -> K network with ReLU.
+ * Input standardisation z_k = (v_k - mean_k) * istd_k, each product and
+ * difference rounded to float.  Every dot product is a chain of fmaf calls
+ * starting from the bias, inputs in ascending order; that fixed order makes
+ * the logits reproducible bit for bit.  Weights are row-major [out][in].     */
+void orc_mlp_forward_f32(int32_t h1, int32_t h2, int32_t k,
+                         const float *mean, const float *istd,
+                         const float *W1, const float *b1, const float *W2, const float *b2,
+                         const float *W3, const float *b3, const float *v, float *logits)
+{
+    float z[16], a1[256], a2[256];
+    for (int i = 0; i < 16; ++i) z[i] = (v[i] - mean[i]) * istd[i];
+    for (int o = 0; o < h1; ++o) {
+        float acc = b1[o];
+        for (int i = 0; i < 16; ++i) acc = fmaf(W1[o * 16 + i], z[i], acc);
+        a1[o] = acc > 0.0f ? acc : 0.0f;
+    }
+    for (int o = 0; o < h2; ++o) {
+        float acc = b2[o];
+        for (int i = 0; i < h1; ++i) acc = fmaf(W2[o * h1 + i], a1[i], acc);
+        a2[o] = acc > 0.0f ? acc : 0.0f;
+    }
+    for (int o = 0; o < k; ++o) {
+        float acc = b3[o];
+        for (int i = 0; i < h2; ++i) acc = fmaf(W3[o * h2 + i], a2[i], acc);
+        logits[o] = acc;
+    }
+}
+
+/* argmax with ties to the lowest index; margin = best - second best logit. */
+int32_t orc_argmax(int32_t k, const float *logits, float *margin)
+{
+    int32_t b = 0;
+    for (int32_t o = 1; o < k; ++o) if (logits[o] > logits[b]) b = o;
+    float second = -INFINITY;
+    for (int32_t o = 0; o < k; ++o) if (o != b && logits[o] > second) second = logits[o];
+    *margin = k > 1 ? logits[b] - second : INFINITY;
+    return b;
+}
+
+/* FP64 forward + backward of the mean softmax cross-entropy over a batch,
+ * given standardized inputs z[B][16] and labels.  Gradients are written to
+ * g* (same layouts as the weights); returns the loss.  Textbook
+ * backpropagation, written out loop by loop.                                  */
+double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
+                             const double *W1, const double *b1, const double *W2,
+                             const double *b2, const double *W3, const double *b3,
+                             const double *z, const int32_t *label,
+                             double *gW1, double *gb1, double *gW2, double *gb2,
+                             double *gW3, double *gb3)
+{
+    memset(gW1, 0, sizeof(double) * h1 * 16); memset(gb1, 0, sizeof(double) * h1);
+    memset(gW2, 0, sizeof(double) * h2 * h1); memset(gb2, 0, sizeof(double) * h2);
+    memset(gW3, 0, sizeof(double) * k * h2);  memset(gb3, 0, sizeof(double) * k);
+    double loss = 0.0;
+    double a1[256], a2[256], p[256], d1[256], d2[256];
+    for (int32_t s = 0; s < batch; ++s) {
+        const double *x = z + (int64_t)s * 16;
+        for (int o = 0; o < h1; ++o) {
+            double acc = b1[o];
+            for (int i = 0; i < 16; ++i) acc += W1[o * 16 + i] * x[i];
+            a1[o] = acc > 0 ? acc : 0;
+        }
+        for (int o = 0; o < h2; ++o) {
+            double acc = b2[o];
+            for (int i = 0; i < h1; ++i) acc += W2[o * h1 + i] * a1[i];
+            a2[o] = acc > 0 ? acc : 0;
+        }
+        double mx = -INFINITY;
+        for (int o = 0; o < k; ++o) {
+            double acc = b3[o];
+            for (int i = 0; i < h2; ++i) acc += W3[o * h2 + i] * a2[i];
+            p[o] = acc;
+            if (acc > mx) mx = acc;
+        }
+        double den = 0.0;
+        for (int o = 0; o < k; ++o) { p[o] = exp(p[o] - mx); den += p[o]; }
+        for (int o = 0; o < k; ++o) p[o] /= den;
+        loss += -log(p[label[s]]);
+        /* dL/dlogit = (p - onehot) / B */
+        for (int o = 0; o < k; ++o) p[o] = (p[o] - (o == label[s] ? 1.0 : 0.0)) / batch;
+        for (int i = 0; i < h2; ++i) d2[i] = 0.0;
+        for (int o = 0; o < k; ++o) {
+            gb3[o] += p[o];
+            for (int i = 0; i < h2; ++i) { gW3[o * h2 + i] += p[o] * a2[i]; d2[i] += W3[o * h2 + i] * p[o]; }
+        }
+        for (int i = 0; i < h2; ++i) if (a2[i] <= 0) d2[i] = 0.0;
+        for (int i = 0; i < h1; ++i) d1[i] = 0.0;
+        for (int o = 0; o < h2; ++o) {
+            gb2[o] += d2[o];
+            for (int i = 0; i < h1; ++i) { gW2[o * h1 + i] += d2[o] * a1[i]; d1[i] += W2[o * h1 + i] * d2[o]; }
+        }
+        for (int i = 0; i < h1; ++i) if (a1[i] <= 0) d1[i] = 0.0;
+        for (int o = 0; o < h1; ++o) {
+            gb1[o] += d1[o];
+            for (int i = 0; i < 16; ++i) gW1[o * 16 + i] += d1[o] * x[i];
+        }
+    }
+    return loss / batch;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Conjugate gradients (Hestenes-Stiefel), the iterative solver the paper's
+ * SpMV serves (Section 1), in FP64 with sequential dot products.  When
+ * vkind != 0 the inner product A p uses the low-precision stored values
+ * lowval (1 = float32, 2 = bfloat16) and, every `refine` iterations (> 0),
+ * the residual is recomputed as r = b - A x with the FP64 values.
+ * resid[t] = ||r_t||_2 after iteration t (t = 0 is the initial residual).
+ * x holds x0 on entry.  Work arrays r, p, q have n entries each.             */
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i];
+    return s;
+}
+
+void orc_cg(int64_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+            int32_t vkind, const void *lowval, int32_t refine,
+            const double *b, double *x, int32_t iters, double *resid,
+            double *r, double *p, double *q)
+{
+    orc_spmv(n, rowptr, colind, val, x, q);
+    for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
+    double rs = dot(n, r, r);
+    resid[0] = sqrt(rs);
+    for (int32_t t = 1; t <= iters; ++t) {
+        if (vkind == 0) orc_spmv(n, rowptr, colind, val, p, q);
+        else orc_spmv_lowp(n, rowptr, colind, vkind, lowval, p, q);
+        double pq = dot(n, p, q);
+        double alpha = rs / pq;
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+        if (vkind != 0 && refine > 0 && t % refine == 0) {
+            orc_spmv(n, rowptr, colind, val, x, q);
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        } else {
+            for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+        }
+        double rs_new = dot(n, r, r);
+        double beta = rs_new / rs;
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rs = rs_new;
+        resid[t] = sqrt(rs);
+    }
+}

@@ -1,0 +1,456 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(hand-derived worked examples, closed forms, invariants, exact arithmetic and
+brute force), never against the oracle's own formulas.  CPU only."""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+
+def _exact_row_sums(A, x):
+    """Exact rational y_i = sum val_j * x_colj (every double is a rational)."""
+    rp, ci, v = A.rowptr.numpy(), A.colind.numpy(), A.val.numpy()
+    xs = [Fraction(float(t)) for t in np.asarray(x)]
+    out = []
+    for i in range(A.n_rows):
+        s = Fraction(0)
+        for j in range(rp[i], rp[i + 1]):
+            s += Fraction(float(v[j])) * xs[ci[j]]
+        out.append(s)
+    return out
+
+
+# --------------------------------------------------------------- SpMV (Alg. 1)
+def test_spmv_matches_dense_brute_force():
+    for seed in range(5):
+        A = synth.random_csr(23, 17, 9, seed=seed)
+        x = synth.uniform_vector(17, seed + 100)
+        D = np.zeros((23, 17))
+        rp, ci, v = A.rowptr.numpy(), A.colind.numpy(), A.val.numpy()
+        for i in range(23):
+            for j in range(rp[i], rp[i + 1]):
+                D[i, ci[j]] = v[j]
+        y = oracle.spmv(A, x)
+        exact = _exact_row_sums(A, x)
+        _, scale = oracle.spmv_ref(A, x)
+        for i in range(23):
+            # sequential FP64 sum of k terms: |err| <= k * u * sum|a x| (first order)
+            k = rp[i + 1] - rp[i]
+            assert abs(Fraction(y[i]) - exact[i]) <= Fraction(k * 2.0 ** -52 * scale[i] + 1e-300)
+        np.testing.assert_allclose(y, D @ x.numpy(), rtol=0, atol=1e-13)
+
+
+def test_spmv_integer_valued_is_exact_against_dense():
+    g = np.random.default_rng(3)
+    D = g.integers(-5, 6, size=(40, 31)).astype(np.float64)
+    D[g.random((40, 31)) < 0.6] = 0.0
+    D[7] = 0.0  # an empty row
+    A = synth.dense_to_csr(torch.from_numpy(D))
+    x = g.integers(-9, 10, size=31).astype(np.float64)
+    y = oracle.spmv(A, x)
+    assert np.array_equal(y, D @ x)
+    assert y[7] == 0.0
+
+
+def test_spmv_identity_and_permutation_exact():
+    n = 257
+    x = synth.uniform_vector(n, 1).numpy()
+    I = synth.dense_to_csr(torch.eye(n, dtype=torch.float64))
+    assert np.array_equal(oracle.spmv(I, x), x)
+    perm = np.random.default_rng(5).permutation(n)
+    P = np.zeros((n, n))
+    P[np.arange(n), perm] = 1.0
+    assert np.array_equal(oracle.spmv(synth.dense_to_csr(torch.from_numpy(P)), x), x[perm])
+
+
+def test_spmv_laplacian_closed_forms():
+    A = synth.laplacian_2d_5pt(64, 64)
+    # A 1 = 4 - (number of neighbours): 0 inside, 1 on an edge, 2 at a corner
+    y = oracle.spmv(A, np.ones(4096))
+    gy, gx = np.divmod(np.arange(4096), 64)
+    missing = (gy == 0).astype(int) + (gy == 63) + (gx == 0) + (gx == 63)
+    assert np.array_equal(y, missing.astype(np.float64))
+    # linear field a*gx + b*gy + c is annihilated at interior points
+    f = (3 * gx - 5 * gy + 7).astype(np.float64)
+    y = oracle.spmv(A, f)
+    inner = (gy > 0) & (gy < 63) & (gx > 0) & (gx < 63)
+    assert np.all(y[inner] == 0.0)
+
+
+def test_spmv_empty_matrix_and_rows():
+    A = synth.random_csr(0, 5, 3)
+    assert oracle.spmv(A, np.ones(5)).size == 0
+    A = synth.random_csr(50, 40, 0, seed=1)  # all rows empty
+    assert np.all(oracle.spmv(A, np.ones(40)) == 0.0)
+
+
+def test_spmv_ref_is_within_one_ulp_of_exact():
+    A = synth.random_csr(30, 30, 30, seed=7, empty_frac=0.0)
+    # cancellation-heavy values
+    A.val = torch.from_numpy(np.random.default_rng(7).standard_normal(A.nnz) * 1e8)
+    # x = 1: every product is exact, so the compensated sum is within one ulp
+    ones = np.ones(30)
+    y1, s1 = oracle.spmv_ref(A, ones)
+    exact1 = _exact_row_sums(A, ones)
+    for i in range(30):
+        assert abs(Fraction(y1[i]) - exact1[i]) <= Fraction(math.ulp(abs(y1[i])))
+        assert s1[i] == pytest.approx(float(np.abs(A.val.numpy()[A.rowptr[i]:A.rowptr[i + 1]]).sum()))
+    # general x: each product adds at most u |p| of rounding before the sum
+    x = synth.uniform_vector(30, 8)
+    y, scale = oracle.spmv_ref(A, x)
+    exact = _exact_row_sums(A, x)
+    for i in range(30):
+        bound = Fraction(math.ulp(abs(y[i]))) + Fraction(2.0 ** -52) * Fraction(scale[i])
+        assert abs(Fraction(y[i]) - exact[i]) <= bound
+    # the subset form agrees with the full form
+    rows = np.array([29, 0, 13], np.int64)
+    ys, ss = oracle.spmv_ref(A, x, rows)
+    assert np.array_equal(ys, y[rows]) and np.array_equal(ss, scale[rows])
+
+
+def test_spmv_lowp_equals_fp64_on_representable_values():
+    A = synth.random_csr(60, 50, 12, seed=2)
+    # values with 8 significant bits are exact in bfloat16 and float32
+    g = np.random.default_rng(2)
+    A.val = torch.from_numpy(g.integers(-128, 128, A.nnz).astype(np.float64) / 64.0)
+    x = synth.uniform_vector(50, 3)
+    ref = oracle.spmv(A, x)
+    assert np.array_equal(oracle.spmv_lowp(A, x, 1, oracle.round_f32(A.val)), ref)
+    assert np.array_equal(oracle.spmv_lowp(A, x, 2, oracle.round_bf16(A.val)), ref)
+
+
+# --------------------------------------------------------------- rounding
+def test_bf16_rounding_golden(golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "bf16_rounding.json")))
+    for c in d["cases"]:
+        v = Fraction(0)
+        for e in c["pow2"]:
+            if isinstance(e, str):
+                v -= Fraction(2) ** int(e[1:])
+            else:
+                v += Fraction(2) ** e
+        if c.get("neg"):
+            v = -v
+        got = int(oracle.round_bf16(np.array([float(v)]))[0])
+        assert got == int(c["bits"], 16), (c, hex(got))
+
+
+def _bf16_value(bits):
+    """Exact value of a finite bfloat16 bit pattern."""
+    s = -1 if bits & 0x8000 else 1
+    e = (bits >> 7) & 0xFF
+    f = bits & 0x7F
+    if e == 0:
+        return s * Fraction(f) * Fraction(2) ** -133
+    return s * (1 + Fraction(f, 128)) * Fraction(2) ** (e - 127)
+
+
+def test_bf16_rounding_brute_force_nearest_even():
+    """For random doubles across the range, the result is the nearest
+    bfloat16 by exact arithmetic, ties to the even fraction."""
+    g = np.random.default_rng(11)
+    vals = np.concatenate([g.standard_normal(300) * 2.0 ** g.integers(-140, 120, 300),
+                           g.uniform(-1, 1, 100)])
+    got = oracle.round_bf16(vals)
+    for v, b in zip(vals, got):
+        b = int(b)
+        fv = Fraction(float(v))
+        mag = abs(fv)
+        # candidates: the result and its neighbours
+        cand = [(c, _bf16_value(c)) for c in {b & 0x7FFF, max((b & 0x7FFF) - 1, 0), (b & 0x7FFF) + 1}
+                if ((c >> 7) & 0xFF) != 0xFF]
+        best = min(abs(_bf16_value(c) - mag) for c, _ in cand)
+        assert abs(_bf16_value(b & 0x7FFF) - mag) == best
+        ties = [c for c, val in cand if abs(val - mag) == best]
+        if len(ties) > 1:
+            assert (b & 1) == 0
+        assert (b >> 15) == (1 if v < 0 else 0)
+
+
+def test_f32_rounding_matches_numpy_cast():
+    v = np.random.default_rng(4).standard_normal(1000) * 1e3
+    assert np.array_equal(oracle.round_f32(v), v.astype(np.float32))
+
+
+# --------------------------------------------------------------- Table 1 features
+def test_features_tiny_worked_example(golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "features_tiny_4x4.json")))
+    D = np.zeros((4, 4))
+    for i, r in enumerate(d["rows"]):
+        D[i, r] = 1.0
+    A = synth.dense_to_csr(torch.from_numpy(D))
+    for lb, misses in d["misses_sum_by_line_bytes"].items():
+        f = oracle.features(A, line_bytes=int(lb), l2_bytes=1 << 20)
+        assert f["misses_sum"] == misses
+    f = oracle.features(A, line_bytes=64, l2_bytes=1 << 20)
+    for k in ("nnz_sum", "nnz_sumsq", "nnz_min", "nnz_max", "bw_min", "bw_max", "bw_sum",
+              "bw_sumsq", "ngroups_sum"):
+        assert f[k] == d[k], k
+    assert f["nnz_avg"] == d["nnz_avg"]
+    assert f["nnz_sd"] == pytest.approx(math.sqrt(d["nnz_sd_sq"]), rel=1e-15)
+    pr = d["per_row"]
+    q = [(n << 32) // m for n, m in pr["disp"]]
+    assert f["disp_sum"] == sum(q)
+    assert f["disp_avg"] == pytest.approx(sum(Fraction(n, m) for n, m in pr["disp"]) / 4, rel=1e-9)
+    cq = [(n << 32) // m for n, m in pr["clust"]]
+    assert f["clust_sum"] == sum(cq)
+    assert f["clustering"] == pytest.approx(float(sum(Fraction(n, m) for n, m in pr["clust"]) / 4),
+                                            rel=1e-9)
+    assert f["size"] == 1.0 and f["density"] == 7 / 16
+
+
+def test_features_laplacian_64_golden(golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "features_laplacian2d_64.json")))
+    A = synth.laplacian_2d_5pt(64, 64)
+    f = oracle.features(A, line_bytes=128, l2_bytes=126 << 20)
+    for k in ("nnz_sum", "nnz_sumsq", "nnz_min", "nnz_max", "bw_sum", "bw_sumsq", "bw_min",
+              "bw_max", "ngroups_sum", "misses_sum"):
+        assert f[k] == d[k], k
+    assert f["density"] == d["density"] and f["nnz_avg"] == d["nnz_avg"]
+    assert f["miss_ratio"] == d["miss_ratio"]
+    assert sum(t["count"] for t in d["row_types"]) == d["n"]
+    # per-row fixed-point sums from the hand-derived row classes
+    disp = sum(t["count"] * ((t["nnz"] << 32) // (t["bw"] + 1)) for t in d["row_types"])
+    clust = sum(t["count"] * ((t["ngroups"] << 32) // t["nnz"]) for t in d["row_types"])
+    assert f["disp_sum"] == disp and f["clust_sum"] == clust
+    exact_clust = sum(Fraction(t["count"] * t["ngroups"], t["nnz"]) for t in d["row_types"]) / 4096
+    assert f["clustering"] == pytest.approx(float(exact_clust), abs=4096 * 2.0 ** -32)
+    f64 = oracle.features(A, line_bytes=64, l2_bytes=0)
+    assert f64["misses_sum"] == d["misses_sum"] and f64["size"] == 0.0
+
+
+@pytest.mark.parametrize("n", [4, 8, 13])
+def test_features_27pt_stencil_closed_forms(n):
+    A = synth.stencil_27pt(n, seed=0)
+    f = oracle.features(A, line_bytes=128, l2_bytes=0)
+    assert f["nnz"] == (3 * n - 2) ** 3
+    assert (f["nnz_min"], f["nnz_max"]) == (8, 27)
+    assert f["bw_max"] == 2 * (n * n + n + 1) and f["bw_min"] == n * n + n + 1
+    # each row of the stencil has 9 groups (one per (dz,dy) pair present)
+    per_row = (3 - (np.arange(n) == 0) - (np.arange(n) == n - 1))
+    groups = int(np.sum(np.multiply.outer(per_row, per_row)) * n)  # pairs (z, y) present x rows in x
+    assert f["ngroups_sum"] == groups
+
+
+def test_features_empty_and_degenerate():
+    f = oracle.features(synth.random_csr(0, 0, 0), 128, 0)
+    assert f["nnz"] == 0 and f["nnz_min"] == 0 and f["nnz_avg"] == 0.0
+    A = synth.random_csr(10, 10, 0, seed=0)
+    f = oracle.features(A, 128, 1 << 20)
+    assert f["nnz_max"] == 0 and f["misses_sum"] == 0 and f["clustering"] == 0.0
+    # a single full dense row: one group, disp 1
+    A = synth.dense_to_csr(torch.ones(1, 300, dtype=torch.float64))
+    f = oracle.features(A, 128, 1 << 20)
+    assert f["ngroups_sum"] == 1 and f["disp_sum"] == 1 << 32 and f["bw_max"] == 299
+
+
+def test_features_invariants_random():
+    for seed in range(4):
+        A = synth.random_csr(200, 500, 40, seed=seed)
+        f = oracle.features(A, 64, 1 << 30)
+        lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
+        assert f["nnz_sum"] == A.nnz == int(lens.sum())
+        assert f["nnz_sumsq"] == int((lens.astype(np.int64) ** 2).sum())
+        assert f["nnz_sd"] == pytest.approx(float(np.std(lens)), rel=1e-12)
+        # misses and groups never exceed nnz; every nonempty row has >= 1 of each
+        nonempty = int((lens > 0).sum())
+        assert nonempty <= f["ngroups_sum"] <= A.nnz and nonempty <= f["misses_sum"] <= A.nnz
+        # shifting all columns by a constant changes nothing
+        B = synth.HostCSR(A.n_rows, A.n_cols + 3, A.rowptr, A.colind + 3, A.val)
+        g = oracle.features(B, 64, 1 << 30)
+        for k in ("bw_sum", "ngroups_sum", "misses_sum", "disp_sum", "clust_sum"):
+            assert f[k] == g[k]
+
+
+def test_feature_vector_definition():
+    A = synth.laplacian_2d_5pt(64, 64)
+    f = oracle.features(A, 128, 1 << 30)
+    v = f["vec"]
+    assert v.dtype == np.float32 and v.shape == (16,)
+    assert v[0] == 1.0 and v[14] == np.float32(math.log2(4097.0))
+    assert v[2] == np.float32(2.0)  # log2(1 + 3)
+
+
+# --------------------------------------------------------------- profile rule
+def test_profile_rule_golden(golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "profile_rule_cases.json")))
+    for c in d["cases"]:
+        got = oracle.profile_class(*c["s"], tau=tuple(d["tau"]))
+        assert d["classes"][got] == c["class"], c
+
+
+def test_profile_rule_nan_never_selected():
+    assert oracle.profile_class(float("nan"), 1.0, 1.0) == oracle.CMP
+    assert oracle.profile_class(float("nan"), 2.0, 1.0) == oracle.MB
+
+
+def test_class_to_variant_table():
+    # Table 2 analogue: CML -> latency (5), MB -> compressed (6),
+    # IMB -> merge-path (3), CMP -> stream (2)
+    assert [oracle.class_variant(c) for c in range(4)] == [5, 6, 3, 2]
+
+
+# --------------------------------------------------------------- partitions
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_static_partition_is_smallest_row_reaching_target(seed):
+    A = synth.zipf_rows(3000, 3000, 1.5, 800, seed=seed)
+    rp = A.rowptr.numpy().astype(np.int64)
+    for W in (1, 7, 64, 5000):
+        b = oracle.static_partition(A, W)
+        targets = (np.arange(W) * A.nnz) // W
+        assert np.array_equal(b[:-1], np.searchsorted(rp, targets, side="left"))
+        assert b[-1] == A.n_rows and np.all(np.diff(b) >= 0)
+
+
+def test_row_blocks_cover_rows_by_window():
+    A = synth.zipf_rows(2000, 2000, 1.6, 700, seed=4)
+    rp = A.rowptr.numpy().astype(np.int64)
+    for B in (64, 256, 1024):
+        R = oracle.row_blocks(A, B)
+        nb = -(-A.nnz // B)
+        assert R.size == nb + 1 and R[0] == 0 and R[-1] == A.n_rows
+        assert np.array_equal(R[:-1], np.searchsorted(rp, np.arange(nb) * B, side="left"))
+
+
+def _merge_coords_by_sorting(rp, items):
+    """Merge path by explicit sort of all items: row end i has key
+    (rowptr[i+1], 0, i), nonzero j has key (j, 1, j)."""
+    n = rp.size - 1
+    nnz = int(rp[-1])
+    keys = [(int(rp[i + 1]), 0, i) for i in range(n)] + [(j, 1, j) for j in range(nnz)]
+    keys.sort()
+    is_row = np.array([k[1] == 0 for k in keys], dtype=np.int64)
+    rows_before = np.concatenate([[0], np.cumsum(is_row)])
+    total = n + nnz
+    parts = max(1, -(-total // items))
+    d = np.minimum(np.arange(parts + 1) * items, total)
+    return rows_before[d], d - rows_before[d]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_merge_path_matches_sorted_merge(seed):
+    A = synth.random_csr(150, 90, 30, seed=seed, empty_frac=0.3)
+    rp = A.rowptr.numpy().astype(np.int64)
+    for items in (1, 5, 32, 224, 10 ** 6):
+        rs, ns = oracle.merge_path(A, items)
+        er, en = _merge_coords_by_sorting(rp, items)
+        assert np.array_equal(rs, er) and np.array_equal(ns, en)
+
+
+def test_compress_u16_decodes_and_flags_wide_rows():
+    A = synth.random_csr(300, 200_000, 6, seed=9)
+    base, off, wide = oracle.compress_u16(A)
+    rp, ci = A.rowptr.numpy(), A.colind.numpy()
+    n_wide = 0
+    for i in range(A.n_rows):
+        b, e = rp[i], rp[i + 1]
+        if b == e:
+            assert base[i] == 0
+            continue
+        if ci[e - 1] - ci[b] >= 65536:
+            n_wide += 1
+            assert base[i] == -1
+        else:
+            assert np.array_equal(base[i] + off[b:e].astype(np.int64), ci[b:e])
+    assert wide == n_wide > 0
+
+
+# --------------------------------------------------------------- MLP
+def _params(h1=64, h2=64, k=7, seed=0, scale=0.3):
+    g = np.random.default_rng(seed)
+    return {"mean": g.standard_normal(16).astype(np.float32),
+            "istd": (0.5 + g.random(16)).astype(np.float32),
+            "W1": (g.standard_normal((h1, 16)) * scale).astype(np.float32),
+            "b1": (g.standard_normal(h1) * 0.1).astype(np.float32),
+            "W2": (g.standard_normal((h2, h1)) * scale / 2).astype(np.float32),
+            "b2": (g.standard_normal(h2) * 0.1).astype(np.float32),
+            "W3": (g.standard_normal((k, h2)) * scale / 2).astype(np.float32),
+            "b3": (g.standard_normal(k) * 0.1).astype(np.float32)}
+
+
+def test_mlp_forward_exact_on_dyadic_network():
+    """Small dyadic weights make every float op exact: the result is the exact
+    real-arithmetic network output."""
+    g = np.random.default_rng(1)
+    P = {k: (np.round(v * 8) / 8).astype(np.float32) for k, v in _params(8, 8, 4, 1).items()}
+    P["istd"] = np.ones(16, np.float32)
+    v = (g.integers(-8, 8, (5, 16)) / 4).astype(np.float32)
+    got = oracle.mlp_forward_f32(P, v)
+    z = v.astype(np.float64) - P["mean"]
+    a1 = np.maximum(z @ P["W1"].T.astype(np.float64) + P["b1"], 0)
+    a2 = np.maximum(a1 @ P["W2"].T.astype(np.float64) + P["b2"], 0)
+    assert np.array_equal(got.astype(np.float64), a2 @ P["W3"].T.astype(np.float64) + P["b3"])
+
+
+def test_mlp_forward_close_to_fp64():
+    P = _params()
+    v = np.random.default_rng(2).standard_normal((20, 16)).astype(np.float32)
+    got = oracle.mlp_forward_f32(P, v)
+    z = (v - P["mean"]).astype(np.float64) * P["istd"]
+    a1 = np.maximum(z @ P["W1"].T.astype(np.float64) + P["b1"], 0)
+    a2 = np.maximum(a1 @ P["W2"].T.astype(np.float64) + P["b2"], 0)
+    ref = a2 @ P["W3"].T.astype(np.float64) + P["b3"]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-4)
+
+
+def test_argmax_ties_to_lowest_and_margin():
+    assert oracle.argmax(np.array([1, 3, 3, 2], np.float32)) == (1, 0.0)
+    assert oracle.argmax(np.array([5, 1, 2], np.float32)) == (0, 3.0)
+
+
+def test_mlp_gradients_match_finite_differences():
+    P = _params(16, 12, 5, 3)
+    g = np.random.default_rng(5)
+    z = g.standard_normal((9, 16))
+    lab = g.integers(0, 5, 9).astype(np.int32)
+    P64 = {k: v.astype(np.float64) for k, v in P.items()}
+    loss, G = oracle.mlp_loss_grad_f64(P64, z, lab)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = P64[name].reshape(-1)
+        for idx in g.choice(flat.size, min(12, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = oracle.mlp_loss_grad_f64(P64, z, lab)
+            flat[idx] = old - h
+            lm, _ = oracle.mlp_loss_grad_f64(P64, z, lab)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert G[name].reshape(-1)[idx] == pytest.approx(fd, rel=1e-5, abs=1e-8), name
+    # loss of uniform logits is log K
+    Z = {k: np.zeros_like(v) for k, v in P64.items()}
+    l0, _ = oracle.mlp_loss_grad_f64(Z, z, lab)
+    assert l0 == pytest.approx(math.log(5), rel=1e-15)
+
+
+# --------------------------------------------------------------- CG
+def test_cg_solves_small_spd_exactly_in_n_steps():
+    g = np.random.default_rng(0)
+    n = 12
+    M = g.standard_normal((n, n))
+    D = M @ M.T + n * np.eye(n)
+    A = synth.dense_to_csr(torch.from_numpy(D))
+    b = g.standard_normal(n)
+    x, resid = oracle.cg(A, b, np.zeros(n), n)
+    np.testing.assert_allclose(x, np.linalg.solve(D, b), rtol=1e-10, atol=1e-12)
+    assert resid[0] == pytest.approx(np.linalg.norm(b), rel=1e-15)
+    assert resid[n] < 1e-9 * resid[0]
+
+
+def test_cg_lowp_with_representable_values_equals_fp64():
+    A = synth.laplacian_3d_7pt(6)
+    b = synth.uniform_vector(A.n_rows, 2).numpy()
+    x64, r64 = oracle.cg(A, b, np.zeros(A.n_rows), 40)
+    x2, r2 = oracle.cg(A, b, np.zeros(A.n_rows), 40, vkind=2, lowval=oracle.round_bf16(A.val))
+    assert np.array_equal(x64, x2) and np.array_equal(r64, r2)
+    # with refinement the recomputed residual equals the recursive one to rounding
+    x3, r3 = oracle.cg(A, b, np.zeros(A.n_rows), 40, vkind=1, lowval=oracle.round_f32(A.val),
+                       refine=10)
+    np.testing.assert_allclose(x3, x64, rtol=1e-9, atol=1e-12)
