@@ -1,0 +1,265 @@
+/*
+ * spmv.h -- C ABI of the GB300 SpMV optimization-selection library.
+ *
+ * The library implements the method of Elafrou, Goumas and Koziris, "A
+ * lightweight optimization selection method for Sparse Matrix-Vector
+ * Multiplication" (arXiv 1511.02494) for one NVIDIA GB300 (sm_103a):
+ *
+ *   spmv_features(A)          structural features of Table 1 (Section 3.2.2)
+ *   spmv_profile(A, x)        the profiling runs of Section 3.2.1
+ *                             (baseline, noxmiss, inflate, balance)
+ *   spmv_select(f | profile)  bottleneck class (Section 3.1) and the variant
+ *                             that tackles it (Section 3.3, Table 2)
+ *   spmv_prepare(A, choice)   any format conversion the variant needs
+ *   spmv(P, x, y)             y = A x (Algorithm 1) with the chosen variant
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are CSR with 0-based int32 row pointers and column indices and
+ *     FP64 values; rowptr[0] = 0, rowptr[n_rows] = nnz, rowptr non-decreasing,
+ *     column indices in [0, n_cols) and strictly increasing within a row.
+ *   - Pointers inside spmv_csr_t and the x / y vectors are DEVICE pointers on
+ *     the current CUDA device, borrowed: the caller owns them and keeps them
+ *     alive while any call or prepared object uses them.  Host pointers are
+ *     named *_host.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernels
+ *     are launched on it; calls that return host results synchronize it.
+ *   - Every call returns an spmv_status; nothing throws across the ABI.  On
+ *     failure spmv_last_error() gives a message for the calling thread.
+ *   - No call falls back to the CPU: without a usable GPU calls fail with
+ *     SPMV_ERR_CUDA.
+ */
+#ifndef PAPER_1511_02494_GB300_SPMV_H
+#define PAPER_1511_02494_GB300_SPMV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *spmv_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, bad option */
+    SPMV_ERR_INVALID_CSR = 2,  /* the matrix breaks a CSR rule above      */
+    SPMV_ERR_UNSUPPORTED = 3,  /* variant/option not applicable to A       */
+    SPMV_ERR_NOMEM = 4,        /* device or host allocation failed         */
+    SPMV_ERR_CUDA = 5,         /* a CUDA runtime call or launch failed     */
+    SPMV_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up       */
+    SPMV_ERR_MODEL = 7         /* selector model missing, corrupt or bad   */
+} spmv_status;
+
+/* SpMV variants.  The class -> variant map (the GPU counterpart of Table 2,
+ * Section 3.3) is CML -> LATENCY, MB -> COMPRESSED, IMB -> MERGE,
+ * CMP -> STREAM.  SCALAR is the unoptimized CSR kernel (one thread per row,
+ * Algorithm 1 as written) against which speedups are reported. */
+typedef enum {
+    SPMV_V0_SCALAR = 0,     /* one thread per row                                */
+    SPMV_V1_SUBWARP = 1,    /* T lanes per row (T = 1..32), shuffle reduction    */
+    SPMV_V2_STREAM = 2,     /* row blocks staged through shared memory           */
+    SPMV_V3_MERGE = 3,      /* merge-path split of rows + nonzeros per warp      */
+    SPMV_V4_DYNAMIC = 4,    /* persistent warps taking row chunks from a counter */
+    SPMV_V5_LATENCY = 5,    /* gathers of x issued ahead, x kept in L2           */
+    SPMV_V6_COMPRESSED = 6, /* 16-bit column offsets, FP64/FP32/BF16 values      */
+    SPMV_NUM_VARIANTS = 7
+} spmv_variant;
+
+/* Bottleneck classes of Section 3.1. */
+typedef enum {
+    SPMV_CLASS_CML = 0, /* cache-miss latency on x        */
+    SPMV_CLASS_MB = 1,  /* memory bandwidth               */
+    SPMV_CLASS_IMB = 2, /* thread/workload imbalance      */
+    SPMV_CLASS_CMP = 3  /* computation / short rows       */
+} spmv_class;
+
+/* Storage type of the values of the COMPRESSED variant (x, y and the
+ * accumulation are always FP64). */
+typedef enum { SPMV_VAL_F64 = 0, SPMV_VAL_F32 = 1, SPMV_VAL_BF16 = 2 } spmv_value_type;
+
+/* A CSR matrix; all pointers are device pointers, borrowed. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int32_t *rowptr; /* [n_rows + 1] */
+    const int32_t *colind; /* [nnz]        */
+    const double *val;     /* [nnz]        */
+} spmv_csr_t;
+
+/* Structural features, Table 1 (Section 3.2.2).  The integer aggregates are
+ * exact; the doubles are computed from them on the host:
+ *   nnz_i   = nonzeros of row i
+ *   bw_i    = last column - first column of row i (0 when nnz_i <= 1)
+ *   span_i  = bw_i + 1 (the "distance" of disp_i)
+ *   disp_i  = nnz_i / span_i, kept as q = floor(2^32 disp_i)
+ *   clust_i = ngroups_i / nnz_i, kept as q = floor(2^32 clust_i); ngroups_i
+ *             counts maximal runs of consecutive columns
+ *   misses_i = 1 + #{j > first : 8 (c_j - c_{j-1}) > line_bytes}
+ * Empty rows count with every per-row quantity 0.  Averages divide by n_rows;
+ * deviations are population deviations, sqrt(N S2 - S1^2) / N.
+ * 128-bit sums are split into _lo / _hi 64-bit words.
+ * vec[16] is the selector input: size, log2 density, log2(1+v) of nnz_min,
+ * nnz_max, nnz_avg, nnz_sd, bw_min, bw_max, bw_avg, bw_sd, then disp_avg,
+ * disp_sd, clustering, log2(1 + miss_ratio), log2(1 + n_rows),
+ * log2(1 + nnz), each rounded to float. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz, line_bytes, l2_bytes, working_set_bytes;
+    int64_t nnz_min, nnz_max;
+    uint64_t nnz_sum, nnz_sumsq_lo, nnz_sumsq_hi;
+    int64_t bw_min, bw_max;
+    uint64_t bw_sum, bw_sumsq_lo, bw_sumsq_hi;
+    uint64_t disp_sum, disp_sumsq_lo, disp_sumsq_hi;
+    uint64_t clust_sum;
+    uint64_t ngroups_sum, misses_sum;
+    double size, density, nnz_avg, nnz_sd, bw_avg, bw_sd;
+    double disp_avg, disp_sd, clustering, miss_ratio;
+    float vec[16];
+} spmv_features_t;
+
+/* Result of the profiling runs of Section 3.2.1.  All runs use the baseline
+ * kernel: static 1-D row partition with equal nonzeros per worker (a warp),
+ * each worker walking its rows.
+ *   t_base_ms      median time of the baseline
+ *   t_noxmiss_ms   median time with every column index replaced by 0
+ *   t_inflate_ms   median time with 64-bit rowptr and colind
+ *   t_span_ms      balance run: last worker end - first worker start
+ *   t_worker_mean_ms  balance run: arithmetic mean of worker durations
+ *   s_noxmiss = t_base / t_noxmiss, s_inflate = t_inflate / t_base,
+ *   s_balance = t_span / t_worker_mean
+ *   total_ms       wall time of the whole spmv_profile call */
+typedef struct {
+    double t_base_ms, t_noxmiss_ms, t_inflate_ms, t_span_ms, t_worker_mean_ms;
+    double s_noxmiss, s_inflate, s_balance;
+    double total_ms;
+    int32_t n_workers, reps;
+} spmv_profile_t;
+
+/* Thresholds of the profiling rule (Section 3.2.1); a probe's speedup must be
+ * strictly greater than its threshold.  The paper does not print its values;
+ * spmv_default_thresholds() gives this library's calibrated defaults. */
+typedef struct {
+    double tau_noxmiss, tau_inflate, tau_balance;
+} spmv_thresholds_t;
+
+/* A variant and its launch parameters.  Zero parameters mean "choose".
+ *   threads_per_row : SUBWARP / LATENCY / COMPRESSED lanes per row (1..32, power of 2)
+ *   block_nnz       : STREAM nonzeros per row-block window (64..8192, power of 2)
+ *   items_per_warp  : MERGE merge-path items per warp (32 * k, k = 1..16)
+ *   value_type      : COMPRESSED value storage (spmv_value_type)
+ * Filled by spmv_select: cls (or -1), margin (model logit gap, or 0),
+ * used_fallback (1 when the model deferred to the profile rule), source
+ * (0 explicit, 1 profile rule, 2 model). */
+typedef struct {
+    int32_t variant;
+    int32_t cls;
+    int32_t threads_per_row;
+    int32_t block_nnz;
+    int32_t items_per_warp;
+    int32_t value_type;
+    float margin;
+    int32_t used_fallback;
+    int32_t source;
+} spmv_choice_t;
+
+/* A matrix prepared for one variant (opaque).  It borrows A's arrays and owns
+ * whatever the variant built from them. */
+typedef struct spmv_prepared spmv_prepared_t;
+
+/* What a prepared object holds (for inspection and tests). */
+typedef struct {
+    int32_t variant, threads_per_row, block_nnz, items_per_warp, value_type;
+    int64_t n_rows, n_cols, nnz;
+    int64_t n_blocks;      /* STREAM row blocks / MERGE parts / DYNAMIC chunks */
+    int64_t n_wide_rows;   /* COMPRESSED rows that kept 32-bit columns          */
+    int64_t owned_bytes;   /* device bytes owned by the object                  */
+    int64_t min_bytes;     /* minimum traffic of one spmv() with this format    */
+} spmv_prepared_info_t;
+
+/* Arrays a prepared object can export (spmv_prepared_export). */
+typedef enum {
+    SPMV_EXPORT_ROW_BLOCKS = 0, /* STREAM: int32 [n_blocks + 1] first row of each block */
+    SPMV_EXPORT_MERGE_ROWS = 1, /* MERGE: int32 [n_blocks + 1] start row of each part   */
+    SPMV_EXPORT_MERGE_NZ = 2,   /* MERGE: int32 [n_blocks + 1] start nonzero of a part  */
+    SPMV_EXPORT_ROWBASE = 3,    /* COMPRESSED: int32 [n_rows] first column, -1 = wide   */
+    SPMV_EXPORT_OFFSETS = 4,    /* COMPRESSED: uint16 [nnz] column - rowbase            */
+    SPMV_EXPORT_VALUES = 5      /* COMPRESSED: [nnz] values in value_type               */
+} spmv_export;
+
+/* ---- status ---------------------------------------------------------- */
+const char *spmv_status_str(spmv_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char *spmv_last_error(void);
+
+/* ---- validation -------------------------------------------------------- */
+/* Checks every CSR rule above on the device.  SPMV_ERR_INVALID_CSR when one
+ * fails; no device access ever leaves the arrays' declared extents. */
+spmv_status spmv_validate(const spmv_csr_t *A, spmv_stream_t stream);
+
+/* ---- Table 1 features (Section 3.2.2) ------------------------------------- */
+/* One pass over rowptr and colind (validating A on the way); fills *out
+ * (host) and synchronizes `stream`.  line_bytes: cache line assumed by the
+ * miss count (0 = 128, the GB300 L2 line).  size compares the working set
+ * with the device's L2 capacity. */
+spmv_status spmv_features(const spmv_csr_t *A, int32_t line_bytes, spmv_features_t *out,
+                          spmv_stream_t stream);
+
+/* ---- profiling runs (Section 3.2.1) ---------------------------------------- */
+/* Runs the baseline and the noxmiss, inflate and balance probes on A with the
+ * input vector x (device, n_cols), `reps` timed runs each (0 = 5) after one
+ * warm-up, and fills *out (host).  Allocates and frees its own temporary
+ * device buffers (a zeroed colind and 64-bit index copies: 4 nnz +
+ * 8 (n_rows + 1 + nnz) bytes).  Synchronizes `stream`. */
+spmv_status spmv_profile(const spmv_csr_t *A, const double *x, int32_t reps,
+                         spmv_profile_t *out, spmv_stream_t stream);
+
+/* ---- selection (Sections 3.1-3.3) ----------------------------------------- */
+spmv_thresholds_t spmv_default_thresholds(void);
+
+/* Class of a profile by the rule of Section 3.2.1: probe speedups examined
+ * from the largest down (ties in the order CML, MB, IMB); the first above its
+ * threshold names the class; none -> CMP.  th may be NULL (defaults). */
+spmv_status spmv_classify_profile(const spmv_profile_t *p, const spmv_thresholds_t *th,
+                                  int32_t *cls);
+
+/* Variant that tackles a class (see spmv_variant). */
+int32_t spmv_class_variant(int32_t cls);
+
+/* Chooses a variant.  With a profile (p != NULL) and no model, the profile
+ * rule decides.  Host-only; does not touch the GPU.  f may be NULL when p is
+ * given.  SPMV_ERR_INVALID_ARG when p holds a NaN or non-positive speedup. */
+spmv_status spmv_select(const spmv_features_t *f, const spmv_profile_t *p,
+                        const spmv_thresholds_t *th, spmv_choice_t *out);
+
+/* ---- prepare / run ---------------------------------------------------------- */
+/* Builds the prepared form of A for c->variant (validating A first unless
+ * `trusted` is non-zero), allocating device memory it owns.  Runs on
+ * `stream` and synchronizes it.  On failure *out is NULL. */
+spmv_status spmv_prepare(const spmv_csr_t *A, const spmv_choice_t *c, int32_t trusted,
+                         spmv_prepared_t **out, spmv_stream_t stream);
+
+/* y = A x (Algorithm 1, FP64 accumulation).  x: device [n_cols], y: device
+ * [n_rows]; x and y must not overlap.  Asynchronous on `stream`; does not
+ * allocate. */
+spmv_status spmv(const spmv_prepared_t *P, const double *x, double *y, spmv_stream_t stream);
+
+/* End-to-end form of spmv for host vectors: copies x_host [n_cols] to the
+ * device, runs spmv, copies y back to y_host [n_rows] and synchronizes
+ * `stream`.  Page-locked host buffers give full copy bandwidth.  The device
+ * staging vectors are allocated on the first call and owned by P. */
+spmv_status spmv_host(spmv_prepared_t *P, const double *x_host, double *y_host,
+                      spmv_stream_t stream);
+
+spmv_status spmv_prepared_info(const spmv_prepared_t *P, spmv_prepared_info_t *info);
+
+/* Copies one owned array of P (see spmv_export) into host memory dst of
+ * `bytes` bytes (must equal the array's size).  Synchronizes `stream`. */
+spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *dst,
+                                 int64_t bytes, spmv_stream_t stream);
+
+/* Releases everything P owns (device sync first).  NULL is ignored. */
+void spmv_prepared_free(spmv_prepared_t *P);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1511_02494_GB300_SPMV_H */

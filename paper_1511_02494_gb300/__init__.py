@@ -1,0 +1,205 @@
+"""GB300 SpMV optimization selection (arXiv 1511.02494) -- Python binding.
+
+A thin ctypes layer over the C ABI of ``include/spmv.h`` (library
+``libspmv_gb300.so``, built by :mod:`paper_1511_02494_gb300.build`).  The
+functions keep the C names; they only marshal arguments: every step of the
+computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the library is not built or
+no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from ._abi import (  # noqa: F401  (re-exported)
+    Choice, CSR, Features, PreparedInfo, Profile, Thresholds,
+    SPMV_OK, STATUS_NAMES, VARIANTS, VARIANT_IDS, CLASSES, VAL_F64, VAL_F32, VAL_BF16,
+    EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
+    EXPORT_VALUES, declare,
+)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspmv_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class SpmvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {LIB_PATH} is not built; run "
+                    "`python -m paper_1511_02494_gb300.build` (needs nvcc)")
+            _lib = declare(C.CDLL(LIB_PATH))
+    return _lib
+
+
+def _check(status: int):
+    if status != SPMV_OK:
+        msg = lib().spmv_last_error()
+        raise SpmvError(status, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+class DeviceCSR:
+    """A CSR matrix on the GPU (torch tensors) plus its ABI descriptor."""
+
+    def __init__(self, n_rows, n_cols, rowptr, colind, val):
+        import torch
+        for t, dt in ((rowptr, torch.int32), (colind, torch.int32), (val, torch.float64)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("DeviceCSR needs contiguous CUDA int32/int32/float64 tensors")
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.rowptr, self.colind, self.val = rowptr, colind, val
+        self.desc = CSR(self.n_rows, self.n_cols, int(colind.numel()),
+                        _ptr(rowptr), _ptr(colind), _ptr(val))
+
+    @property
+    def nnz(self):
+        return int(self.colind.numel())
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        """From any object with n_rows, n_cols, rowptr, colind, val tensors."""
+        return cls(A.n_rows, A.n_cols, A.rowptr.to(device).contiguous(),
+                   A.colind.to(device).contiguous(), A.val.to(device).contiguous())
+
+
+def _desc(A):
+    return A.desc if isinstance(A, DeviceCSR) else DeviceCSR.from_host(A).desc
+
+
+def spmv_status_str(status: int) -> str:
+    return lib().spmv_status_str(status).decode()
+
+
+def spmv_last_error() -> str:
+    return lib().spmv_last_error().decode()
+
+
+def spmv_validate(A: DeviceCSR, stream=None) -> None:
+    """Raises SpmvError(SPMV_ERR_INVALID_CSR) when A breaks a CSR rule."""
+    _check(lib().spmv_validate(C.byref(A.desc), _stream(stream)))
+
+
+def spmv_features(A: DeviceCSR, line_bytes: int = 128, stream=None) -> Features:
+    """Table 1 structural features (Section 3.2.2) computed on the GPU."""
+    out = Features()
+    _check(lib().spmv_features(C.byref(A.desc), line_bytes, C.byref(out), _stream(stream)))
+    return out
+
+
+def spmv_profile(A: DeviceCSR, x, reps: int = 5, stream=None) -> Profile:
+    """Profiling runs of Section 3.2.1 (baseline, noxmiss, inflate, balance)."""
+    out = Profile()
+    _check(lib().spmv_profile(C.byref(A.desc), _ptr(x), reps, C.byref(out), _stream(stream)))
+    return out
+
+
+def spmv_default_thresholds() -> Thresholds:
+    return lib().spmv_default_thresholds()
+
+
+def spmv_classify_profile(profile: Profile, thresholds: Thresholds | None = None) -> int:
+    cls = C.c_int32()
+    _check(lib().spmv_classify_profile(C.byref(profile),
+                                       C.byref(thresholds) if thresholds else None, C.byref(cls)))
+    return cls.value
+
+
+def spmv_class_variant(cls: int) -> int:
+    return int(lib().spmv_class_variant(cls))
+
+
+def spmv_select(features: Features | None = None, profile: Profile | None = None,
+                thresholds: Thresholds | None = None) -> Choice:
+    out = Choice()
+    _check(lib().spmv_select(C.byref(features) if features else None,
+                             C.byref(profile) if profile else None,
+                             C.byref(thresholds) if thresholds else None, C.byref(out)))
+    return out
+
+
+def make_choice(variant, threads_per_row=0, block_nnz=0, items_per_warp=0,
+                value_type=VAL_F64) -> Choice:
+    v = VARIANT_IDS[variant] if isinstance(variant, str) else int(variant)
+    c = Choice()
+    c.variant, c.cls = v, -1
+    c.threads_per_row, c.block_nnz, c.items_per_warp = threads_per_row, block_nnz, items_per_warp
+    c.value_type = value_type
+    return c
+
+
+class Prepared:
+    """Owner of an spmv_prepared_t; keeps the matrix tensors alive."""
+
+    def __init__(self, handle, A: DeviceCSR):
+        self.handle, self.A = handle, A
+
+    def info(self) -> PreparedInfo:
+        return spmv_prepared_info(self)
+
+    def free(self):
+        if self.handle:
+            lib().spmv_prepared_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spmv_prepare(A: DeviceCSR, choice: Choice, trusted: bool = False, stream=None) -> Prepared:
+    h = C.c_void_p()
+    _check(lib().spmv_prepare(C.byref(A.desc), C.byref(choice), int(trusted), C.byref(h),
+                              _stream(stream)))
+    return Prepared(h, A)
+
+
+def spmv(P: Prepared, x, y, stream=None) -> None:
+    """y = A x on the GPU (asynchronous on the stream)."""
+    _check(lib().spmv(P.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def spmv_host(P: Prepared, x_host, y_host, stream=None) -> None:
+    """y_host = A x_host with host (ideally pinned) float64 tensors."""
+    _check(lib().spmv_host(P.handle, _ptr(x_host), _ptr(y_host), _stream(stream)))
+
+
+def spmv_prepared_info(P: Prepared) -> PreparedInfo:
+    out = PreparedInfo()
+    _check(lib().spmv_prepared_info(P.handle, C.byref(out)))
+    return out
+
+
+def spmv_prepared_export(P: Prepared, which: int, out_tensor, stream=None) -> None:
+    """Copies an owned array of P into a host tensor of exactly its size."""
+    nbytes = out_tensor.numel() * out_tensor.element_size()
+    _check(lib().spmv_prepared_export(P.handle, which, _ptr(out_tensor), nbytes, _stream(stream)))
+
+
+def spmv_prepared_free(P: Prepared) -> None:
+    P.free()

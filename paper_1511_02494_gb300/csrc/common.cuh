@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (that is include/spmv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "spmv.h"
+
+namespace spmvlib {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// ---- error reporting ------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+const char* last_error_cstr();
+spmv_status fail(spmv_status s, const std::string& msg);
+spmv_status cuda_fail(cudaError_t e, const char* what);
+
+#define SPMV_CUDA_TRY(expr)                                        \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return ::spmvlib::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ---- device facts ------------------------------------------------------------
+struct DeviceInfo {
+    int device = -1;
+    int sm_count = 0;
+    int l2_bytes = 0;
+    int max_persist_l2 = 0;
+    int max_window = 0;
+};
+// Facts of the current device (queried once per device).
+spmv_status current_device(DeviceInfo* out);
+
+// ---- matrix checks on the host side of the ABI ----------------------------------
+spmv_status check_csr_args(const spmv_csr_t* A);
+
+// ---- the prepared object ----------------------------------------------------------
+}  // namespace spmvlib
+
+struct spmv_prepared {
+    spmv_csr_t A{};
+    spmv_choice_t c{};
+    int device = -1;
+    int64_t n_blocks = 0;          // STREAM blocks / MERGE parts / DYNAMIC chunks
+    int32_t* blocks = nullptr;     // STREAM row blocks, MERGE start rows
+    int32_t* merge_nz = nullptr;   // MERGE start nonzeros
+    int32_t* carry_row = nullptr;  // MERGE per-part carry row
+    double* carry_val = nullptr;   // MERGE per-part carry value
+    unsigned int* counter = nullptr;  // DYNAMIC work counter
+    int32_t* rowbase = nullptr;    // COMPRESSED
+    uint16_t* off16 = nullptr;     // COMPRESSED
+    void* lowval = nullptr;        // COMPRESSED values (F32/BF16), or NULL for F64
+    int64_t n_wide = 0;
+    double* x_stage = nullptr;     // spmv_host staging
+    double* y_stage = nullptr;
+    int64_t owned_bytes = 0;
+    int sm_count = 0;
+    int l2_window_bytes = 0;       // LATENCY: bytes of x kept persisting in L2
+};
+
+namespace spmvlib {
+
+// ---- kernel launchers (spmv_kernels.cu) -------------------------------------------
+cudaError_t launch_scalar(const spmv_csr_t& A, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_subwarp(const spmv_csr_t& A, int T, const double* x, double* y,
+                           cudaStream_t s);
+cudaError_t launch_row_blocks(const spmv_csr_t& A, int64_t block_nnz, int64_t n_blocks,
+                              int32_t* blocks, cudaStream_t s);
+cudaError_t launch_stream(const spmv_csr_t& A, const int32_t* blocks, int64_t n_blocks,
+                          int block_nnz, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_merge_coords(const spmv_csr_t& A, int items, int64_t n_parts,
+                                int32_t* mrow, int32_t* mnz, cudaStream_t s);
+cudaError_t launch_merge(const spmv_csr_t& A, int items, const int32_t* mrow,
+                         const int32_t* mnz, int64_t n_parts, int32_t* carry_row,
+                         double* carry_val, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_dynamic(const spmv_csr_t& A, int T, int chunk_rows, unsigned int* counter,
+                           int sm_count, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_latency(const spmv_csr_t& A, int T, const double* x, double* y,
+                           int l2_window_bytes, cudaStream_t s);
+cudaError_t launch_compress(const spmv_csr_t& A, int32_t* rowbase, uint16_t* off16,
+                            unsigned long long* n_wide, int value_type, void* lowval,
+                            cudaStream_t s);
+cudaError_t launch_compressed(const spmv_csr_t& A, int T, int value_type,
+                              const int32_t* rowbase, const uint16_t* off16,
+                              const void* lowval, bool all_wide, const double* x, double* y,
+                              cudaStream_t s);
+
+// ---- features / validation (features.cu) --------------------------------------------
+// Per-row pass; when `features_out` is NULL only validates.  err bits:
+// 1 rowptr[0] != 0, 2 rowptr[n] != nnz, 4 rowptr decreasing / out of range,
+// 8 column out of range, 16 columns not strictly increasing.
+spmv_status run_feature_pass(const spmv_csr_t* A, int32_t line_bytes,
+                             spmv_features_t* features_out, cudaStream_t s);
+
+// Default lanes per row for a mean row length.
+int auto_threads_per_row(double mean_nnz);
+
+}  // namespace spmvlib

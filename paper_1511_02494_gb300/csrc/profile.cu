@@ -1,0 +1,214 @@
+// Profiling runs of the profiling-based classifier (Section 3.2.1).
+//
+// The baseline is CSR SpMV under the paper's default partitioning: a static
+// 1-D row partition with (as nearly as possible) equal nonzeros per worker.
+// On the GPU a worker is one warp; the number of workers is the number of
+// warps the device keeps resident at once, so every worker runs from the
+// start of the launch.  A worker walks its rows in order, its 32 lanes
+// striding each row's nonzeros.
+//   noxmiss: the same kernel with every column index replaced by 0, which
+//            removes the irregular accesses to x;
+//   inflate: the same kernel with 64-bit rowptr and colind, which enlarges
+//            the working set;
+//   balance: the same kernel recording each worker's start and end time
+//            (%globaltimer); the metric is the launch span over the mean
+//            worker duration, i.e. what balancing the load could reclaim.
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+
+namespace spmvlib {
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounds[w] = smallest row i with rowptr[i] >= floor(w * nnz / W); bounds[W] = N.
+__global__ void k_static_bounds(int64_t n_rows, int64_t nnz, const int* __restrict__ rp,
+                                int64_t n_workers, int64_t* __restrict__ bounds)
+{
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > n_workers) return;
+    if (w == n_workers) { bounds[w] = n_rows; return; }
+    const int64_t target = (w * nnz) / n_workers;
+    int64_t lo = 0, hi = n_rows;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)rp[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    bounds[w] = lo;
+}
+
+template <typename IT>
+__global__ void k_widen(int64_t n, const int* __restrict__ in, IT* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (IT)in[i];
+}
+
+template <typename IT, bool STAMP>
+__global__ void __launch_bounds__(256)
+k_base(int64_t n_workers, const int64_t* __restrict__ bounds, const IT* __restrict__ rp,
+       const IT* __restrict__ ci, const double* __restrict__ v, const double* __restrict__ x,
+       double* __restrict__ y, unsigned long long* __restrict__ stamps)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_workers) return;
+    unsigned long long t0 = 0;
+    if (STAMP) t0 = global_ns();
+    const int64_t rb = bounds[w], re = bounds[w + 1];
+    for (int64_t r = rb; r < re; ++r) {
+        const int64_t b = (int64_t)rp[r], e = (int64_t)rp[r + 1];
+        double s = 0.0;
+        for (int64_t j = b + lane; j < e; j += 32) s += v[j] * x[ci[j]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+        if (lane == 0) y[r] = s;
+    }
+    if (STAMP && lane == 0) {
+        const unsigned long long t1 = global_ns();
+        stamps[2 * w] = t0;
+        stamps[2 * w + 1] = t1;
+    }
+}
+
+template <typename IT, bool STAMP>
+cudaError_t launch_base(int64_t n_workers, const int64_t* bounds, const IT* rp, const IT* ci,
+                        const double* v, const double* x, double* y, unsigned long long* st,
+                        cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((n_workers * 32 + 255) / 256);
+    k_base<IT, STAMP><<<grid, 256, 0, s>>>(n_workers, bounds, rp, ci, v, x, y, st);
+    return cudaGetLastError();
+}
+
+double median(std::vector<double> v)
+{
+    std::sort(v.begin(), v.end());
+    const size_t n = v.size();
+    return n % 2 ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
+};
+
+}  // namespace
+
+}  // namespace spmvlib
+
+using namespace spmvlib;
+
+extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_t reps,
+                                    spmv_profile_t* out, spmv_stream_t stream)
+{
+    clear_error();
+    const auto wall0 = std::chrono::steady_clock::now();
+    if (!out || !x) return fail(SPMV_ERR_INVALID_ARG, "spmv_profile: NULL argument");
+    spmv_status st = check_csr_args(A);
+    if (st != SPMV_OK) return st;
+    if (A->n_rows == 0 || A->nnz == 0)
+        return fail(SPMV_ERR_UNSUPPORTED, "spmv_profile: empty matrix has nothing to profile");
+    if (reps <= 0) reps = 5;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceInfo dev;
+    st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    st = run_feature_pass(A, 128, nullptr, s);  // validation only
+    if (st != SPMV_OK) return st;
+
+    int per_sm = 0;
+    SPMV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_base<int, false>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t W = (int64_t)dev.sm_count * per_sm * 8;
+    const int64_t N = A->n_rows, NNZ = A->nnz;
+
+    DevBuf b_bounds, b_zero, b_rp64, b_ci64, b_y, b_st;
+    b_bounds.s = b_zero.s = b_rp64.s = b_ci64.s = b_y.s = b_st.s = s;
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_bounds.p, sizeof(int64_t) * (W + 1), s));
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_zero.p, sizeof(int) * NNZ, s));
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_rp64.p, sizeof(int64_t) * (N + 1), s));
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_ci64.p, sizeof(int64_t) * NNZ, s));
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_y.p, sizeof(double) * N, s));
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_st.p, sizeof(unsigned long long) * 2 * W, s));
+    int64_t* bounds = static_cast<int64_t*>(b_bounds.p);
+    int* zero_ci = static_cast<int*>(b_zero.p);
+    int64_t* rp64 = static_cast<int64_t*>(b_rp64.p);
+    int64_t* ci64 = static_cast<int64_t*>(b_ci64.p);
+    double* y = static_cast<double*>(b_y.p);
+    unsigned long long* stamps = static_cast<unsigned long long*>(b_st.p);
+
+    k_static_bounds<<<(unsigned)((W + 1 + 255) / 256), 256, 0, s>>>(N, NNZ, A->rowptr, W, bounds);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    SPMV_CUDA_TRY(cudaMemsetAsync(zero_ci, 0, sizeof(int) * NNZ, s));
+    k_widen<int64_t><<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(N + 1, A->rowptr, rp64);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    k_widen<int64_t><<<(unsigned)((NNZ + 255) / 256), 256, 0, s>>>(NNZ, A->colind, ci64);
+    SPMV_CUDA_TRY(cudaGetLastError());
+
+    cudaEvent_t e0, e1;
+    SPMV_CUDA_TRY(cudaEventCreate(&e0));
+    SPMV_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_runs = [&](int which, double* ms_out) -> cudaError_t {
+        std::vector<double> t;
+        for (int r = 0; r <= reps; ++r) {
+            cudaError_t e = cudaEventRecord(e0, s);
+            if (e != cudaSuccess) return e;
+            if (which == 0)
+                e = launch_base<int, false>(W, bounds, A->rowptr, A->colind, A->val, x, y, nullptr, s);
+            else if (which == 1)
+                e = launch_base<int, false>(W, bounds, A->rowptr, zero_ci, A->val, x, y, nullptr, s);
+            else
+                e = launch_base<int64_t, false>(W, bounds, rp64, ci64, A->val, x, y, nullptr, s);
+            if (e != cudaSuccess) return e;
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+            if (r > 0) t.push_back(ms);  // the first run is the warm-up
+        }
+        *ms_out = median(t);
+        return cudaSuccess;
+    };
+    spmv_profile_t p = {};
+    cudaError_t e = time_runs(0, &p.t_base_ms);
+    if (e == cudaSuccess) e = time_runs(1, &p.t_noxmiss_ms);
+    if (e == cudaSuccess) e = time_runs(2, &p.t_inflate_ms);
+    std::vector<unsigned long long> h(2 * W);
+    if (e == cudaSuccess)
+        e = launch_base<int, true>(W, bounds, A->rowptr, A->colind, A->val, x, y, stamps, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), stamps, sizeof(unsigned long long) * 2 * W,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_profile runs");
+
+    unsigned long long tmin = ~0ull, tmax = 0;
+    double sum = 0.0;
+    for (int64_t w = 0; w < W; ++w) {
+        tmin = std::min(tmin, h[2 * w]);
+        tmax = std::max(tmax, h[2 * w + 1]);
+        sum += (double)(h[2 * w + 1] - h[2 * w]);
+    }
+    p.t_span_ms = (double)(tmax - tmin) * 1e-6;
+    p.t_worker_mean_ms = sum / (double)W * 1e-6;
+    p.s_noxmiss = p.t_base_ms / p.t_noxmiss_ms;
+    p.s_inflate = p.t_inflate_ms / p.t_base_ms;
+    p.s_balance = p.t_worker_mean_ms > 0 ? p.t_span_ms / p.t_worker_mean_ms : 1.0;
+    p.n_workers = (int32_t)W;
+    p.reps = reps;
+    // buffers are released (stream-ordered) by the DevBuf destructors; the
+    // wall time includes everything up to here
+    p.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    *out = p;
+    return SPMV_OK;
+}

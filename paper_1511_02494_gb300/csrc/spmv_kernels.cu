@@ -1,0 +1,639 @@
+// SpMV variants y = A x over CSR (Algorithm 1, Section 2), one per bottleneck
+// class of Section 3.1, plus the preprocessing kernels some of them need.
+//
+// Every kernel writes every y[i] (empty rows get 0), accumulates in FP64 and
+// never reads outside the arrays' extents for a CSR that passed validation.
+// Loads of the streamed arrays (rowptr, colind, val) bypass L1 allocation
+// where they are touched once; gathers of x go through the read-only
+// (non-coherent) path.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace spmvlib {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double ldg_x(const double* p) { return __ldg(p); }
+
+// streaming (evict-first) loads for data touched once
+__device__ __forceinline__ int ld_cs(const int* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_cs(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ unsigned short ld_cs(const unsigned short* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_cs(const float* p) { return __ldcs(p); }
+
+__device__ __forceinline__ double warp_sum(double s, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+    return s;
+}
+
+// ------------------------------------------------------------------------
+// V0 SCALAR: one thread per row, Algorithm 1 as written.  The unoptimized
+// CSR kernel that speedups are measured against.
+__global__ void __launch_bounds__(kBlock)
+k_scalar(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ ci,
+         const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y)
+{
+    int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n_rows) return;
+    int b = rp[i], e = rp[i + 1];
+    double s = 0.0;
+    for (int j = b; j < e; ++j) s += v[j] * x[ci[j]];
+    y[i] = s;
+}
+
+// ------------------------------------------------------------------------
+// V1 SUBWARP: T lanes per row (CMP class: short-row loop overhead and
+// vectorisation, Table 2 "unrolling + vectorization").  Each lane keeps two
+// independent partial sums; the T partials are combined by shuffles.
+template <int T>
+__global__ void __launch_bounds__(kBlock)
+k_subwarp(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ ci,
+          const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t row = (int64_t)blockIdx.x * (kBlock / T) + threadIdx.x / T;
+    const int lane = threadIdx.x & (T - 1);
+    int64_t b = 0, e = 0;
+    if (row < n_rows) { b = rp[row]; e = rp[row + 1]; }
+    double s0 = 0.0, s1 = 0.0;
+    int64_t j = b + lane;
+    for (; j + T < e; j += 2 * T) {
+        s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+        s1 = fma(ld_cs(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
+    }
+    if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+    double s = warp_sum(s0 + s1, T);
+    if (lane == 0 && row < n_rows) y[row] = s;
+}
+
+// ------------------------------------------------------------------------
+// V2 STREAM: row blocks.  Block k owns the rows whose first nonzero lies in
+// the window [k B, (k+1) B).  The CTA stages the products val*x of the whole
+// block in shared memory with coalesced loads, then reduces each row from
+// shared memory with a power-of-two group of threads per row.  A block whose
+// nonzeros exceed the staging capacity (it holds a row longer than B) is
+// reduced row by row by the whole CTA straight from global memory.
+
+// R_k = smallest i with rowptr[i] >= k B (k < n_blocks), R_n_blocks = n_rows.
+__global__ void k_row_blocks(int64_t n_rows, const int* __restrict__ rp, int64_t block_nnz,
+                             int64_t n_blocks, int32_t* __restrict__ out)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_blocks) return;
+    if (k == n_blocks) { out[k] = (int32_t)n_rows; return; }
+    int64_t target = k * block_nnz;
+    int64_t lo = 0, hi = n_rows;  // answer in [0, n_rows]
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)rp[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    out[k] = (int32_t)lo;
+}
+
+__device__ __forceinline__ double block_sum(double s, double* red) {
+    s = warp_sum(s, 32);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = lane < (kBlock / 32) ? red[lane] : 0.0;
+        t = warp_sum(t, 32);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_stream(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+         const double* __restrict__ x, double* __restrict__ y, const int32_t* __restrict__ blocks,
+         int cap)
+{
+    extern __shared__ double prod[];
+    __shared__ double red[kBlock / 32];
+    const int64_t k = blockIdx.x;
+    const int r0 = blocks[k], r1 = blocks[k + 1];
+    if (r0 == r1) return;
+    const int nz0 = rp[r0], nz1 = rp[r1];
+    const int cnt = nz1 - nz0;
+    const int nrows = r1 - r0;
+    if (cnt <= cap) {
+        for (int t = threadIdx.x; t < cnt; t += kBlock)
+            prod[t] = ld_cs(v + nz0 + t) * ldg_x(x + ld_cs(ci + nz0 + t));
+        __syncthreads();
+        if (nrows >= kBlock) {
+            for (int r = threadIdx.x; r < nrows; r += kBlock) {
+                const int b = rp[r0 + r] - nz0, e = rp[r0 + r + 1] - nz0;
+                double s = 0.0;
+                for (int j = b; j < e; ++j) s += prod[j];
+                y[r0 + r] = s;
+            }
+        } else {
+            int T = 1;
+            while (T < 32 && nrows * (T * 2) <= kBlock) T *= 2;
+            const int g = threadIdx.x / T, lane = threadIdx.x & (T - 1);
+            double s = 0.0;
+            int b = 0, e = 0;
+            if (g < nrows) { b = rp[r0 + g] - nz0; e = rp[r0 + g + 1] - nz0; }
+            for (int j = b + lane; j < e; j += T) s += prod[j];
+            s = warp_sum(s, T);
+            if (lane == 0 && g < nrows) y[r0 + g] = s;
+        }
+    } else {
+        for (int r = r0; r < r1; ++r) {
+            const int b = rp[r], e = rp[r + 1];
+            double s0 = 0.0, s1 = 0.0;
+            int j = b + threadIdx.x;
+            for (; j + kBlock < e; j += 2 * kBlock) {
+                s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+                s1 = fma(ld_cs(v + j + kBlock), ldg_x(x + ld_cs(ci + j + kBlock)), s1);
+            }
+            if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+            double s = block_sum(s0 + s1, red);
+            if (threadIdx.x == 0) y[r] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// V3 MERGE: merge-path split (IMB class; the GPU counterpart of balancing
+// the work of Table 2's dynamic scheduling).  The path merges the row ends
+// rowptr[1..N] with the nonzero indices; every warp gets the same number of
+// path items (rows + nonzeros), so a long row is shared by many warps and
+// many short rows by one.  Part p starts at diagonal p * ITEMS.
+
+__global__ void k_merge_coords(int64_t n_rows, int64_t nnz, const int* __restrict__ rp,
+                               int64_t items, int64_t n_parts, int32_t* __restrict__ mrow,
+                               int32_t* __restrict__ mnz)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > n_parts) return;
+    const int64_t total = n_rows + nnz;
+    const int64_t d = p * items < total ? p * items : total;
+    // number i of row ends among the first d path items: the path takes the
+    // end of row i before nonzero j exactly when rowptr[i+1] <= j.
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < n_rows ? d : n_rows;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)rp[mid + 1] <= d - mid - 1) lo = mid + 1; else hi = mid;
+    }
+    mrow[p] = (int32_t)lo;
+    mnz[p] = (int32_t)(d - lo);
+}
+
+constexpr int kMergeWarps = 4;
+
+template <int IPT>
+__global__ void __launch_bounds__(kMergeWarps * 32)
+k_merge(int64_t n_parts, const int* __restrict__ rp, const int* __restrict__ ci,
+        const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y,
+        const int32_t* __restrict__ mrow, const int32_t* __restrict__ mnz,
+        int32_t* __restrict__ carry_row, double* __restrict__ carry_val)
+{
+    constexpr int ITEMS = 32 * IPT;
+    __shared__ double s_prod[kMergeWarps][ITEMS];
+    __shared__ int s_end[kMergeWarps][ITEMS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kMergeWarps + w;
+    if (p >= n_parts) return;  // uniform per warp
+    const int r0 = mrow[p], r1 = mrow[p + 1];
+    const int n0 = mnz[p], n1 = mnz[p + 1];
+    const int nr = r1 - r0, nn = n1 - n0;
+    for (int k = lane; k < nn; k += 32)
+        s_prod[w][k] = ld_cs(v + n0 + k) * ldg_x(x + ld_cs(ci + n0 + k));
+    for (int k = lane; k < nr; k += 32) s_end[w][k] = rp[r0 + 1 + k];
+    __syncwarp();
+
+    const int total = nr + nn;
+    const int d = min(lane * IPT, total);
+    const int dend = min(d + IPT, total);
+    int lo = max(0, d - nn), hi = min(d, nr);
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (s_end[w][mid] <= n0 + d - mid - 1) lo = mid + 1; else hi = mid;
+    }
+    int i = lo, j = d - lo;
+    double run = 0.0, first_val = 0.0;
+    int first_row = -1;
+    for (int t = d; t < dend; ++t) {
+        if (i < nr && s_end[w][i] <= n0 + j) {
+            if (first_row < 0) { first_row = i; first_val = run; }
+            else y[r0 + i] = run;
+            run = 0.0;
+            ++i;
+        } else {
+            run += s_prod[w][j];
+            ++j;
+        }
+    }
+    // segmented inclusive scan over lanes: a lane that ended a row starts a
+    // new segment with its own trailing partial sum
+    double val = run;
+    int flag = first_row >= 0;
+    for (int o = 1; o < 32; o <<= 1) {
+        double vu = __shfl_up_sync(FULL_MASK, val, o);
+        int fu = __shfl_up_sync(FULL_MASK, flag, o);
+        if (lane >= o) {
+            if (!flag) val += vu;
+            flag |= fu;
+        }
+    }
+    double cin = __shfl_up_sync(FULL_MASK, val, 1);
+    if (lane == 0) cin = 0.0;
+    if (first_row >= 0) y[r0 + first_row] = first_val + cin;
+    if (lane == 31) { carry_row[p] = r1; carry_val[p] = val; }
+}
+
+// Adds each part's trailing partial sum to its row, summing the parts of one
+// row in part order (deterministic).  carry_row is non-decreasing.
+__global__ void k_merge_fixup(int64_t n_parts, int64_t n_rows, const int32_t* __restrict__ carry_row,
+                              const double* __restrict__ carry_val, double* __restrict__ y)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_parts) return;
+    const int r = carry_row[p];
+    if (r >= n_rows) return;
+    if (p > 0 && carry_row[p - 1] == r) return;
+    double s = 0.0;
+    for (int64_t q = p; q < n_parts && carry_row[q] == r; ++q) s += carry_val[q];
+    y[r] += s;
+}
+
+// ------------------------------------------------------------------------
+// V4 DYNAMIC: persistent warps take chunks of consecutive rows from a global
+// counter (the GPU form of OpenMP dynamic scheduling, Table 2, IMB class).
+// The last warp to run out of work resets the counters for the next launch.
+template <int T>
+__global__ void __launch_bounds__(kBlock)
+k_dynamic(int64_t n_rows, int chunk_rows, const int* __restrict__ rp, const int* __restrict__ ci,
+          const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y,
+          unsigned int* __restrict__ counter)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const int grp = lane / T;
+    const int64_t n_chunks = (n_rows + chunk_rows - 1) / chunk_rows;
+    const unsigned total_warps = gridDim.x * (kBlock / 32);
+    for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1u);
+        c = __shfl_sync(FULL_MASK, c, 0);
+        if ((int64_t)c >= n_chunks) break;
+        const int64_t rbeg = (int64_t)c * chunk_rows;
+        const int64_t rend = rbeg + chunk_rows < n_rows ? rbeg + chunk_rows : n_rows;
+        for (int64_t r0 = rbeg; r0 < rend; r0 += 32 / T) {
+            const int64_t row = r0 + grp;
+            int64_t b = 0, e = 0;
+            if (row < rend) { b = rp[row]; e = rp[row + 1]; }
+            double s0 = 0.0, s1 = 0.0;
+            int64_t j = b + sub;
+            for (; j + T < e; j += 2 * T) {
+                s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+                s1 = fma(ld_cs(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
+            }
+            if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+            double s = warp_sum(s0 + s1, T);
+            if (sub == 0 && row < rend) y[row] = s;
+        }
+    }
+    if (lane == 0) {
+        __threadfence();
+        unsigned done = atomicAdd(counter + 1, 1u);
+        if (done == total_warps - 1) {
+            counter[0] = 0u;
+            counter[1] = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// V5 LATENCY: for matrices bound by the latency of irregular x accesses (CML
+// class; Table 2 software prefetching of x).  Each lane first loads four
+// column indices, then issues the four gathers of x together, then the
+// values, so four misses are in flight per lane; x is read through the
+// non-coherent path and the launch marks x as persisting in L2.
+template <int T>
+__global__ void __launch_bounds__(kBlock)
+k_latency(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ ci,
+          const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t row = (int64_t)blockIdx.x * (kBlock / T) + threadIdx.x / T;
+    const int lane = threadIdx.x & (T - 1);
+    int64_t b = 0, e = 0;
+    if (row < n_rows) { b = rp[row]; e = rp[row + 1]; }
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t j = b + lane;
+    for (; j + 3 * T < e; j += 4 * T) {
+        const int c0 = ld_cs(ci + j), c1 = ld_cs(ci + j + T);
+        const int c2 = ld_cs(ci + j + 2 * T), c3 = ld_cs(ci + j + 3 * T);
+        const double x0 = ldg_x(x + c0), x1 = ldg_x(x + c1);
+        const double x2 = ldg_x(x + c2), x3 = ldg_x(x + c3);
+        s0 = fma(ld_cs(v + j), x0, s0);
+        s1 = fma(ld_cs(v + j + T), x1, s1);
+        s2 = fma(ld_cs(v + j + 2 * T), x2, s2);
+        s3 = fma(ld_cs(v + j + 3 * T), x3, s3);
+    }
+    for (; j < e; j += T) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+    double s = warp_sum((s0 + s1) + (s2 + s3), T);
+    if (lane == 0 && row < n_rows) y[row] = s;
+}
+
+// ------------------------------------------------------------------------
+// V6 COMPRESSED (MB class; Table 2 column-index compression): each row keeps
+// its first column in rowbase and its columns as 16-bit offsets from it;
+// rows spanning 65536 columns or more keep their 32-bit columns (rowbase -1)
+// and read them from the original colind.  Values are stored as FP64, FP32
+// or BF16; the accumulation is FP64.
+
+__global__ void k_compress_rows(int64_t n_rows, const int* __restrict__ rp,
+                                const int* __restrict__ ci, int32_t* __restrict__ rowbase,
+                                unsigned long long* __restrict__ n_wide)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    const int b = rp[i], e = rp[i + 1];
+    int base = 0;
+    if (e > b) {
+        const int first = ci[b], last = ci[e - 1];
+        if ((int64_t)last - first >= 65536) {
+            base = -1;
+            atomicAdd(n_wide, 1ull);
+        } else {
+            base = first;
+        }
+    }
+    rowbase[i] = base;
+}
+
+__global__ void k_compress_offsets(int64_t n_rows, const int* __restrict__ rp,
+                                   const int* __restrict__ ci, const int32_t* __restrict__ rowbase,
+                                   uint16_t* __restrict__ off)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const int b = rp[row], e = rp[row + 1];
+    const int base = rowbase[row];
+    for (int j = b + lane; j < e; j += 32)
+        off[j] = base < 0 ? (uint16_t)0 : (uint16_t)(ci[j] - base);
+}
+
+__global__ void k_cast_values(int64_t n, const double* __restrict__ v, int value_type,
+                              void* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (value_type == SPMV_VAL_F32)
+        static_cast<float*>(out)[i] = __double2float_rn(v[i]);
+    else
+        static_cast<__nv_bfloat16*>(out)[i] = __double2bfloat16(v[i]);
+}
+
+template <typename VT>
+__device__ __forceinline__ double load_val(const VT* p) { return (double)ld_cs(p); }
+template <>
+__device__ __forceinline__ double load_val<__nv_bfloat16>(const __nv_bfloat16* p) {
+    unsigned short bits = ld_cs(reinterpret_cast<const unsigned short*>(p));
+    return (double)__uint_as_float(((unsigned)bits) << 16);
+}
+
+template <int T, typename VT, bool ALL_WIDE>
+__global__ void __launch_bounds__(kBlock)
+k_compressed(int64_t n_rows, const int* __restrict__ rp, const int32_t* __restrict__ rowbase,
+             const uint16_t* __restrict__ off, const int* __restrict__ ci,
+             const VT* __restrict__ v, const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t row = (int64_t)blockIdx.x * (kBlock / T) + threadIdx.x / T;
+    const int lane = threadIdx.x & (T - 1);
+    int64_t b = 0, e = 0;
+    int base = -1;
+    if (row < n_rows) {
+        b = rp[row];
+        e = rp[row + 1];
+        if (!ALL_WIDE) base = rowbase[row];
+    }
+    double s0 = 0.0, s1 = 0.0;
+    int64_t j = b + lane;
+    if (ALL_WIDE || base < 0) {
+        for (; j + T < e; j += 2 * T) {
+            s0 = fma(load_val(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+            s1 = fma(load_val(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
+        }
+        if (j < e) s0 = fma(load_val(v + j), ldg_x(x + ld_cs(ci + j)), s0);
+    } else {
+        const double* xb = x + base;
+        for (; j + T < e; j += 2 * T) {
+            s0 = fma(load_val(v + j), ldg_x(xb + ld_cs(off + j)), s0);
+            s1 = fma(load_val(v + j + T), ldg_x(xb + ld_cs(off + j + T)), s1);
+        }
+        if (j < e) s0 = fma(load_val(v + j), ldg_x(xb + ld_cs(off + j)), s0);
+    }
+    double s = warp_sum(s0 + s1, T);
+    if (lane == 0 && row < n_rows) y[row] = s;
+}
+
+inline unsigned grid_for(int64_t threads) {
+    return (unsigned)((threads + kBlock - 1) / kBlock);
+}
+
+}  // namespace
+
+// ============================================================================
+// launchers
+
+cudaError_t launch_scalar(const spmv_csr_t& A, const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    k_scalar<<<grid_for(A.n_rows), kBlock, 0, s>>>(A.n_rows, A.rowptr, A.colind, A.val, x, y);
+    return cudaGetLastError();
+}
+
+#define SPMV_DISPATCH_T(T, KERNEL, GRID, SMEM, STREAM, ...)                       \
+    switch (T) {                                                                  \
+        case 1: KERNEL<1><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;    \
+        case 2: KERNEL<2><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;    \
+        case 4: KERNEL<4><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;    \
+        case 8: KERNEL<8><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;    \
+        case 16: KERNEL<16><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;  \
+        case 32: KERNEL<32><<<GRID, kBlock, SMEM, STREAM>>>(__VA_ARGS__); break;  \
+        default: return cudaErrorInvalidValue;                                    \
+    }
+
+cudaError_t launch_subwarp(const spmv_csr_t& A, int T, const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    const unsigned grid = grid_for(A.n_rows * (int64_t)T);
+    SPMV_DISPATCH_T(T, k_subwarp, grid, 0, s, A.n_rows, A.rowptr, A.colind, A.val, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_blocks(const spmv_csr_t& A, int64_t block_nnz, int64_t n_blocks,
+                              int32_t* blocks, cudaStream_t s)
+{
+    k_row_blocks<<<grid_for(n_blocks + 1), kBlock, 0, s>>>(A.n_rows, A.rowptr, block_nnz,
+                                                            n_blocks, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream(const spmv_csr_t& A, const int32_t* blocks, int64_t n_blocks,
+                          int block_nnz, const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    const int cap = 2 * block_nnz;
+    const size_t smem = (size_t)cap * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_stream<<<(unsigned)n_blocks, kBlock, smem, s>>>(A.rowptr, A.colind, A.val, x, y, blocks, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_coords(const spmv_csr_t& A, int items, int64_t n_parts, int32_t* mrow,
+                                int32_t* mnz, cudaStream_t s)
+{
+    k_merge_coords<<<grid_for(n_parts + 1), kBlock, 0, s>>>(A.n_rows, A.nnz, A.rowptr, items,
+                                                             n_parts, mrow, mnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const spmv_csr_t& A, int items, const int32_t* mrow, const int32_t* mnz,
+                         int64_t n_parts, int32_t* carry_row, double* carry_val,
+                         const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n_parts + kMergeWarps - 1) / kMergeWarps);
+    const int ipt = items / 32;
+#define SPMV_MERGE_CASE(K)                                                                   \
+    case K:                                                                                  \
+        k_merge<K><<<grid, kMergeWarps * 32, 0, s>>>(n_parts, A.rowptr, A.colind, A.val, x, y, \
+                                                     mrow, mnz, carry_row, carry_val);       \
+        break;
+    switch (ipt) {
+        SPMV_MERGE_CASE(1) SPMV_MERGE_CASE(2) SPMV_MERGE_CASE(4) SPMV_MERGE_CASE(6)
+        SPMV_MERGE_CASE(7) SPMV_MERGE_CASE(8) SPMV_MERGE_CASE(12) SPMV_MERGE_CASE(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SPMV_MERGE_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_merge_fixup<<<grid_for(n_parts), kBlock, 0, s>>>(n_parts, A.n_rows, carry_row, carry_val, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dynamic(const spmv_csr_t& A, int T, int chunk_rows, unsigned int* counter,
+                           int sm_count, const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e;
+    switch (T) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<1>, kBlock, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<2>, kBlock, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<4>, kBlock, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<8>, kBlock, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<16>, kBlock, 0); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<32>, kBlock, 0); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const unsigned grid = (unsigned)(sm_count * per_sm);
+    SPMV_DISPATCH_T(T, k_dynamic, grid, 0, s, A.n_rows, chunk_rows, A.rowptr, A.colind, A.val, x,
+                    y, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_latency(const spmv_csr_t& A, int T, const double* x, double* y,
+                           int l2_window_bytes, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_for(A.n_rows * (int64_t)T));
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    if (l2_window_bytes > 0) {
+        const size_t xbytes = (size_t)A.n_cols * sizeof(double);
+        const size_t win = xbytes < (size_t)l2_window_bytes ? xbytes : (size_t)l2_window_bytes;
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = const_cast<double*>(x);
+        attr[0].val.accessPolicyWindow.num_bytes = win;
+        attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.numAttrs = 1;
+    }
+    const int64_t n = A.n_rows;
+    switch (T) {
+        case 1: return cudaLaunchKernelEx(&cfg, k_latency<1>, n, A.rowptr, A.colind, A.val, x, y);
+        case 2: return cudaLaunchKernelEx(&cfg, k_latency<2>, n, A.rowptr, A.colind, A.val, x, y);
+        case 4: return cudaLaunchKernelEx(&cfg, k_latency<4>, n, A.rowptr, A.colind, A.val, x, y);
+        case 8: return cudaLaunchKernelEx(&cfg, k_latency<8>, n, A.rowptr, A.colind, A.val, x, y);
+        case 16: return cudaLaunchKernelEx(&cfg, k_latency<16>, n, A.rowptr, A.colind, A.val, x, y);
+        case 32: return cudaLaunchKernelEx(&cfg, k_latency<32>, n, A.rowptr, A.colind, A.val, x, y);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_compress(const spmv_csr_t& A, int32_t* rowbase, uint16_t* off16,
+                            unsigned long long* n_wide, int value_type, void* lowval,
+                            cudaStream_t s)
+{
+    if (A.n_rows > 0) {
+        k_compress_rows<<<grid_for(A.n_rows), kBlock, 0, s>>>(A.n_rows, A.rowptr, A.colind,
+                                                              rowbase, n_wide);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (off16) {
+            k_compress_offsets<<<grid_for(A.n_rows * 32), kBlock, 0, s>>>(A.n_rows, A.rowptr,
+                                                                           A.colind, rowbase, off16);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (lowval && A.nnz > 0) {
+        k_cast_values<<<grid_for(A.nnz), kBlock, 0, s>>>(A.nnz, A.val, value_type, lowval);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_compressed(const spmv_csr_t& A, int T, int value_type, const int32_t* rowbase,
+                              const uint16_t* off16, const void* lowval, bool all_wide,
+                              const double* x, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    const unsigned grid = grid_for(A.n_rows * (int64_t)T);
+    const int64_t n = A.n_rows;
+#define SPMV_CMP_LAUNCH(TT, VT, AW)                                                           \
+    k_compressed<TT, VT, AW><<<grid, kBlock, 0, s>>>(n, A.rowptr, rowbase, off16, A.colind,   \
+                                                     static_cast<const VT*>(vp), x, y)
+#define SPMV_CMP_T(VT, AW)                                   \
+    switch (T) {                                             \
+        case 1: SPMV_CMP_LAUNCH(1, VT, AW); break;           \
+        case 2: SPMV_CMP_LAUNCH(2, VT, AW); break;           \
+        case 4: SPMV_CMP_LAUNCH(4, VT, AW); break;           \
+        case 8: SPMV_CMP_LAUNCH(8, VT, AW); break;           \
+        case 16: SPMV_CMP_LAUNCH(16, VT, AW); break;         \
+        case 32: SPMV_CMP_LAUNCH(32, VT, AW); break;         \
+        default: return cudaErrorInvalidValue;               \
+    }
+    const void* vp = value_type == SPMV_VAL_F64 ? static_cast<const void*>(A.val) : lowval;
+    if (value_type == SPMV_VAL_F64) {
+        if (all_wide) { SPMV_CMP_T(double, true) } else { SPMV_CMP_T(double, false) }
+    } else if (value_type == SPMV_VAL_F32) {
+        if (all_wide) { SPMV_CMP_T(float, true) } else { SPMV_CMP_T(float, false) }
+    } else {
+        if (all_wide) { SPMV_CMP_T(__nv_bfloat16, true) } else { SPMV_CMP_T(__nv_bfloat16, false) }
+    }
+#undef SPMV_CMP_T
+#undef SPMV_CMP_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace spmvlib

@@ -1,0 +1,166 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every function
+include/spmv.h declares, its structures have the header's layout, its
+host-only selection logic agrees bit for bit with the oracle, and calls that
+need the GPU fail loudly instead of falling back to the CPU."""
+import ctypes as C
+import json
+import math
+import os
+import re
+import subprocess
+
+import pytest
+import torch
+
+import oracle
+import paper_1511_02494_gb300 as sp
+from paper_1511_02494_gb300 import _abi
+from paper_1511_02494_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return sp.lib()
+
+
+def _declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s*(spmv\w*)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", sp.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)  # resolvable through dlsym
+
+
+def test_python_binding_declares_every_function(lib):
+    names = _declared_functions()
+    py = {n for n in dir(sp) if n.startswith("spmv")}
+    assert set(names) - {"spmv_status_str"} <= py | {"spmv_status_str"}
+
+
+_STRUCTS = {
+    "spmv_csr_t": _abi.CSR, "spmv_features_t": _abi.Features, "spmv_profile_t": _abi.Profile,
+    "spmv_thresholds_t": _abi.Thresholds, "spmv_choice_t": _abi.Choice,
+    "spmv_prepared_info_t": _abi.PreparedInfo,
+}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Compile a probe against the header with gcc and compare sizeof and
+    every field offset with the ctypes mirror."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "spmv.h"', 'int main(void){']
+    for cname, cls in _STRUCTS.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for cname, cls in _STRUCTS.items():
+        assert got[(cname, "sizeof")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_status_strings(lib):
+    for code, name in _abi.STATUS_NAMES.items():
+        assert sp.spmv_status_str(code) == name
+
+
+def test_profile_rule_bit_exact_with_oracle(lib, golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "profile_rule_cases.json")))
+    th = _abi.Thresholds(*d["tau"])
+    for c in d["cases"]:
+        p = _abi.Profile()
+        p.s_noxmiss, p.s_inflate, p.s_balance = c["s"]
+        got = sp.spmv_classify_profile(p, th)
+        assert got == oracle.profile_class(*c["s"], tau=tuple(d["tau"]))
+        assert _abi.CLASSES[got] == c["class"]
+        ch = sp.spmv_select(profile=p, thresholds=th)
+        assert ch.cls == got and ch.variant == oracle.class_variant(got) and ch.source == 1
+
+
+def test_profile_rule_random_profiles_bit_exact(lib):
+    g = torch.Generator().manual_seed(0)
+    s = 0.5 + 2.0 * torch.rand((2000, 3), generator=g, dtype=torch.float64)
+    s[::7, 1] = s[::7, 0]  # force ties
+    t = spmvt = sp.spmv_default_thresholds()
+    tau = (t.tau_noxmiss, t.tau_inflate, t.tau_balance)
+    for row in s.tolist():
+        p = _abi.Profile()
+        p.s_noxmiss, p.s_inflate, p.s_balance = row
+        assert sp.spmv_classify_profile(p) == oracle.profile_class(*row, tau=tau)
+
+
+def test_class_variant_table(lib):
+    assert [sp.spmv_class_variant(c) for c in range(4)] == [oracle.class_variant(c) for c in range(4)]
+    assert sp.spmv_class_variant(9) == -1
+
+
+@pytest.mark.parametrize("bad", [float("nan"), 0.0, -1.0, float("inf")])
+def test_select_rejects_bad_profiles(lib, bad):
+    p = _abi.Profile()
+    p.s_noxmiss, p.s_inflate, p.s_balance = 1.0, bad, 1.0
+    with pytest.raises(sp.SpmvError) as e:
+        sp.spmv_select(profile=p)
+    assert e.value.status == 1
+
+
+def test_select_without_profile_or_model_is_model_error(lib):
+    with pytest.raises(sp.SpmvError) as e:
+        sp.spmv_select()
+    assert e.value.status == 7
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks behaviour without a GPU")
+def test_gpu_calls_fail_loudly_without_gpu(lib):
+    """No CPU fallback: without a device the library reports SPMV_ERR_CUDA."""
+    desc = _abi.CSR(1, 1, 1, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16))
+    out = _abi.Features()
+    st = lib.spmv_features(C.byref(desc), 128, C.byref(out), None)
+    assert st == 5
+    assert "cuda" in lib.spmv_last_error().decode().lower()
+    h = C.c_void_p()
+    ch = sp.make_choice("scalar")
+    assert lib.spmv_prepare(C.byref(desc), C.byref(ch), 1, C.byref(h), None) == 5
+    assert not h.value
+
+
+def test_invalid_arguments_rejected_before_device_use(lib):
+    h = C.c_void_p()
+    ch = sp.make_choice("scalar")
+    assert lib.spmv_prepare(None, C.byref(ch), 0, C.byref(h), None) == 1
+    desc = _abi.CSR(-1, 4, 0, C.c_void_p(16), None, None)
+    assert lib.spmv_prepare(C.byref(desc), C.byref(ch), 0, C.byref(h), None) == 1
+    desc = _abi.CSR(4, 4, 4, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16))
+    bad = sp.make_choice("subwarp", threads_per_row=3)
+    assert lib.spmv_prepare(C.byref(desc), C.byref(bad), 0, C.byref(h), None) == 1
+    bad = sp.make_choice("stream", value_type=sp.VAL_BF16)
+    assert lib.spmv_prepare(C.byref(desc), C.byref(bad), 0, C.byref(h), None) == 3
+    bad = sp.make_choice("merge", items_per_warp=100)
+    assert lib.spmv_prepare(C.byref(desc), C.byref(bad), 0, C.byref(h), None) == 1

@@ -1,0 +1,332 @@
+"""GPU parity of the CUDA library against the CPU oracle, through the C ABI.
+
+Floating point: |y_gpu - y_ref| <= 1e-12 * sum_j |a_ij x_j| per row (rows whose
+scale is 0 must be exactly 0); integer-valued, identity and permutation
+inputs must match bit for bit.  Integer work (features, prepared arrays,
+selections) must be bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1511_02494_gb300 as sp
+import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1511_02494_gb300.build import build
+    build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sp.lib()
+
+
+def _assert_close(y_gpu, A, x, rows=None, rtol=RTOL):
+    y_ref, scale = oracle.spmv_ref(A, x, rows)
+    y = y_gpu.detach().cpu().numpy()
+    if rows is not None:
+        y = y[np.asarray(rows)]
+    err = np.abs(y - y_ref)
+    bad = err > rtol * scale
+    assert not bad.any(), (f"{int(bad.sum())} rows off; worst row {int(np.argmax(err - rtol * scale))}"
+                           f" err {err.max():.3e}")
+    assert np.all(y[scale == 0] == 0.0)
+
+
+def _run(A, choice, x=None, reps=1):
+    dA = sp.DeviceCSR.from_host(A)
+    if x is None:
+        x = synth.uniform_vector(A.n_cols, 1)
+    dx = x.cuda()
+    dy = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+    P = sp.spmv_prepare(dA, choice)
+    outs = []
+    for _ in range(reps):
+        dy.fill_(float("nan"))
+        sp.spmv(P, dx, dy)
+        torch.cuda.synchronize()
+        outs.append(dy.clone())
+    P.free()
+    return outs if reps > 1 else outs[0], x
+
+
+CHOICES = [
+    ("scalar", {}),
+    ("subwarp", {"threads_per_row": 1}), ("subwarp", {"threads_per_row": 2}),
+    ("subwarp", {"threads_per_row": 4}), ("subwarp", {"threads_per_row": 8}),
+    ("subwarp", {"threads_per_row": 16}), ("subwarp", {"threads_per_row": 32}),
+    ("subwarp", {}),
+    ("stream", {"block_nnz": 64}), ("stream", {"block_nnz": 256}), ("stream", {}),
+    ("stream", {"block_nnz": 8192}),
+    ("merge", {"items_per_warp": 32}), ("merge", {"items_per_warp": 224}), ("merge", {}),
+    ("merge", {"items_per_warp": 512}),
+    ("dynamic", {"threads_per_row": 1}), ("dynamic", {"threads_per_row": 8}), ("dynamic", {}),
+    ("dynamic", {"threads_per_row": 32, "block_nnz": 1}),
+    ("latency", {"threads_per_row": 1}), ("latency", {"threads_per_row": 4}), ("latency", {}),
+    ("latency", {"threads_per_row": 32}),
+    ("compressed", {}), ("compressed", {"threads_per_row": 1}),
+    ("compressed", {"threads_per_row": 32}),
+]
+
+
+def _matrices():
+    yield "laplacian64", synth.laplacian_2d_5pt(64, 64)
+    yield "random_empty_rows", synth.random_csr(1000, 700, 40, seed=3, empty_frac=0.3)
+    yield "zipf_long_rows", synth.zipf_rows(5000, 5000, 1.5, 3000, seed=1)
+    yield "short_rows", synth.short_rows(3001, 8, seed=2)
+    yield "stencil27_n10", synth.stencil_27pt(10, seed=4)
+    yield "one_dense_row", synth.dense_to_csr(torch.cat([torch.rand(1, 9000, dtype=torch.float64) + 0.1,
+                                                         torch.zeros(3, 9000, dtype=torch.float64)]))
+    yield "rectangular_wide", synth.random_csr(300, 200_000, 50, seed=5)
+    yield "rectangular_tall", synth.random_csr(5000, 17, 9, seed=6)
+    yield "single_row", synth.random_csr(1, 50, 50, seed=7, empty_frac=0.0)
+    yield "all_empty", synth.random_csr(777, 100, 0, seed=8)
+
+
+MATS = list(_matrices())
+
+
+@pytest.mark.parametrize("variant,params", CHOICES, ids=[f"{v}{p}" for v, p in CHOICES])
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_spmv_variant_parity(variant, params, name, A):
+    y, x = _run(A, sp.make_choice(variant, **params))
+    _assert_close(y, A, x)
+
+
+@pytest.mark.parametrize("variant,params", CHOICES, ids=[f"{v}{p}" for v, p in CHOICES])
+def test_spmv_bit_exact_on_integer_inputs(variant, params):
+    g = np.random.default_rng(0)
+    D = g.integers(-7, 8, size=(600, 450)).astype(np.float64)
+    D[g.random(D.shape) < 0.9] = 0.0
+    D[5] = 0.0
+    A = synth.dense_to_csr(torch.from_numpy(D))
+    x = torch.from_numpy(g.integers(-20, 21, 450).astype(np.float64))
+    y, _ = _run(A, sp.make_choice(variant, **params), x)
+    assert np.array_equal(y.cpu().numpy(), oracle.spmv(A, x))
+
+
+@pytest.mark.parametrize("variant", sp.VARIANTS)
+def test_identity_and_permutation_bit_exact(variant):
+    n = 4099
+    x = synth.uniform_vector(n, 11)
+    I = synth.HostCSR(n, n, torch.arange(n + 1, dtype=torch.int32),
+                      torch.arange(n, dtype=torch.int32), torch.ones(n, dtype=torch.float64))
+    y, _ = _run(I, sp.make_choice(variant), x)
+    assert torch.equal(y.cpu(), x)
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(2))
+    P = synth.HostCSR(n, n, torch.arange(n + 1, dtype=torch.int32),
+                      perm.to(torch.int32), torch.ones(n, dtype=torch.float64))
+    y, _ = _run(P, sp.make_choice(variant), x)
+    assert torch.equal(y.cpu(), x[perm])
+
+
+@pytest.mark.parametrize("variant", ["dynamic", "merge", "stream", "latency"])
+def test_repeated_launches_identical(variant):
+    """Back-to-back launches (counter reset, carry reuse) give the same y."""
+    A = synth.zipf_rows(20000, 20000, 1.6, 5000, seed=9)
+    outs, x = _run(A, sp.make_choice(variant), reps=4)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    _assert_close(outs[0], A, x)
+
+
+def test_merge_long_row_spans_many_parts():
+    A = synth.zipf_rows(3000, 60000, 1.3, 40000, seed=10)
+    y, x = _run(A, sp.make_choice("merge", items_per_warp=32))
+    _assert_close(y, A, x)
+
+
+def test_empty_matrix_all_variants():
+    A = synth.random_csr(0, 10, 3)
+    dA = sp.DeviceCSR.from_host(A)
+    for v in sp.VARIANTS:
+        P = sp.spmv_prepare(dA, sp.make_choice(v))
+        sp.spmv(P, torch.zeros(10, dtype=torch.float64, device="cuda"),
+                torch.zeros(0, dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        P.free()
+
+
+# ----------------------------------------------------------------- features
+def _features_match(A, line_bytes=128):
+    dA = sp.DeviceCSR.from_host(A)
+    g = sp.spmv_features(dA, line_bytes).as_dict()
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    o = oracle.features(A, line_bytes=line_bytes, l2_bytes=l2)
+    for k, v in o.items():
+        if k == "vec":
+            assert np.array_equal(np.array(g["vec"], np.float32), v), (k, g["vec"], v)
+        else:
+            assert g[k] == v, (k, g[k], v)
+
+
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_features_bit_exact(name, A):
+    _features_match(A, 128)
+    _features_match(A, 64)
+
+
+def test_features_bit_exact_config1_laplacian():
+    A = synth.laplacian_2d_5pt(64, 64)
+    _features_match(A)
+    f = sp.spmv_features(sp.DeviceCSR.from_host(A)).as_dict()
+    assert f["misses_sum"] == 12160 and f["nnz_sumsq"] == 100104
+
+
+def test_features_empty_matrix():
+    _features_match(synth.random_csr(0, 0, 0))
+
+
+def _bad_csr(kind):
+    rp = torch.tensor([0, 2, 3, 5], dtype=torch.int32)
+    ci = torch.tensor([0, 2, 1, 0, 3], dtype=torch.int32)
+    if kind == "rowptr0":
+        rp = torch.tensor([1, 2, 3, 5], dtype=torch.int32)
+    elif kind == "decreasing":
+        rp = torch.tensor([0, 3, 2, 5], dtype=torch.int32)
+    elif kind == "beyond_nnz":
+        rp = torch.tensor([0, 2, 9, 5], dtype=torch.int32)
+    elif kind == "col_range":
+        ci = torch.tensor([0, 2, 1, 0, 4], dtype=torch.int32)
+    elif kind == "negative_col":
+        ci = torch.tensor([0, 2, -1, 0, 3], dtype=torch.int32)
+    elif kind == "unsorted":
+        ci = torch.tensor([2, 0, 1, 0, 3], dtype=torch.int32)
+    elif kind == "duplicate":
+        ci = torch.tensor([0, 2, 1, 3, 3], dtype=torch.int32)
+    return synth.HostCSR(3, 4, rp, ci, torch.ones(5, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("kind", ["rowptr0", "decreasing", "beyond_nnz", "col_range",
+                                  "negative_col", "unsorted", "duplicate"])
+def test_invalid_csr_rejected(kind):
+    dA = sp.DeviceCSR.from_host(_bad_csr(kind))
+    for call in (lambda: sp.spmv_validate(dA), lambda: sp.spmv_features(dA),
+                 lambda: sp.spmv_prepare(dA, sp.make_choice("merge"))):
+        with pytest.raises(sp.SpmvError) as e:
+            call()
+        assert e.value.status == 2
+    sp.spmv_validate(sp.DeviceCSR.from_host(_bad_csr("ok")))
+
+
+# ----------------------------------------------------------------- prepared arrays
+def _export(P, which, n, dtype):
+    t = torch.empty(n, dtype=dtype)
+    sp.spmv_prepared_export(P, which, t)
+    return t.numpy()
+
+
+@pytest.mark.parametrize("name,A", MATS[:6], ids=[m[0] for m in MATS[:6]])
+def test_prepared_arrays_bit_exact(name, A):
+    dA = sp.DeviceCSR.from_host(A)
+    for B in (64, 1024):
+        P = sp.spmv_prepare(dA, sp.make_choice("stream", block_nnz=B))
+        n = P.info().n_blocks
+        assert np.array_equal(_export(P, sp.EXPORT_ROW_BLOCKS, n + 1, torch.int32),
+                              oracle.row_blocks(A, B))
+    for items in (32, 256, 512):
+        P = sp.spmv_prepare(dA, sp.make_choice("merge", items_per_warp=items))
+        n = P.info().n_blocks
+        rs, ns = oracle.merge_path(A, items)
+        assert np.array_equal(_export(P, sp.EXPORT_MERGE_ROWS, n + 1, torch.int32), rs)
+        assert np.array_equal(_export(P, sp.EXPORT_MERGE_NZ, n + 1, torch.int32), ns)
+    P = sp.spmv_prepare(dA, sp.make_choice("compressed"))
+    base, off, wide = oracle.compress_u16(A)
+    assert P.info().n_wide_rows == wide
+    assert np.array_equal(_export(P, sp.EXPORT_ROWBASE, A.n_rows, torch.int32), base)
+    if wide < A.n_rows and A.nnz:
+        got = _export(P, sp.EXPORT_OFFSETS, A.nnz, torch.int16).view(np.uint16)
+        assert np.array_equal(got, off)
+
+
+def test_compressed_value_rounding_bit_exact():
+    A = synth.random_csr(2000, 3000, 30, seed=12)
+    # include values that straddle bfloat16 ties
+    A.val = torch.from_numpy(np.random.default_rng(1).standard_normal(A.nnz) * 3.0)
+    A.val[:4] = torch.tensor([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -40, 2.0 ** -134],
+                             dtype=torch.float64)
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=sp.VAL_BF16))
+    got = _export(P, sp.EXPORT_VALUES, A.nnz, torch.int16).view(np.uint16)
+    assert np.array_equal(got, oracle.round_bf16(A.val))
+    P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=sp.VAL_F32))
+    got = _export(P, sp.EXPORT_VALUES, A.nnz, torch.float32)
+    assert np.array_equal(got, oracle.round_f32(A.val))
+
+
+@pytest.mark.parametrize("vt", [sp.VAL_F32, sp.VAL_BF16])
+@pytest.mark.parametrize("name,A", [MATS[0], MATS[2], MATS[6]], ids=["laplacian", "zipf", "wide"])
+def test_compressed_low_precision_parity(vt, name, A):
+    lowval = oracle.round_f32(A.val) if vt == sp.VAL_F32 else oracle.round_bf16(A.val)
+    y, x = _run(A, sp.make_choice("compressed", value_type=vt))
+    ref = oracle.spmv_lowp(A, x, 1 if vt == sp.VAL_F32 else 2, lowval)
+    _, scale = oracle.spmv_ref(A, x)
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= RTOL * scale * 1.01)
+
+
+# ----------------------------------------------------------------- profile + select
+def test_profile_runs_and_selection_consistent():
+    A = synth.zipf_rows(200_000, 200_000, 1.5, 50_000, seed=3)
+    dA = sp.DeviceCSR.from_host(A)
+    x = synth.uniform_vector(A.n_cols, 0).cuda()
+    p = sp.spmv_profile(dA, x, reps=3)
+    d = p.as_dict()
+    for k in ("t_base_ms", "t_noxmiss_ms", "t_inflate_ms", "t_span_ms", "t_worker_mean_ms"):
+        assert d[k] > 0 and np.isfinite(d[k]), k
+    assert d["s_noxmiss"] == d["t_base_ms"] / d["t_noxmiss_ms"]
+    assert d["s_inflate"] == d["t_inflate_ms"] / d["t_base_ms"]
+    assert d["t_span_ms"] >= d["t_worker_mean_ms"]
+    ch = sp.spmv_select(profile=p)
+    t = sp.spmv_default_thresholds()
+    cls = oracle.profile_class(d["s_noxmiss"], d["s_inflate"], d["s_balance"],
+                               tau=(t.tau_noxmiss, t.tau_inflate, t.tau_balance))
+    assert ch.cls == cls and ch.variant == oracle.class_variant(cls)
+    # one giant row among short ones: the balance probe must see the imbalance
+    assert d["s_balance"] > 2.0
+
+
+def test_spmv_host_end_to_end():
+    A = synth.stencil_27pt(12, seed=1)
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("stream"))
+    x = synth.uniform_vector(A.n_cols, 5).pin_memory()
+    y = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        sp.spmv_host(P, x, y)
+        _assert_close(y, A, x)
+
+
+# ----------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def four_class():
+    return synth.four_class_set()
+
+
+def _sample_rows(A, k=3000, seed=0):
+    g = np.random.default_rng(seed)
+    lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
+    rows = np.concatenate([[0, A.n_rows - 1, int(np.argmax(lens))], g.integers(0, A.n_rows, k)])
+    return np.unique(rows)
+
+
+FULL_CHOICES = [("scalar", {}), ("subwarp", {}), ("stream", {}), ("merge", {}), ("dynamic", {}),
+                ("latency", {}), ("compressed", {})]
+
+
+@pytest.mark.parametrize("variant,params", FULL_CHOICES, ids=[v for v, _ in FULL_CHOICES])
+def test_full_size_sampled_parity(four_class, variant, params):
+    """The four-class matrices at full size (2.1M-8.4M rows, 17M-67M nonzeros)
+    in the launch configuration the benchmark times; rows sampled."""
+    for A in four_class:
+        y, x = _run(A, sp.make_choice(variant, **params))
+        _assert_close(y, A, x, rows=_sample_rows(A))
+
+
+def test_full_size_features_bit_exact(four_class):
+    for A in four_class:
+        _features_match(A)
