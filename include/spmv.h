@@ -51,15 +51,15 @@ typedef enum {
 } spmv_status;
 
 /* SpMV variants.  The class -> variant map (the GPU counterpart of Table 2,
- * Section 3.3) is CML -> LATENCY, MB -> COMPRESSED, IMB -> MERGE,
- * CMP -> STREAM.  SCALAR is the unoptimized CSR kernel (one thread per row,
+ * Section 3.3) is CML -> LATENCY, MB -> COMPRESSED, IMB -> DYNAMIC,
+ * CMP -> SUBWARP.  SCALAR is the unoptimized CSR kernel (one thread per row,
  * Algorithm 1 as written) against which speedups are reported. */
 typedef enum {
     SPMV_V0_SCALAR = 0,     /* one thread per row                                */
     SPMV_V1_SUBWARP = 1,    /* T lanes per row (T = 1..32), shuffle reduction    */
-    SPMV_V2_STREAM = 2,     /* row blocks staged through shared memory           */
-    SPMV_V3_MERGE = 3,      /* merge-path split of rows + nonzeros per warp      */
-    SPMV_V4_DYNAMIC = 4,    /* persistent warps taking row chunks from a counter */
+    SPMV_V2_STREAM = 2,     /* windows of B nonzeros staged through shared memory */
+    SPMV_V3_MERGE = 3,      /* merge-path split of rows + nonzeros per CTA tile  */
+    SPMV_V4_DYNAMIC = 4,    /* rows tiered by length, long rows split, dynamic queue */
     SPMV_V5_LATENCY = 5,    /* gathers of x issued ahead, x kept in L2           */
     SPMV_V6_COMPRESSED = 6, /* 16-bit column offsets, FP64/FP32/BF16 values      */
     SPMV_NUM_VARIANTS = 7
@@ -141,9 +141,19 @@ typedef struct {
 } spmv_thresholds_t;
 
 /* A variant and its launch parameters.  Zero parameters mean "choose".
- *   threads_per_row : SUBWARP / LATENCY / COMPRESSED lanes per row (1..32, power of 2)
- *   block_nnz       : STREAM nonzeros per row-block window (64..8192, power of 2)
- *   items_per_warp  : MERGE merge-path items per warp (32 * k, k = 1..16)
+ *   threads_per_row : SUBWARP / LATENCY / COMPRESSED / DYNAMIC (short rows) lanes
+ *                     per row (1..32, power of 2)
+ *   block_nnz       : STREAM nonzeros per window (64..8192, power of 2; default
+ *                     2048).  With 1024 or 2048 and 16-byte-aligned arrays the
+ *                     pipelined bulk-copy kernel runs; otherwise a kernel that
+ *                     stages each row block with plain loads
+ *   block_nnz       : MERGE merge-path items (row ends + nonzeros) per CTA tile of
+ *                     the pipelined kernel, 1024, 1536 or 2048 (default 2048)
+ *   items_per_warp  : MERGE items per warp of the warp-level kernel used instead
+ *                     when rowptr, colind or val is not 16-byte aligned
+ *                     (32 k, k in {1, 2, 4, 6, 7, 8, 12, 16})
+ *   block_nnz       : DYNAMIC nonzeros per segment of a long row (power of two,
+ *                     256..2^20; default 2048)
  *   value_type      : COMPRESSED value storage (spmv_value_type)
  * Filled by spmv_select: cls (or -1), margin (model logit gap, or 0),
  * used_fallback (1 when the model deferred to the profile rule), source
@@ -168,10 +178,12 @@ typedef struct spmv_prepared spmv_prepared_t;
 typedef struct {
     int32_t variant, threads_per_row, block_nnz, items_per_warp, value_type;
     int64_t n_rows, n_cols, nnz;
-    int64_t n_blocks;      /* STREAM row blocks / MERGE parts / DYNAMIC chunks */
+    int64_t n_blocks;      /* STREAM windows / MERGE tiles / DYNAMIC work items */
     int64_t n_wide_rows;   /* COMPRESSED rows that kept 32-bit columns          */
     int64_t owned_bytes;   /* device bytes owned by the object                  */
     int64_t min_bytes;     /* minimum traffic of one spmv() with this format    */
+    int32_t tile_items;    /* MERGE: merge-path items per tile as prepared      */
+    int32_t bulk_copy;     /* 1 when the pipelined bulk-copy kernel is used     */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */
@@ -254,6 +266,11 @@ spmv_status spmv_prepared_info(const spmv_prepared_t *P, spmv_prepared_info_t *i
  * `bytes` bytes (must equal the array's size).  Synchronizes `stream`. */
 spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *dst,
                                  int64_t bytes, spmv_stream_t stream);
+
+/* SPMV_ERR_TIMEOUT when a bounded device-side wait of an earlier spmv() on P
+ * gave up (that call's y is then incomplete), else SPMV_OK; clears the flag.
+ * Synchronizes `stream`. */
+spmv_status spmv_prepared_status(const spmv_prepared_t *P, spmv_stream_t stream);
 
 /* Releases everything P owns (device sync first).  NULL is ignored. */
 void spmv_prepared_free(spmv_prepared_t *P);

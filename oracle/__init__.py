@@ -173,7 +173,7 @@ def features(A, line_bytes: int = 128, l2_bytes: int = 0) -> dict:
 CML, MB, IMB, CMP = 0, 1, 2, 3
 
 
-def profile_class(s_noxmiss, s_inflate, s_balance, tau=(1.40, 1.15, 1.25)) -> int:
+def profile_class(s_noxmiss, s_inflate, s_balance, tau=(1.15, 1.25, 3.0)) -> int:
     """Section 3.2.1 profiling-based classification rule (readings O9-O12)."""
     return int(_load().orc_profile_class(s_noxmiss, s_inflate, s_balance, *tau))
 

@@ -271,11 +271,11 @@ int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
 
 /* Table 2 analogue on the GPU: class -> variant id.  Variant ids:
  * 0 scalar, 1 sub-warp, 2 stream, 3 merge-path, 4 dynamic, 5 latency,
- * 6 compressed.  CML -> latency, MB -> compressed, IMB -> merge-path,
- * CMP -> stream.                                                            */
+ * 6 compressed.  CML -> latency, MB -> compressed, IMB -> dynamic,
+ * CMP -> sub-warp.                                                          */
 int32_t orc_class_variant(int32_t cls)
 {
-    static const int32_t map[4] = {5, 6, 3, 2};
+    static const int32_t map[4] = {5, 6, 4, 1};
     return (cls >= 0 && cls < 4) ? map[cls] : -1;
 }
 

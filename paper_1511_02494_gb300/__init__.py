@@ -201,5 +201,11 @@ def spmv_prepared_export(P: Prepared, which: int, out_tensor, stream=None) -> No
     _check(lib().spmv_prepared_export(P.handle, which, _ptr(out_tensor), nbytes, _stream(stream)))
 
 
+def spmv_prepared_status(P: Prepared, stream=None) -> None:
+    """Raises SpmvError(SPMV_ERR_TIMEOUT) if a bounded device wait of an
+    earlier spmv on P gave up."""
+    _check(lib().spmv_prepared_status(P.handle, _stream(stream)))
+
+
 def spmv_prepared_free(P: Prepared) -> None:
     P.free()

@@ -69,7 +69,8 @@ class PreparedInfo(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("variant", "threads_per_row", "block_nnz",
                                          "items_per_warp", "value_type")] + \
         [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_blocks", "n_wide_rows",
-                                  "owned_bytes", "min_bytes")]
+                                  "owned_bytes", "min_bytes")] + \
+        [("tile_items", C.c_int32), ("bulk_copy", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +95,7 @@ def declare(lib):
         "spmv_host": (I32, [P, P, P, P]),
         "spmv_prepared_info": (I32, [P, C.POINTER(PreparedInfo)]),
         "spmv_prepared_export": (I32, [P, I32, P, I64, P]),
+        "spmv_prepared_status": (I32, [P, P]),
         "spmv_prepared_free": (None, [P]),
     }
     for name, (res, args) in sig.items():

@@ -43,6 +43,17 @@ spmv_status check_csr_args(const spmv_csr_t* A);
 // ---- the prepared object ----------------------------------------------------------
 }  // namespace spmvlib
 
+// DYNAMIC variant plan (dynamic.cu)
+struct DynPlan {
+    int seg = 0, lim_s = 0, chunk_rows = 0;
+    int n_m1 = 0, n_m2 = 0, n_long = 0, n_seg = 0;
+    int* m1 = nullptr;       // rows with lim_s < len <= 64
+    int* m2 = nullptr;       // rows with 64 < len <= seg
+    int* lrow = nullptr;     // rows longer than seg
+    int* seg_off = nullptr;  // first segment of each long row, [n_long + 1]
+    double* partial = nullptr;  // one partial sum per segment
+};
+
 struct spmv_prepared {
     spmv_csr_t A{};
     spmv_choice_t c{};
@@ -62,6 +73,10 @@ struct spmv_prepared {
     int64_t owned_bytes = 0;
     int sm_count = 0;
     int l2_window_bytes = 0;       // LATENCY: bytes of x kept persisting in L2
+    int tile_items = 0;            // MERGE: path items per tile (CTA or warp)
+    bool bulk = false;             // STREAM / MERGE: pipelined bulk-copy kernel in use
+    unsigned* status = nullptr;    // device status word (bounded-wait timeouts)
+    DynPlan dyn;
 };
 
 namespace spmvlib {
@@ -79,8 +94,17 @@ cudaError_t launch_merge_coords(const spmv_csr_t& A, int items, int64_t n_parts,
 cudaError_t launch_merge(const spmv_csr_t& A, int items, const int32_t* mrow,
                          const int32_t* mnz, int64_t n_parts, int32_t* carry_row,
                          double* carry_val, const double* x, double* y, cudaStream_t s);
-cudaError_t launch_dynamic(const spmv_csr_t& A, int T, int chunk_rows, unsigned int* counter,
-                           int sm_count, const double* x, double* y, cudaStream_t s);
+bool tma_aligned(const spmv_csr_t& A);
+cudaError_t launch_merge_tma(const spmv_csr_t& A, int tile_items, const int32_t* mrow,
+                             const int32_t* mnz, int64_t n_tiles, int32_t* carry_row,
+                             double* carry_val, unsigned* status, int sm_count, const double* x,
+                             double* y, cudaStream_t s);
+cudaError_t launch_window(const spmv_csr_t& A, int block_nnz, const int32_t* blocks, int64_t n_win,
+                          int32_t* carry_row, double* carry_val, unsigned* status, int sm_count,
+                          const double* x, double* y, cudaStream_t s);
+spmv_status prepared_alloc(spmv_prepared* P, void** p, int64_t bytes);
+spmv_status dyn_prepare(spmv_prepared* P, cudaStream_t s);
+cudaError_t launch_dyn(const spmv_prepared* P, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_latency(const spmv_csr_t& A, int T, const double* x, double* y,
                            int l2_window_bytes, cudaStream_t s);
 cudaError_t launch_compress(const spmv_csr_t& A, int32_t* rowbase, uint16_t* off16,

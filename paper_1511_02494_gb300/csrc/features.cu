@@ -12,8 +12,6 @@
 // The doubles of Table 1 are derived on the host from these integers.
 #include <math.h>
 
-#include <vector>
-
 #include "common.cuh"
 
 namespace spmvlib {
@@ -65,18 +63,26 @@ __device__ __forceinline__ u64 warp_max_u64(u64 v) {
     return v;
 }
 
-// Sub-warp of T lanes per row; a grid-stride loop over row groups.
+constexpr int kFields = 16;  // FeatAcc words reduced per block (err excluded)
+
+// Sub-warp of T lanes per row; a grid-stride loop over row groups.  Each lane
+// examines elements j = b + lane + k T, four per pass, comparing each column
+// with its predecessor in the row.
 template <int T, bool FEATURES>
 __global__ void __launch_bounds__(256)
 k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restrict__ rp,
                const int* __restrict__ ci, int64_t line_bytes, FeatAcc* __restrict__ acc)
 {
+    constexpr int U = 4;
+    __shared__ u64 s_red[8][kFields];
+    __shared__ u64 s_err;
     const int lane = threadIdx.x & (T - 1);
     const int64_t groups_total = (int64_t)gridDim.x * (blockDim.x / T);
     u64 nnz_min_c = 0, nnz_max = 0, nnz_sum = 0, nnz_sq = 0;
     u64 bw_min_c = 0, bw_max = 0, bw_sum = 0, disp_sum = 0, clust_sum = 0, ng_sum = 0, ms_sum = 0;
     u128 bw_sq = 0, disp_sq = 0;
     u64 err = 0;
+    if (threadIdx.x == 0) s_err = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (rp[0] != 0) err |= 1;
         if ((int64_t)rp[n_rows] != nnz) err |= 2;
@@ -93,14 +99,26 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
             if (b < 0 || e < b || e > nnz) { err |= 4; ok = false; b = e = 0; }
         }
         u64 ng = 0, ms = 0, bad = 0;
-        for (int64_t j = b + lane; j < e; j += T) {
-            const int64_t c = ci[j];
-            if (c < 0 || c >= n_cols) bad |= 8;
-            if (j > b) {
-                const int64_t d = c - (int64_t)ci[j - 1];
-                if (d <= 0) bad |= 16;
-                ng += (d != 1);
-                ms += (8 * d > line_bytes);
+        for (int64_t j0 = b + lane; j0 < e; j0 += (int64_t)U * T) {
+            int64_t c[U], cp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t j = j0 + u * T;
+                c[u] = j < e ? (int64_t)ci[j] : 0;
+                cp[u] = (j < e && j > b) ? (int64_t)ci[j - 1] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t j = j0 + u * T;
+                if (j < e) {
+                    if (c[u] < 0 || c[u] >= n_cols) bad |= 8;
+                    if (j > b) {
+                        const int64_t d = c[u] - cp[u];
+                        if (d <= 0) bad |= 16;
+                        ng += (d != 1);
+                        ms += (8 * d > line_bytes);
+                    }
+                }
             }
         }
         for (int o = T >> 1; o > 0; o >>= 1) {
@@ -134,8 +152,9 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
             ms_sum += ms;
         }
     }
-    // warp reduction, then one set of atomics per warp
+    // warp reduction, then block reduction, then one set of atomics per block
     for (int o = 16; o > 0; o >>= 1) err |= shfl_u64(err, o);
+    const int w = threadIdx.x >> 5;
     if (FEATURES) {
         nnz_min_c = warp_max_u64(nnz_min_c);
         nnz_max = warp_max_u64(nnz_max);
@@ -151,22 +170,45 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
         ng_sum = warp_sum_u64(ng_sum);
         ms_sum = warp_sum_u64(ms_sum);
     }
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-        if (err) atomicOr(&acc->err, err);
+        if (err) atomicOr(&s_err, err);
+        u64* r = s_red[w];
+        r[0] = nnz_min_c; r[1] = nnz_max; r[2] = nnz_sum; r[3] = nnz_sq;
+        r[4] = bw_min_c; r[5] = bw_max; r[6] = bw_sum;
+        r[7] = (u64)bw_sq; r[8] = (u64)(bw_sq >> 64);
+        r[9] = disp_sum; r[10] = (u64)disp_sq; r[11] = (u64)(disp_sq >> 64);
+        r[12] = clust_sum; r[13] = ng_sum; r[14] = ms_sum; r[15] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        if (s_err) atomicOr(&acc->err, s_err);
         if (FEATURES) {
-            if (nnz_min_c) atomicMax(&acc->nnz_min_c, nnz_min_c);
-            if (nnz_max) atomicMax(&acc->nnz_max, nnz_max);
-            if (nnz_sum) atomicAdd(&acc->nnz_sum, nnz_sum);
-            if (nnz_sq) atomicAdd(&acc->nnz_sumsq, nnz_sq);
-            if (bw_min_c) atomicMax(&acc->bw_min_c, bw_min_c);
-            if (bw_max) atomicMax(&acc->bw_max, bw_max);
-            if (bw_sum) atomicAdd(&acc->bw_sum, bw_sum);
-            atomic_add_u128(&acc->bw_sq_lo, &acc->bw_sq_hi, bw_sq);
-            if (disp_sum) atomicAdd(&acc->disp_sum, disp_sum);
-            atomic_add_u128(&acc->disp_sq_lo, &acc->disp_sq_hi, disp_sq);
-            if (clust_sum) atomicAdd(&acc->clust_sum, clust_sum);
-            if (ng_sum) atomicAdd(&acc->ngroups_sum, ng_sum);
-            if (ms_sum) atomicAdd(&acc->misses_sum, ms_sum);
+            u64 t[kFields] = {0};
+            u128 bsq = 0, dsq = 0;
+            for (int k = 0; k < nw; ++k) {
+                const u64* r = s_red[k];
+                t[0] = max(t[0], r[0]); t[1] = max(t[1], r[1]); t[2] += r[2]; t[3] += r[3];
+                t[4] = max(t[4], r[4]); t[5] = max(t[5], r[5]); t[6] += r[6];
+                bsq += ((u128)r[8] << 64) | r[7];
+                t[9] += r[9];
+                dsq += ((u128)r[11] << 64) | r[10];
+                t[12] += r[12]; t[13] += r[13]; t[14] += r[14];
+            }
+            if (t[0]) atomicMax(&acc->nnz_min_c, t[0]);
+            if (t[1]) atomicMax(&acc->nnz_max, t[1]);
+            if (t[2]) atomicAdd(&acc->nnz_sum, t[2]);
+            if (t[3]) atomicAdd(&acc->nnz_sumsq, t[3]);
+            if (t[4]) atomicMax(&acc->bw_min_c, t[4]);
+            if (t[5]) atomicMax(&acc->bw_max, t[5]);
+            if (t[6]) atomicAdd(&acc->bw_sum, t[6]);
+            atomic_add_u128(&acc->bw_sq_lo, &acc->bw_sq_hi, bsq);
+            if (t[9]) atomicAdd(&acc->disp_sum, t[9]);
+            atomic_add_u128(&acc->disp_sq_lo, &acc->disp_sq_hi, dsq);
+            if (t[12]) atomicAdd(&acc->clust_sum, t[12]);
+            if (t[13]) atomicAdd(&acc->ngroups_sum, t[13]);
+            if (t[14]) atomicAdd(&acc->misses_sum, t[14]);
         }
     }
 }
@@ -199,6 +241,8 @@ float lg1p(double v) { return (float)log2(1.0 + v); }
 
 // pinned host staging for the accumulator readback, one per host thread
 thread_local FeatAcc* t_host_acc = nullptr;
+thread_local FeatAcc* t_dev_acc = nullptr;
+thread_local int t_dev_acc_device = -1;
 
 }  // namespace
 
@@ -225,13 +269,19 @@ spmv_status run_feature_pass(const spmv_csr_t* A, int32_t line_bytes, spmv_featu
             return fail(SPMV_ERR_NOMEM, "cudaMallocHost for the feature readback failed");
         t_host_acc = static_cast<FeatAcc*>(p);
     }
-    FeatAcc* acc = nullptr;
-    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&acc), sizeof(FeatAcc), s));
+    // one device accumulator per host thread and device, kept for reuse
+    if (t_dev_acc_device != dev.device || !t_dev_acc) {
+        void* p = nullptr;
+        SPMV_CUDA_TRY(cudaMalloc(&p, sizeof(FeatAcc)));
+        t_dev_acc = static_cast<FeatAcc*>(p);
+        t_dev_acc_device = dev.device;
+    }
+    FeatAcc* acc = t_dev_acc;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(FeatAcc), s);
     if (e == cudaSuccess && A->n_rows > 0) {
-        const int T = auto_threads_per_row(A->n_rows ? (double)A->nnz / (double)A->n_rows : 1.0);
+        const int T = auto_threads_per_row((double)A->nnz / (double)A->n_rows / 4.0);
         int64_t blocks = (A->n_rows * T + 255) / 256;
-        const int64_t cap = (int64_t)dev.sm_count * 8;
+        const int64_t cap = (int64_t)dev.sm_count * 16;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
         e = out ? launch_pass<true>(T, (unsigned)blocks, s, A, line_bytes, acc)
@@ -239,8 +289,6 @@ spmv_status run_feature_pass(const spmv_csr_t* A, int32_t line_bytes, spmv_featu
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(t_host_acc, acc, sizeof(FeatAcc),
                                               cudaMemcpyDeviceToHost, s);
-    cudaError_t ef = cudaFreeAsync(acc, s);
-    if (e == cudaSuccess) e = ef;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "feature pass");
 

@@ -4,8 +4,8 @@
 // 1-D row partition with (as nearly as possible) equal nonzeros per worker.
 // On the GPU a worker is one warp; the number of workers is the number of
 // warps the device keeps resident at once, so every worker runs from the
-// start of the launch.  A worker walks its rows in order, its 32 lanes
-// striding each row's nonzeros.
+// start of the launch.  A worker walks its rows in order, 32/T rows at a
+// time, each row by a group of T lanes (T from the mean row length).
 //   noxmiss: the same kernel with every column index replaced by 0, which
 //            removes the irregular accesses to x;
 //   inflate: the same kernel with 64-bit rowptr and colind, which enlarges
@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "rowdot.cuh"
 
 namespace spmvlib {
 namespace {
@@ -51,7 +52,7 @@ __global__ void k_widen(int64_t n, const int* __restrict__ in, IT* __restrict__ 
     if (i < n) out[i] = (IT)in[i];
 }
 
-template <typename IT, bool STAMP>
+template <typename IT, bool STAMP, int T>
 __global__ void __launch_bounds__(256)
 k_base(int64_t n_workers, const int64_t* __restrict__ bounds, const IT* __restrict__ rp,
        const IT* __restrict__ ci, const double* __restrict__ v, const double* __restrict__ x,
@@ -63,12 +64,13 @@ k_base(int64_t n_workers, const int64_t* __restrict__ bounds, const IT* __restri
     unsigned long long t0 = 0;
     if (STAMP) t0 = global_ns();
     const int64_t rb = bounds[w], re = bounds[w + 1];
-    for (int64_t r = rb; r < re; ++r) {
-        const int64_t b = (int64_t)rp[r], e = (int64_t)rp[r + 1];
-        double s = 0.0;
-        for (int64_t j = b + lane; j < e; j += 32) s += v[j] * x[ci[j]];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-        if (lane == 0) y[r] = s;
+    for (int64_t r0 = rb; r0 < re; r0 += 32 / T) {
+        const int64_t row = r0 + lane / T;
+        int64_t b = 0, e = 0;
+        if (row < re) { b = (int64_t)rp[row]; e = (int64_t)rp[row + 1]; }
+        const double s = dev::group_sum(
+            dev::row_partial<T, 4>(b, e, lane & (T - 1), dev::ColPlain<IT>{ci}, v, x), T);
+        if ((lane & (T - 1)) == 0 && row < re) y[row] = s;
     }
     if (STAMP && lane == 0) {
         const unsigned long long t1 = global_ns();
@@ -78,12 +80,19 @@ k_base(int64_t n_workers, const int64_t* __restrict__ bounds, const IT* __restri
 }
 
 template <typename IT, bool STAMP>
-cudaError_t launch_base(int64_t n_workers, const int64_t* bounds, const IT* rp, const IT* ci,
-                        const double* v, const double* x, double* y, unsigned long long* st,
-                        cudaStream_t s)
+cudaError_t launch_base(int T, int64_t n_workers, const int64_t* bounds, const IT* rp,
+                        const IT* ci, const double* v, const double* x, double* y,
+                        unsigned long long* st, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((n_workers * 32 + 255) / 256);
-    k_base<IT, STAMP><<<grid, 256, 0, s>>>(n_workers, bounds, rp, ci, v, x, y, st);
+    switch (T) {
+#define SPMV_BASE_CASE(TT) \
+    case TT: k_base<IT, STAMP, TT><<<grid, 256, 0, s>>>(n_workers, bounds, rp, ci, v, x, y, st); break;
+        SPMV_BASE_CASE(1) SPMV_BASE_CASE(2) SPMV_BASE_CASE(4) SPMV_BASE_CASE(8)
+        SPMV_BASE_CASE(16) SPMV_BASE_CASE(32)
+#undef SPMV_BASE_CASE
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -125,10 +134,11 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
     if (st != SPMV_OK) return st;
 
     int per_sm = 0;
-    SPMV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_base<int, false>, 256, 0));
+    SPMV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_base<int, false, 4>, 256, 0));
     if (per_sm < 1) per_sm = 1;
     const int64_t W = (int64_t)dev.sm_count * per_sm * 8;
     const int64_t N = A->n_rows, NNZ = A->nnz;
+    const int T = auto_threads_per_row((double)NNZ / (double)N / 4.0);
 
     DevBuf b_bounds, b_zero, b_rp64, b_ci64, b_y, b_st;
     b_bounds.s = b_zero.s = b_rp64.s = b_ci64.s = b_y.s = b_st.s = s;
@@ -162,11 +172,11 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
             cudaError_t e = cudaEventRecord(e0, s);
             if (e != cudaSuccess) return e;
             if (which == 0)
-                e = launch_base<int, false>(W, bounds, A->rowptr, A->colind, A->val, x, y, nullptr, s);
+                e = launch_base<int, false>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, nullptr, s);
             else if (which == 1)
-                e = launch_base<int, false>(W, bounds, A->rowptr, zero_ci, A->val, x, y, nullptr, s);
+                e = launch_base<int, false>(T, W, bounds, A->rowptr, zero_ci, A->val, x, y, nullptr, s);
             else
-                e = launch_base<int64_t, false>(W, bounds, rp64, ci64, A->val, x, y, nullptr, s);
+                e = launch_base<int64_t, false>(T, W, bounds, rp64, ci64, A->val, x, y, nullptr, s);
             if (e != cudaSuccess) return e;
             if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
@@ -183,7 +193,7 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
     if (e == cudaSuccess) e = time_runs(2, &p.t_inflate_ms);
     std::vector<unsigned long long> h(2 * W);
     if (e == cudaSuccess)
-        e = launch_base<int, true>(W, bounds, A->rowptr, A->colind, A->val, x, y, stamps, s);
+        e = launch_base<int, true>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, stamps, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), stamps, sizeof(unsigned long long) * 2 * W,
                             cudaMemcpyDeviceToHost, s);

@@ -1,0 +1,98 @@
+// Device building blocks shared by the SpMV kernels: cache-hinted loads and
+// the per-row dot product of a group of T lanes with U independent loads in
+// flight per lane.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace spmvlib {
+namespace dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// x is gathered through the read-only (non-coherent) path; arrays that are
+// streamed once are loaded evict-first so they do not push x out of L2.
+__device__ __forceinline__ double ldx(const double* p) { return __ldg(p); }
+__device__ __forceinline__ int ldcs(const int* p) { return __ldcs(p); }
+__device__ __forceinline__ long long ldcs(const long long* p) { return __ldcs(p); }
+__device__ __forceinline__ int64_t ldcs(const int64_t* p) {
+    return (int64_t)__ldcs(reinterpret_cast<const long long*>(p));
+}
+__device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldcs(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ unsigned short ldcs(const unsigned short* p) { return __ldcs(p); }
+
+__device__ __forceinline__ double ldval(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ double ldval(const float* p) { return (double)__ldcs(p); }
+__device__ __forceinline__ double ldval(const __nv_bfloat16* p) {
+    const unsigned short b = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return (double)__uint_as_float(((unsigned)b) << 16);
+}
+
+__device__ __forceinline__ double group_sum(double s, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    return s;
+}
+
+// Column of element j: plain index array, or 16-bit offset from a row base.
+template <typename IT>
+struct ColPlain {
+    const IT* ci;
+    __device__ __forceinline__ int64_t operator()(int64_t j) const { return (int64_t)ldcs(ci + j); }
+};
+struct ColOff16 {
+    const unsigned short* off;
+    int64_t base;
+    __device__ __forceinline__ int64_t operator()(int64_t j) const {
+        return base + (int64_t)ldcs(off + j);
+    }
+};
+
+// Partial dot product of row [b, e) for lane `lane` of a group of T lanes:
+// lane handles j = b + lane + k T.
+//
+// FP64 is the scarce resource on this GPU (about 2 DFMA per clock per SM), so
+// the loop spends exactly one DFMA per element and nothing else in FP64: one
+// accumulator, no per-lane partial sums to combine.  Memory parallelism comes
+// from the loads instead: each pass issues U column and U value loads, then
+// U gathers of x, before its U chained DFMAs.  The remainder (< U elements
+// per lane) issues its loads together and runs only as many DFMAs as the
+// longest lane of the warp needs.  Every lane of the warp must call this
+// (the remainder uses warp votes).
+template <int T, int U, typename COL, typename VT>
+__device__ __forceinline__ double row_partial(int64_t b, int64_t e, int lane, const COL& col,
+                                              const VT* __restrict__ v,
+                                              const double* __restrict__ x)
+{
+    double acc = 0.0;
+    int64_t j = b + lane;
+    for (; j + (int64_t)(U - 1) * T < e; j += (int64_t)U * T) {
+        int64_t c[U];
+        double a[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { c[u] = col(j + u * T); a[u] = ldval(v + j + u * T); }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = ldx(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc = fma(a[u], xv[u], acc);
+    }
+    const int rem = j < e ? (int)((e - j + T - 1) / T) : 0;  // 0 <= rem < U
+    int64_t c[U];
+    double a[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U - 1; ++u) {
+        const bool ok = u < rem;
+        c[u] = ok ? col(j + u * T) : 0;
+        a[u] = ok ? ldval(v + j + u * T) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U - 1; ++u) xv[u] = u < rem ? ldx(x + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U - 1; ++u)
+        if (__any_sync(FULL, u < rem)) acc = u < rem ? fma(a[u], xv[u], acc) : acc;
+    return acc;
+}
+
+}  // namespace dev
+}  // namespace spmvlib

@@ -9,24 +9,18 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "rowdot.cuh"
 
 namespace spmvlib {
 namespace {
 
+using namespace dev;
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ double ldg_x(const double* p) { return __ldg(p); }
-
-// streaming (evict-first) loads for data touched once
-__device__ __forceinline__ int ld_cs(const int* p) { return __ldcs(p); }
-__device__ __forceinline__ double ld_cs(const double* p) { return __ldcs(p); }
-__device__ __forceinline__ unsigned short ld_cs(const unsigned short* p) { return __ldcs(p); }
-__device__ __forceinline__ float ld_cs(const float* p) { return __ldcs(p); }
-
-__device__ __forceinline__ double warp_sum(double s, int width) {
-    for (int o = width >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-    return s;
-}
+__device__ __forceinline__ double warp_sum(double s, int width) { return group_sum(s, width); }
+__device__ __forceinline__ double ldg_x(const double* p) { return ldx(p); }
+template <typename P>
+__device__ __forceinline__ auto ld_cs(const P* p) { return ldcs(p); }
 
 // ------------------------------------------------------------------------
 // V0 SCALAR: one thread per row, Algorithm 1 as written.  The unoptimized
@@ -56,14 +50,7 @@ k_subwarp(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ ci
     const int lane = threadIdx.x & (T - 1);
     int64_t b = 0, e = 0;
     if (row < n_rows) { b = rp[row]; e = rp[row + 1]; }
-    double s0 = 0.0, s1 = 0.0;
-    int64_t j = b + lane;
-    for (; j + T < e; j += 2 * T) {
-        s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-        s1 = fma(ld_cs(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
-    }
-    if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-    double s = warp_sum(s0 + s1, T);
+    const double s = group_sum(row_partial<T, 4>(b, e, lane, ColPlain<int>{ci}, v, x), T);
     if (lane == 0 && row < n_rows) y[row] = s;
 }
 
@@ -119,8 +106,21 @@ k_stream(const int* __restrict__ rp, const int* __restrict__ ci, const double* _
     const int cnt = nz1 - nz0;
     const int nrows = r1 - r0;
     if (cnt <= cap) {
-        for (int t = threadIdx.x; t < cnt; t += kBlock)
-            prod[t] = ld_cs(v + nz0 + t) * ldg_x(x + ld_cs(ci + nz0 + t));
+        for (int t0 = threadIdx.x; t0 < cnt; t0 += 4 * kBlock) {
+            int c[4];
+            double a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * kBlock;
+                c[u] = t < cnt ? ld_cs(ci + nz0 + t) : 0;
+                a[u] = t < cnt ? ld_cs(v + nz0 + t) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * kBlock;
+                if (t < cnt) prod[t] = a[u] * ldg_x(x + c[u]);
+            }
+        }
         __syncthreads();
         if (nrows >= kBlock) {
             for (int r = threadIdx.x; r < nrows; r += kBlock) {
@@ -142,15 +142,9 @@ k_stream(const int* __restrict__ rp, const int* __restrict__ ci, const double* _
         }
     } else {
         for (int r = r0; r < r1; ++r) {
-            const int b = rp[r], e = rp[r + 1];
-            double s0 = 0.0, s1 = 0.0;
-            int j = b + threadIdx.x;
-            for (; j + kBlock < e; j += 2 * kBlock) {
-                s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-                s1 = fma(ld_cs(v + j + kBlock), ldg_x(x + ld_cs(ci + j + kBlock)), s1);
-            }
-            if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-            double s = block_sum(s0 + s1, red);
+            const double p = row_partial<kBlock, 4>(rp[r], rp[r + 1], threadIdx.x,
+                                                    ColPlain<int>{ci}, v, x);
+            const double s = block_sum(p, red);
             if (threadIdx.x == 0) y[r] = s;
         }
     }
@@ -201,9 +195,22 @@ k_merge(int64_t n_parts, const int* __restrict__ rp, const int* __restrict__ ci,
     const int r0 = mrow[p], r1 = mrow[p + 1];
     const int n0 = mnz[p], n1 = mnz[p + 1];
     const int nr = r1 - r0, nn = n1 - n0;
-    for (int k = lane; k < nn; k += 32)
-        s_prod[w][k] = ld_cs(v + n0 + k) * ldg_x(x + ld_cs(ci + n0 + k));
-    for (int k = lane; k < nr; k += 32) s_end[w][k] = rp[r0 + 1 + k];
+    {
+        int c[IPT];
+        double a[IPT];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            const int k = lane + 32 * u;
+            c[u] = k < nn ? ld_cs(ci + n0 + k) : 0;
+            a[u] = k < nn ? ld_cs(v + n0 + k) : 0.0;
+            if (k < nr) s_end[w][k] = ld_cs(rp + r0 + 1 + k);
+        }
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            const int k = lane + 32 * u;
+            if (k < nn) s_prod[w][k] = a[u] * ldg_x(x + c[u]);
+        }
+    }
     __syncwarp();
 
     const int total = nr + nn;
@@ -262,53 +269,6 @@ __global__ void k_merge_fixup(int64_t n_parts, int64_t n_rows, const int32_t* __
 }
 
 // ------------------------------------------------------------------------
-// V4 DYNAMIC: persistent warps take chunks of consecutive rows from a global
-// counter (the GPU form of OpenMP dynamic scheduling, Table 2, IMB class).
-// The last warp to run out of work resets the counters for the next launch.
-template <int T>
-__global__ void __launch_bounds__(kBlock)
-k_dynamic(int64_t n_rows, int chunk_rows, const int* __restrict__ rp, const int* __restrict__ ci,
-          const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y,
-          unsigned int* __restrict__ counter)
-{
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (T - 1);
-    const int grp = lane / T;
-    const int64_t n_chunks = (n_rows + chunk_rows - 1) / chunk_rows;
-    const unsigned total_warps = gridDim.x * (kBlock / 32);
-    for (;;) {
-        unsigned c = 0;
-        if (lane == 0) c = atomicAdd(counter, 1u);
-        c = __shfl_sync(FULL_MASK, c, 0);
-        if ((int64_t)c >= n_chunks) break;
-        const int64_t rbeg = (int64_t)c * chunk_rows;
-        const int64_t rend = rbeg + chunk_rows < n_rows ? rbeg + chunk_rows : n_rows;
-        for (int64_t r0 = rbeg; r0 < rend; r0 += 32 / T) {
-            const int64_t row = r0 + grp;
-            int64_t b = 0, e = 0;
-            if (row < rend) { b = rp[row]; e = rp[row + 1]; }
-            double s0 = 0.0, s1 = 0.0;
-            int64_t j = b + sub;
-            for (; j + T < e; j += 2 * T) {
-                s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-                s1 = fma(ld_cs(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
-            }
-            if (j < e) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-            double s = warp_sum(s0 + s1, T);
-            if (sub == 0 && row < rend) y[row] = s;
-        }
-    }
-    if (lane == 0) {
-        __threadfence();
-        unsigned done = atomicAdd(counter + 1, 1u);
-        if (done == total_warps - 1) {
-            counter[0] = 0u;
-            counter[1] = 0u;
-        }
-    }
-}
-
-// ------------------------------------------------------------------------
 // V5 LATENCY: for matrices bound by the latency of irregular x accesses (CML
 // class; Table 2 software prefetching of x).  Each lane first loads four
 // column indices, then issues the four gathers of x together, then the
@@ -323,20 +283,7 @@ k_latency(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ ci
     const int lane = threadIdx.x & (T - 1);
     int64_t b = 0, e = 0;
     if (row < n_rows) { b = rp[row]; e = rp[row + 1]; }
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int64_t j = b + lane;
-    for (; j + 3 * T < e; j += 4 * T) {
-        const int c0 = ld_cs(ci + j), c1 = ld_cs(ci + j + T);
-        const int c2 = ld_cs(ci + j + 2 * T), c3 = ld_cs(ci + j + 3 * T);
-        const double x0 = ldg_x(x + c0), x1 = ldg_x(x + c1);
-        const double x2 = ldg_x(x + c2), x3 = ldg_x(x + c3);
-        s0 = fma(ld_cs(v + j), x0, s0);
-        s1 = fma(ld_cs(v + j + T), x1, s1);
-        s2 = fma(ld_cs(v + j + 2 * T), x2, s2);
-        s3 = fma(ld_cs(v + j + 3 * T), x3, s3);
-    }
-    for (; j < e; j += T) s0 = fma(ld_cs(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-    double s = warp_sum((s0 + s1) + (s2 + s3), T);
+    const double s = group_sum(row_partial<T, 8>(b, e, lane, ColPlain<int>{ci}, v, x), T);
     if (lane == 0 && row < n_rows) y[row] = s;
 }
 
@@ -391,14 +338,6 @@ __global__ void k_cast_values(int64_t n, const double* __restrict__ v, int value
         static_cast<__nv_bfloat16*>(out)[i] = __double2bfloat16(v[i]);
 }
 
-template <typename VT>
-__device__ __forceinline__ double load_val(const VT* p) { return (double)ld_cs(p); }
-template <>
-__device__ __forceinline__ double load_val<__nv_bfloat16>(const __nv_bfloat16* p) {
-    unsigned short bits = ld_cs(reinterpret_cast<const unsigned short*>(p));
-    return (double)__uint_as_float(((unsigned)bits) << 16);
-}
-
 template <int T, typename VT, bool ALL_WIDE>
 __global__ void __launch_bounds__(kBlock)
 k_compressed(int64_t n_rows, const int* __restrict__ rp, const int32_t* __restrict__ rowbase,
@@ -414,23 +353,12 @@ k_compressed(int64_t n_rows, const int* __restrict__ rp, const int32_t* __restri
         e = rp[row + 1];
         if (!ALL_WIDE) base = rowbase[row];
     }
-    double s0 = 0.0, s1 = 0.0;
-    int64_t j = b + lane;
-    if (ALL_WIDE || base < 0) {
-        for (; j + T < e; j += 2 * T) {
-            s0 = fma(load_val(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-            s1 = fma(load_val(v + j + T), ldg_x(x + ld_cs(ci + j + T)), s1);
-        }
-        if (j < e) s0 = fma(load_val(v + j), ldg_x(x + ld_cs(ci + j)), s0);
-    } else {
-        const double* xb = x + base;
-        for (; j + T < e; j += 2 * T) {
-            s0 = fma(load_val(v + j), ldg_x(xb + ld_cs(off + j)), s0);
-            s1 = fma(load_val(v + j + T), ldg_x(xb + ld_cs(off + j + T)), s1);
-        }
-        if (j < e) s0 = fma(load_val(v + j), ldg_x(xb + ld_cs(off + j)), s0);
-    }
-    double s = warp_sum(s0 + s1, T);
+    double p;
+    if (ALL_WIDE || base < 0)
+        p = row_partial<T, 4>(b, e, lane, ColPlain<int>{ci}, v, x);
+    else
+        p = row_partial<T, 4>(b, e, lane, ColOff16{off, base}, v, x);
+    const double s = group_sum(p, T);
     if (lane == 0 && row < n_rows) y[row] = s;
 }
 
@@ -519,29 +447,6 @@ cudaError_t launch_merge(const spmv_csr_t& A, int items, const int32_t* mrow, co
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_merge_fixup<<<grid_for(n_parts), kBlock, 0, s>>>(n_parts, A.n_rows, carry_row, carry_val, y);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dynamic(const spmv_csr_t& A, int T, int chunk_rows, unsigned int* counter,
-                           int sm_count, const double* x, double* y, cudaStream_t s)
-{
-    if (A.n_rows == 0) return cudaSuccess;
-    int per_sm = 0;
-    cudaError_t e;
-    switch (T) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<1>, kBlock, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<2>, kBlock, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<4>, kBlock, 0); break;
-        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<8>, kBlock, 0); break;
-        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<16>, kBlock, 0); break;
-        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dynamic<32>, kBlock, 0); break;
-        default: return cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const unsigned grid = (unsigned)(sm_count * per_sm);
-    SPMV_DISPATCH_T(T, k_dynamic, grid, 0, s, A.n_rows, chunk_rows, A.rowptr, A.colind, A.val, x,
-                    y, counter);
     return cudaGetLastError();
 }
 

@@ -61,11 +61,10 @@ CHOICES = [
     ("subwarp", {"threads_per_row": 16}), ("subwarp", {"threads_per_row": 32}),
     ("subwarp", {}),
     ("stream", {"block_nnz": 64}), ("stream", {"block_nnz": 256}), ("stream", {}),
-    ("stream", {"block_nnz": 8192}),
-    ("merge", {"items_per_warp": 32}), ("merge", {"items_per_warp": 224}), ("merge", {}),
-    ("merge", {"items_per_warp": 512}),
+    ("stream", {"block_nnz": 1024}), ("stream", {"block_nnz": 8192}),
+    ("merge", {"block_nnz": 1024}), ("merge", {"block_nnz": 2048}), ("merge", {}),
     ("dynamic", {"threads_per_row": 1}), ("dynamic", {"threads_per_row": 8}), ("dynamic", {}),
-    ("dynamic", {"threads_per_row": 32, "block_nnz": 1}),
+    ("dynamic", {"threads_per_row": 32, "block_nnz": 256}), ("dynamic", {"block_nnz": 256}),
     ("latency", {"threads_per_row": 1}), ("latency", {"threads_per_row": 4}), ("latency", {}),
     ("latency", {"threads_per_row": 32}),
     ("compressed", {}), ("compressed", {"threads_per_row": 1}),
@@ -213,6 +212,62 @@ def test_invalid_csr_rejected(kind):
     sp.spmv_validate(sp.DeviceCSR.from_host(_bad_csr("ok")))
 
 
+def _unaligned(A):
+    """The same matrix with every array starting 4 or 8 bytes past a 16-byte
+    boundary, which rules out the bulk-copy kernels."""
+    def shifted(t, pad):
+        buf = torch.zeros(t.numel() + pad, dtype=t.dtype, device="cuda")
+        v = buf[pad:]
+        v.copy_(t.to("cuda"))
+        return v
+    return sp.DeviceCSR(A.n_rows, A.n_cols, shifted(A.rowptr, 1), shifted(A.colind, 1),
+                        shifted(A.val, 1))
+
+
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_merge_unaligned_fallback_parity(name, A):
+    dU = _unaligned(A)
+    if A.nnz:
+        assert dU.colind.data_ptr() % 16 != 0
+    x = synth.uniform_vector(A.n_cols, 1)
+    for items in (32, 256):
+        P = sp.spmv_prepare(dU, sp.make_choice("merge", items_per_warp=items))
+        if A.nnz:
+            assert P.info().bulk_copy == 0
+        y = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        sp.spmv(P, x.cuda(), y)
+        torch.cuda.synchronize()
+        _assert_close(y, A, x)
+
+
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_stream_unaligned_fallback_parity(name, A):
+    dU = _unaligned(A)
+    x = synth.uniform_vector(A.n_cols, 1)
+    P = sp.spmv_prepare(dU, sp.make_choice("stream", block_nnz=1024))
+    if A.nnz:
+        assert P.info().bulk_copy == 0
+    y = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+    sp.spmv(P, x.cuda(), y)
+    torch.cuda.synchronize()
+    _assert_close(y, A, x)
+
+
+@pytest.mark.parametrize("variant", ["stream", "merge"])
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_pipelined_kernels_report_no_timeout(variant, name, A):
+    dA = sp.DeviceCSR.from_host(A)
+    for tile in (1024, 2048):
+        P = sp.spmv_prepare(dA, sp.make_choice(variant, block_nnz=tile))
+        assert P.info().bulk_copy == (1 if A.nnz else P.info().bulk_copy)
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        x = synth.uniform_vector(A.n_cols, 2)
+        for _ in range(3):
+            sp.spmv(P, x.cuda(), y)
+        sp.spmv_prepared_status(P)
+        _assert_close(y, A, x)
+
+
 # ----------------------------------------------------------------- prepared arrays
 def _export(P, which, n, dtype):
     t = torch.empty(n, dtype=dtype)
@@ -228,8 +283,17 @@ def test_prepared_arrays_bit_exact(name, A):
         n = P.info().n_blocks
         assert np.array_equal(_export(P, sp.EXPORT_ROW_BLOCKS, n + 1, torch.int32),
                               oracle.row_blocks(A, B))
+    for tile in (1024, 2048):
+        P = sp.spmv_prepare(dA, sp.make_choice("merge", block_nnz=tile))
+        info = P.info()
+        assert info.bulk_copy == 1 and info.tile_items == tile
+        rs, ns = oracle.merge_path(A, tile)
+        assert np.array_equal(_export(P, sp.EXPORT_MERGE_ROWS, info.n_blocks + 1, torch.int32), rs)
+        assert np.array_equal(_export(P, sp.EXPORT_MERGE_NZ, info.n_blocks + 1, torch.int32), ns)
     for items in (32, 256, 512):
-        P = sp.spmv_prepare(dA, sp.make_choice("merge", items_per_warp=items))
+        dU = _unaligned(A)
+        P = sp.spmv_prepare(dU, sp.make_choice("merge", items_per_warp=items))
+        assert P.info().bulk_copy == 0 and P.info().tile_items == items
         n = P.info().n_blocks
         rs, ns = oracle.merge_path(A, items)
         assert np.array_equal(_export(P, sp.EXPORT_MERGE_ROWS, n + 1, torch.int32), rs)

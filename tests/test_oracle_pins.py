@@ -293,8 +293,8 @@ def test_profile_rule_nan_never_selected():
 
 def test_class_to_variant_table():
     # Table 2 analogue: CML -> latency (5), MB -> compressed (6),
-    # IMB -> merge-path (3), CMP -> stream (2)
-    assert [oracle.class_variant(c) for c in range(4)] == [5, 6, 3, 2]
+    # IMB -> dynamic (4), CMP -> sub-warp (1)
+    assert [oracle.class_variant(c) for c in range(4)] == [5, 6, 4, 1]
 
 
 # --------------------------------------------------------------- partitions
