@@ -272,6 +272,33 @@ spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *
  * Synchronizes `stream`. */
 spmv_status spmv_prepared_status(const spmv_prepared_t *P, spmv_stream_t stream);
 
+/* ---- no-allocation entry point ---------------------------------------------- */
+/* The paper has no counterpart of this call; it exists for callers that must
+ * not allocate device memory: an iterative solver's inner loop that may never
+ * stall the device (cudaMalloc and cudaFree synchronize it), or a host program
+ * that commits all device memory through its own allocator at start-up.
+ *
+ * y = A x with the pipelined STREAM kernel (windows of 2048 nonzeros),
+ * asynchronous on `stream`.  It calls no cudaMalloc, cudaFree or allocating
+ * routine: its scratch (window starts, carried partial rows, a status word;
+ * about 1 MB) is a file-scope __device__ array that every GPU which loads the
+ * library keeps until the process exits.
+ *   - A: device CSR, assumed valid (this call does not validate it; use
+ *     spmv_validate once).  rowptr, colind and val must be 16-byte aligned,
+ *     else SPMV_ERR_UNSUPPORTED.  At most 134,217,728 nonzeros (65,536
+ *     windows), else SPMV_ERR_UNSUPPORTED before any device work.
+ *   - x: device [n_cols], y: device [n_rows], not overlapping.
+ *   - The first call on each device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one scratch array and leaves its contents there;
+ *     calls whose kernels overlap on the GPU (other streams, other host
+ *     threads) race on it and must be serialized by the caller.
+ *   - Bounded device waits that give up leave y incomplete; this call never
+ *     synchronizes, so it does not report them. */
+spmv_status spmv_stream_noalloc(const spmv_csr_t *A, const double *x, double *y,
+                                spmv_stream_t stream);
+
 /* Releases everything P owns (device sync first).  NULL is ignored. */
 void spmv_prepared_free(spmv_prepared_t *P);
 

@@ -207,5 +207,11 @@ def spmv_prepared_status(P: Prepared, stream=None) -> None:
     _check(lib().spmv_prepared_status(P.handle, _stream(stream)))
 
 
+def spmv_stream_noalloc(A: DeviceCSR, x, y, stream=None) -> None:
+    """y = A x with the pipelined STREAM kernel and no device allocation
+    (scratch in a fixed static device array; see include/spmv.h)."""
+    _check(lib().spmv_stream_noalloc(C.byref(A.desc), _ptr(x), _ptr(y), _stream(stream)))
+
+
 def spmv_prepared_free(P: Prepared) -> None:
     P.free()

@@ -96,6 +96,7 @@ def declare(lib):
         "spmv_prepared_info": (I32, [P, C.POINTER(PreparedInfo)]),
         "spmv_prepared_export": (I32, [P, I32, P, I64, P]),
         "spmv_prepared_status": (I32, [P, P]),
+        "spmv_stream_noalloc": (I32, [C.POINTER(CSR), P, P, P]),
         "spmv_prepared_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
