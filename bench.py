@@ -41,6 +41,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic(variant: str, matrix: str):
+    """DRAM bytes per launch recorded from ncu for this kernel, or None when
+    no capture exists or its sources changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(f"{variant}@{matrix}")
+        if not rec:
+            return None
+        for path, prefix in rec["sources"].items():
+            with open(os.path.join(ROOT, path), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest()[:len(prefix)] != prefix:
+                    return None
+        return int(rec["dram_bytes"])
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,13 +258,13 @@ def run_ours(args):
         rec["selected_min_bytes"] = P.info().min_bytes
         # every variant, for the "best possible" comparison
         times = {}
-        for v, kw in candidates:
+        for v, kw in ([] if args.no_variant_sweep else candidates):
             Pv = P if v == rec["variant"] else sp.spmv_prepare(dA, sp.make_choice(v, **kw))
             times[v] = time_spmv(Pv, x, y, reps=10)
             if Pv is not P:
                 Pv.free()
         rec["variant_ms"] = {k: round(v, 5) for k, v in times.items()}
-        rec["best_variant"] = min(times, key=times.get)
+        rec["best_variant"] = min(times, key=times.get) if times else None
         rec["P"], rec["P0"] = P, P0
         per.append(rec)
 
@@ -317,7 +335,8 @@ def run_ours(args):
             "frac_hbm": round(r["min_bytes"] / (km * 1e-3) / 1e9 / peak, 4),
             "plain_gbs": round(r["min_bytes"] / (r["plain_ms"] * 1e-3) / 1e9, 1),
             "speedup_vs_plain": round(s, 3),
-            "best_over_selected": round(km / min(r["variant_ms"].values()), 3),
+            "best_over_selected": (round(km / min(r["variant_ms"].values()), 3)
+                                   if r["variant_ms"] else None),
             "features_spmvs": round(r["features_ms"] / r["plain_ms"], 2),
             "profile_spmvs": round(r["profile_select_ms"] / r["plain_ms"], 1),
             "prepare_ms": round(r["prepare_ms"], 2),
@@ -340,7 +359,8 @@ def run_ours(args):
             "profile": round(sum(r["profile_select_ms"] / r["plain_ms"] for r in per) / len(per), 1)},
         "roofline": {"bound": "hbm", "kernel": f"{per[dom]['variant']} on {per[dom]['matrix']}",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": _traffic(per[dom]["variant"], per[dom]["matrix"]),
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "matrices": matrices,
         "gpu_launches": launches_per_step * args.steps,
@@ -360,6 +380,30 @@ def run_ours(args):
     return 0
 
 
+def run_single(args):
+    """One matrix, one variant, a few SpMVs: the command profiled with ncu."""
+    import torch
+    import paper_1511_02494_gb300 as sp
+    import synth
+    from paper_1511_02494_gb300.build import build
+    build()
+    v, _, kv = args.single.partition(":")
+    kw = {k: int(val) for k, val in (p.split("=") for p in kv.split(",") if p)}
+    make = {"stencil": lambda: synth.stencil_27pt(128), "random": lambda: synth.random_columns(),
+            "zipf": lambda: synth.zipf_rows(), "short": lambda: synth.short_rows()}
+    A = make[args.matrix]()
+    dA = sp.DeviceCSR.from_host(A)
+    x = synth.uniform_vector(A.n_cols, 0).cuda()
+    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    P = sp.spmv_prepare(dA, sp.make_choice(v, **kw))
+    for _ in range(3):
+        sp.spmv(P, x, y)
+    torch.cuda.synchronize()
+    sp.spmv_prepared_status(P)
+    print(json.dumps({"single": args.single, "matrix": A.name, "info": P.info().as_dict()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,9 +413,16 @@ def main():
     ap.add_argument("--scale", type=int, default=0, help="shrink rows by 2^scale (not for records)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variant-sweep", action="store_true",
+                    help="skip timing every variant per matrix (best-variant fields become null)")
+    ap.add_argument("--single", default=None,
+                    help="VARIANT[:k=v,...]: run only this variant on --matrix (for ncu)")
+    ap.add_argument("--matrix", default="stencil", choices=["stencil", "random", "zipf", "short"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.single:
+        return run_single(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 
