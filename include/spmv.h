@@ -241,6 +241,68 @@ int32_t spmv_class_variant(int32_t cls);
 spmv_status spmv_select(const spmv_features_t *f, const spmv_profile_t *p,
                         const spmv_thresholds_t *th, spmv_choice_t *out);
 
+/* ---- learned selector ----------------------------------------------------------- */
+/* The paper's feature-based classifier (Section 3.2.2) maps Table 1 features
+ * to a class with a decision tree or naive Bayes.  This library instead maps
+ * spmv_features_t.vec to a variant with a 16 -> h1 -> h2 -> k ReLU network
+ * (FP32) trained on the GPU (spmv_mlp_loss_grad, spmv_mlp_adam), with the
+ * profiling rule of Section 3.2.1 as its fallback when the top two logits are
+ * closer than the model's min_margin.
+ * params packs row-major W1[h1][16], b1[h1], W2[h2][h1], b2[h2], W3[k][h2],
+ * b3[k]; inputs are standardised z = (v - mean) * istd; every dot product is
+ * an fmaf chain from the bias over inputs in ascending order, identical on
+ * host and device, so logits are reproducible bit for bit. */
+typedef struct spmv_model spmv_model_t;
+
+/* Copies the given host arrays into a new model.  variants[o] is the variant
+ * of output o.  SPMV_ERR_MODEL for a bad shape (hidden widths 1..256,
+ * 2 <= k <= 32), an unknown variant or a non-finite parameter. */
+spmv_status spmv_model_create(int32_t h1, int32_t h2, int32_t k, const float *mean16,
+                              const float *istd16, const float *params,
+                              const int32_t *variants, float min_margin,
+                              spmv_model_t **out);
+/* Binary model file: "SPMVMLP1", int32 h1 h2 k, float mean[16] istd[16],
+ * params, int32 variants[k], float min_margin.  Load fails with
+ * SPMV_ERR_MODEL on a missing, truncated, oversized or corrupt file. */
+spmv_status spmv_model_save(const spmv_model_t *m, const char *path);
+spmv_status spmv_model_load(const char *path, spmv_model_t **out);
+void spmv_model_free(spmv_model_t *m);
+
+/* Logits of one host 16-vector (host computation, k outputs). */
+spmv_status spmv_model_logits(const spmv_model_t *m, const float *vec16, float *logits);
+
+/* Variant for the features f: argmax of the logits (ties to the lower
+ * output), margin = best - second logit.  When margin < min_margin and a
+ * profile p is given, the profiling rule decides instead (used_fallback = 1,
+ * source = 1); otherwise source = 2.  Host-only; th may be NULL. */
+spmv_status spmv_select_model(const spmv_features_t *f, const spmv_model_t *m,
+                              const spmv_profile_t *p, const spmv_thresholds_t *th,
+                              spmv_choice_t *out);
+
+/* Device forward for n host-layout 16-vectors v (device, [n][16]) into
+ * logits (device, [n][k]); params, mean16, istd16 are device arrays.
+ * Asynchronous on `stream`. */
+spmv_status spmv_mlp_forward(const float *params, const float *mean16, const float *istd16,
+                             int32_t h1, int32_t h2, int32_t k, const float *v, int32_t n,
+                             float *logits, spmv_stream_t stream);
+
+/* Mean softmax cross-entropy of the network on standardised inputs z
+ * (device, [n][16]) with labels (device int32, [n], in [0, k)), and its
+ * gradient with respect to params (device, packed as params).  loss: device,
+ * 1 float.  Deterministic (fixed summation order).  Hidden widths <= 128.
+ * Allocates (stream-ordered) and frees its own scratch.  Asynchronous. */
+spmv_status spmv_mlp_loss_grad(const float *params, int32_t h1, int32_t h2, int32_t k,
+                               const float *z, const int32_t *labels, int32_t n, float *grad,
+                               float *loss, spmv_stream_t stream);
+
+/* One Adam step on n device floats (step counts from 1):
+ *   m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
+ *   p -= lr (m/c1 / (sqrt(v/c2) + eps) + weight_decay p),
+ * c1 = 1 - b1^step, c2 = 1 - b2^step, every operation rounded to float. */
+spmv_status spmv_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t n,
+                          int32_t step, float lr, float beta1, float beta2, float eps,
+                          float weight_decay, spmv_stream_t stream);
+
 /* ---- prepare / run ---------------------------------------------------------- */
 /* Builds the prepared form of A for c->variant (validating A first unless
  * `trusted` is non-zero), allocating device memory it owns.  Runs on
@@ -271,6 +333,24 @@ spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *
  * gave up (that call's y is then incomplete), else SPMV_OK; clears the flag.
  * Synchronizes `stream`. */
 spmv_status spmv_prepared_status(const spmv_prepared_t *P, spmv_stream_t stream);
+
+/* ---- iterative solver ---------------------------------------------------------- */
+/* Conjugate gradients for a symmetric positive definite A, the kind of
+ * iterative solver in which SpMV's selection cost is amortised (Section 1).
+ * A_inner: prepared matrix used for q = A p every iteration (for instance
+ * COMPRESSED with FP32 or BF16 values).  A_exact: prepared FP64 form used for
+ * r0 = b - A x0 and, every refine_every iterations (> 0), to recompute the
+ * residual r = b - A x in FP64, after which the search direction restarts
+ * from it (p = r); NULL means A_inner.  Vectors, dot products
+ * and scalars are FP64.  b: device [n]; x: device [n], x0 on entry, the
+ * iterate on return; resid: device [iters + 1] receiving ||r_t||_2, or NULL.
+ * Runs `iters` iterations without a convergence test (no host sync inside the
+ * loop); use_graph != 0 captures the whole loop into a CUDA graph and
+ * launches it.  Allocates its work vectors (3n doubles) stream-ordered.
+ * Asynchronous on `stream`; dot products are deterministic. */
+spmv_status spmv_cg(const spmv_prepared_t *A_inner, const spmv_prepared_t *A_exact,
+                    const double *b, double *x, int32_t iters, int32_t refine_every,
+                    double *resid, int32_t use_graph, spmv_stream_t stream);
 
 /* ---- no-allocation entry point ---------------------------------------------- */
 /* The paper has no counterpart of this call; it exists for callers that must

@@ -86,6 +86,7 @@ def _load():
                 "orc_argmax": (i32, [i32, P, P]),
                 "orc_mlp_loss_grad_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
+                "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -252,6 +253,15 @@ def mlp_loss_grad_f64(params: dict, z, labels):
         h1, h2, k, z.shape[0], *[_p(P64[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")],
         _p(z), _p(lab), *[_p(G[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")])
     return float(loss), G
+
+
+def adam_f32(p, g, m, v, lr, b1, b2, eps, wd, c1, c2):
+    """One float Adam step (operations rounded as written); returns new
+    (p, m, v)."""
+    p = _np(p, np.float32).copy(); m = _np(m, np.float32).copy(); v = _np(v, np.float32).copy()
+    g = _np(g, np.float32)
+    _load().orc_adam_f32(p.size, _p(p), _p(g), _p(m), _p(v), lr, b1, b2, eps, wd, c1, c2)
+    return p, m, v
 
 
 def cg(A, b, x0, iters: int, vkind: int = 0, lowval=None, refine: int = 0):

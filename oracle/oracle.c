@@ -462,12 +462,31 @@ double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
     return loss / batch;
 }
 
+/* One Adam step in float, each operation rounded as written:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p = p - lr (m / c1 / (sqrt(v / c2) + eps) + wd p),  c1 = 1 - b1^t, c2 = 1 - b2^t
+ * with c1, c2 given (computed once per step by the caller).                 */
+void orc_adam_f32(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1,
+                  float b2, float eps, float wd, float c1, float c2)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.0f - b1) * gi;
+        float vi = b2 * v[i] + (1.0f - b2) * (gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        float mh = mi / c1, vh = vi / c2;
+        p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Conjugate gradients (Hestenes-Stiefel), the iterative solver the paper's
  * SpMV serves (Section 1), in FP64 with sequential dot products.  When
  * vkind != 0 the inner product A p uses the low-precision stored values
  * lowval (1 = float32, 2 = bfloat16) and, every `refine` iterations (> 0),
- * the residual is recomputed as r = b - A x with the FP64 values.
+ * the residual is recomputed as r = b - A x with the FP64 values and the
+ * search direction restarts from it (p = r).
  * resid[t] = ||r_t||_2 after iteration t (t = 0 is the initial residual).
  * x holds x0 on entry.  Work arrays r, p, q have n entries each.             */
 static double dot(int64_t n, const double *a, const double *b)
@@ -492,14 +511,16 @@ void orc_cg(int64_t n, const int32_t *rowptr, const int32_t *colind, const doubl
         double pq = dot(n, p, q);
         double alpha = rs / pq;
         for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
-        if (vkind != 0 && refine > 0 && t % refine == 0) {
+        int restart = vkind != 0 && refine > 0 && t % refine == 0;
+        if (restart) {
             orc_spmv(n, rowptr, colind, val, x, q);
             for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
         } else {
             for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
         }
         double rs_new = dot(n, r, r);
-        double beta = rs_new / rs;
+        /* after the residual is recomputed the search restarts from it */
+        double beta = restart ? 0.0 : rs_new / rs;
         for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
         rs = rs_new;
         resid[t] = sqrt(rs);

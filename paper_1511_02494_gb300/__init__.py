@@ -213,5 +213,98 @@ def spmv_stream_noalloc(A: DeviceCSR, x, y, stream=None) -> None:
     _check(lib().spmv_stream_noalloc(C.byref(A.desc), _ptr(x), _ptr(y), _stream(stream)))
 
 
+def spmv_cg(A_inner: Prepared, b, x, iters: int, refine_every: int = 0,
+            A_exact: Prepared | None = None, resid=None, use_graph: bool = False,
+            stream=None) -> None:
+    """Conjugate gradients on the device (x holds x0 on entry)."""
+    _check(lib().spmv_cg(A_inner.handle, A_exact.handle if A_exact else None, _ptr(b), _ptr(x),
+                         int(iters), int(refine_every), _ptr(resid), int(use_graph),
+                         _stream(stream)))
+
+
+class Model:
+    """Owner of an spmv_model_t (the learned selector)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            lib().spmv_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _fptr(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def spmv_model_create(h1, h2, k, mean, istd, params, variants, min_margin=0.0) -> Model:
+    import numpy as np
+    mean, pm = _fptr(mean)
+    istd, pi = _fptr(istd)
+    params, pp = _fptr(params)
+    variants = np.ascontiguousarray(variants, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().spmv_model_create(h1, h2, k, pm, pi, pp, variants.ctypes.data_as(C.c_void_p),
+                                   float(min_margin), C.byref(h)))
+    return Model(h)
+
+
+def spmv_model_load(path: str) -> Model:
+    h = C.c_void_p()
+    _check(lib().spmv_model_load(str(path).encode(), C.byref(h)))
+    return Model(h)
+
+
+def spmv_model_save(m: Model, path: str) -> None:
+    _check(lib().spmv_model_save(m.handle, str(path).encode()))
+
+
+def spmv_model_free(m: Model) -> None:
+    m.free()
+
+
+def spmv_model_logits(m: Model, vec16, k: int):
+    import numpy as np
+    v, pv = _fptr(vec16)
+    out = np.empty(k, np.float32)
+    _check(lib().spmv_model_logits(m.handle, pv, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def spmv_select_model(features: Features, model: Model, profile: Profile | None = None,
+                      thresholds: Thresholds | None = None) -> Choice:
+    out = Choice()
+    _check(lib().spmv_select_model(C.byref(features), model.handle,
+                                   C.byref(profile) if profile else None,
+                                   C.byref(thresholds) if thresholds else None, C.byref(out)))
+    return out
+
+
+def spmv_mlp_forward(params, mean, istd, h1, h2, k, v, logits, stream=None) -> None:
+    _check(lib().spmv_mlp_forward(_ptr(params), _ptr(mean), _ptr(istd), h1, h2, k, _ptr(v),
+                                  int(v.shape[0]), _ptr(logits), _stream(stream)))
+
+
+def spmv_mlp_loss_grad(params, h1, h2, k, z, labels, grad, loss, stream=None) -> None:
+    _check(lib().spmv_mlp_loss_grad(_ptr(params), h1, h2, k, _ptr(z), _ptr(labels),
+                                    int(z.shape[0]), _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def spmv_mlp_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  weight_decay=0.0, stream=None) -> None:
+    _check(lib().spmv_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),
+                               int(step), float(lr), float(beta1), float(beta2), float(eps),
+                               float(weight_decay), _stream(stream)))
+
+
 def spmv_prepared_free(P: Prepared) -> None:
     P.free()

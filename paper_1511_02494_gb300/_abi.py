@@ -97,6 +97,18 @@ def declare(lib):
         "spmv_prepared_export": (I32, [P, I32, P, I64, P]),
         "spmv_prepared_status": (I32, [P, P]),
         "spmv_stream_noalloc": (I32, [C.POINTER(CSR), P, P, P]),
+        "spmv_cg": (I32, [P, P, P, P, I32, I32, P, I32, P]),
+        "spmv_model_create": (I32, [I32, I32, I32, P, P, P, P, C.c_float, C.POINTER(P)]),
+        "spmv_model_save": (I32, [P, C.c_char_p]),
+        "spmv_model_load": (I32, [C.c_char_p, C.POINTER(P)]),
+        "spmv_model_free": (None, [P]),
+        "spmv_model_logits": (I32, [P, P, P]),
+        "spmv_select_model": (I32, [C.POINTER(Features), P, C.POINTER(Profile),
+                                    C.POINTER(Thresholds), C.POINTER(Choice)]),
+        "spmv_mlp_forward": (I32, [P, P, P, I32, I32, I32, P, I32, P, P]),
+        "spmv_mlp_loss_grad": (I32, [P, I32, I32, I32, P, P, I32, P, P, P]),
+        "spmv_mlp_adam": (I32, [P, P, P, P, I64, I32, C.c_float, C.c_float, C.c_float,
+                                C.c_float, C.c_float, P]),
         "spmv_prepared_free": (None, [P]),
     }
     for name, (res, args) in sig.items():

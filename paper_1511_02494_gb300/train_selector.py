@@ -1,0 +1,250 @@
+"""Builds the learned selector: training set on the GPU, then training with
+the library's own kernels.
+
+The training set follows the paper's offline stage (Section 3.2.2, "Training
+Data Selection" and "Labeling") with two changes: the matrices are seeded
+synthetic ones from four generator families (the University of Florida
+collection is not available), and each matrix is labelled with the variant
+that was actually fastest when every variant was timed on it (the paper
+labels with its profiling classifier).  For every matrix it records the
+16-entry feature vector, the time of every variant, the profiling runs and
+their rule's choice, and the cost of feature extraction and profiling.
+
+Training: a 16-64-64-K ReLU network, full-batch Adam on the GPU
+(spmv_mlp_loss_grad + spmv_mlp_adam), 80/20 split by seed.  The fallback
+margin is chosen on the training split.  Outputs (in --out):
+selector_dataset.npz, selector_mlp.bin, selector_report.json.
+
+    python -m paper_1511_02494_gb300.train_selector --out DIR [--n 2000]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_1511_02494_gb300 as sp  # noqa: E402
+import synth  # noqa: E402
+
+N_VAR = len(sp.VARIANTS)
+FIELDS = ("seed", "family", "n_rows", "nnz", "vec", "times", "prof", "rule_variant",
+          "features_ms", "profile_ms")
+
+
+def matrix_spec(i: int):
+    """Family and target row count of matrix i (log-uniform in [1e4, 1e7])."""
+    g = np.random.default_rng(10_000 + i)
+    family = synth.FAMILIES[i % 4]
+    n_rows = int(round(10 ** g.uniform(4.0, 7.0)))
+    return family, n_rows
+
+
+def time_variant(dA, v: int, x, y, budget_ms: float = 25.0):
+    P = sp.spmv_prepare(dA, sp.make_choice(v), trusted=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp.spmv(P, x, y)  # warm-up
+    e0.record()
+    sp.spmv(P, x, y)
+    e1.record()
+    e1.synchronize()
+    first = e0.elapsed_time(e1)
+    ts = [first]
+    if first < budget_ms:
+        for _ in range(3):
+            e0.record()
+            sp.spmv(P, x, y)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    P.free()
+    return float(np.median(ts))
+
+
+def build_dataset(n: int, out_path: str, resume: bool = True, log=print):
+    rows = {k: [] for k in FIELDS}
+    done = set()
+    if resume and os.path.exists(out_path):
+        d = np.load(out_path)
+        for k in FIELDS:
+            rows[k] = list(d[k])
+        done = set(int(s) for s in d["seed"])
+        log(f"resuming with {len(done)} matrices")
+    t_start = time.time()
+    for i in range(n):
+        if i in done:
+            continue
+        family, n_rows = matrix_spec(i)
+        A = synth.family_matrix(family, n_rows, seed=i, device="cuda")
+        dA = sp.DeviceCSR(A.n_rows, A.n_cols, A.rowptr.contiguous(), A.colind.contiguous(),
+                          A.val.contiguous())
+        x = synth.uniform_vector(A.n_cols, i, device="cuda")
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        sp.spmv_features(dA)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = sp.spmv_features(dA)
+        feat_ms = (time.perf_counter() - t0) * 1e3
+        prof = sp.spmv_profile(dA, x, reps=3)
+        rule = sp.spmv_select(profile=prof)
+        times = [time_variant(dA, v, x, y) for v in range(N_VAR)]
+        rows["seed"].append(i)
+        rows["family"].append(synth.FAMILIES.index(family))
+        rows["n_rows"].append(A.n_rows)
+        rows["nnz"].append(A.nnz)
+        rows["vec"].append(np.array(list(f.vec), np.float32))
+        rows["times"].append(np.array(times, np.float64))
+        rows["prof"].append(np.array([prof.s_noxmiss, prof.s_inflate, prof.s_balance], np.float64))
+        rows["rule_variant"].append(rule.variant)
+        rows["features_ms"].append(feat_ms)
+        rows["profile_ms"].append(prof.total_ms)
+        del dA, A, x, y
+        if (i + 1) % 50 == 0 or i == n - 1:
+            np.savez(out_path, **{k: np.array(v) for k, v in rows.items()})
+            torch.cuda.empty_cache()
+            log(f"{i + 1}/{n} matrices, {time.time() - t_start:.0f} s")
+    np.savez(out_path, **{k: np.array(v) for k, v in rows.items()})
+    return {k: np.array(v) for k, v in rows.items()}
+
+
+def init_params(h1, h2, k, seed=0):
+    g = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((16, h1), (h1, h2), (h2, k)):
+        bound = math.sqrt(6.0 / fan_in)
+        parts.append(g.uniform(-bound, bound, (fan_out, fan_in)).astype(np.float32).reshape(-1))
+        parts.append(np.zeros(fan_out, np.float32))
+    return np.concatenate(parts)
+
+
+def train(z: np.ndarray, labels: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000, lr=3e-3,
+          wd=1e-4, seed=0, log=print):
+    """Full-batch Adam with the library's loss/gradient and Adam kernels."""
+    p = torch.from_numpy(init_params(h1, h2, k, seed)).cuda()
+    g = torch.zeros_like(p)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    dz = torch.from_numpy(np.ascontiguousarray(z, np.float32)).cuda()
+    dl = torch.from_numpy(np.ascontiguousarray(labels, np.int32)).cuda()
+    hist = []
+    for step in range(1, steps + 1):
+        sp.spmv_mlp_loss_grad(p, h1, h2, k, dz, dl, g, loss)
+        sp.spmv_mlp_adam(p, g, m, v, step, lr=lr, weight_decay=wd)
+        if step % 500 == 0 or step == 1:
+            hist.append((step, float(loss.item())))
+            log(f"step {step} loss {hist[-1][1]:.4f}")
+    return p.cpu().numpy(), hist
+
+
+def logits_of(params, mean, istd, vec, h1, h2, k):
+    out = torch.empty((vec.shape[0], k), dtype=torch.float32, device="cuda")
+    sp.spmv_mlp_forward(torch.from_numpy(params).cuda(), torch.from_numpy(mean).cuda(),
+                        torch.from_numpy(istd).cuda(), h1, h2, k,
+                        torch.from_numpy(np.ascontiguousarray(vec, np.float32)).cuda(), out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def policy_times(times, pred, margin, rule, mu):
+    pick = np.where(margin < mu, rule, pred)
+    return times[np.arange(len(times)), pick], pick
+
+
+def geomean(a):
+    return float(np.exp(np.mean(np.log(a))))
+
+
+def evaluate(d, params, mean, istd, mu, h1, h2, k, idx):
+    times = d["times"][idx]
+    best = times.min(1)
+    lg = logits_of(params, mean, istd, d["vec"][idx], h1, h2, k)
+    pred = lg.argmax(1)
+    srt = np.sort(lg, 1)
+    margin = srt[:, -1] - srt[:, -2]
+    rule = d["rule_variant"][idx]
+    t_mlp = times[np.arange(len(idx)), pred]
+    t_pol, pick = policy_times(times, pred, margin, rule, mu)
+    t_rule = times[np.arange(len(idx)), rule]
+    fixed = int(np.argmin([geomean(times[:, v] / best) for v in range(times.shape[1])]))
+    plain = times[:, 0]
+    feat_spmv = d["features_ms"][idx] / plain
+    prof_spmv = d["profile_ms"][idx] / plain
+    return {
+        "matrices": int(len(idx)),
+        "label_counts": np.bincount(times.argmin(1), minlength=times.shape[1]).tolist(),
+        "misselection_mlp": float(np.mean(pred != times.argmin(1))),
+        "misselection_policy": float(np.mean(pick != times.argmin(1))),
+        "misselection_rule": float(np.mean(rule != times.argmin(1))),
+        "slowdown_vs_best_geomean": {"mlp": geomean(t_mlp / best), "mlp_with_fallback": geomean(t_pol / best),
+                                     "profile_rule": geomean(t_rule / best),
+                                     "best_fixed_variant": geomean(times[:, fixed] / best),
+                                     "plain_csr": geomean(plain / best)},
+        "best_fixed_variant": sp.VARIANTS[fixed],
+        "speedup_vs_plain_geomean": {"best": geomean(plain / best), "mlp": geomean(plain / t_mlp),
+                                     "mlp_with_fallback": geomean(plain / t_pol),
+                                     "profile_rule": geomean(plain / t_rule)},
+        "fallback_rate": float(np.mean(margin < mu)),
+        "overhead_in_plain_spmvs": {"features_median": float(np.median(feat_spmv)),
+                                    "profile_median": float(np.median(prof_spmv)),
+                                    "features_mean": float(np.mean(feat_spmv)),
+                                    "profile_mean": float(np.mean(prof_spmv))},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--n", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--no-resume", action="store_true")
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    from paper_1511_02494_gb300.build import build
+    build()
+    ds_path = os.path.join(args.out, "selector_dataset.npz")
+    d = build_dataset(args.n, ds_path, resume=not args.no_resume)
+    seeds = d["seed"]
+    test = np.where(seeds % 5 == 0)[0]
+    tr = np.where(seeds % 5 != 0)[0]
+    vec = d["vec"].astype(np.float32)
+    mean = vec[tr].mean(0).astype(np.float32)
+    sd = vec[tr].std(0)
+    istd = np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 0.0).astype(np.float32)
+    z = ((vec - mean) * istd).astype(np.float32)
+    labels = d["times"].argmin(1).astype(np.int32)
+    h1, h2, k = 64, 64, N_VAR
+    params, hist = train(z[tr], labels[tr], h1, h2, k, steps=args.steps)
+    # fallback margin: smallest value whose training slowdown is within 0.5 %
+    # of the best any margin achieves
+    lg = logits_of(params, mean, istd, vec[tr], h1, h2, k)
+    srt = np.sort(lg, 1)
+    margin = srt[:, -1] - srt[:, -2]
+    best = d["times"][tr].min(1)
+    cands = [0.0] + sorted(set(np.quantile(margin, np.linspace(0.02, 0.5, 25)).tolist()))
+    slow = [geomean(policy_times(d["times"][tr], lg.argmax(1), margin, d["rule_variant"][tr], mu)[0] / best)
+            for mu in cands]
+    target = min(slow) * 1.005
+    mu = float(next(c for c, s in zip(cands, slow) if s <= target))
+    model = sp.spmv_model_create(h1, h2, k, mean, istd, params, list(range(k)), mu)
+    sp.spmv_model_save(model, os.path.join(args.out, "selector_mlp.bin"))
+    report = {"train": evaluate(d, params, mean, istd, mu, h1, h2, k, tr),
+              "test": evaluate(d, params, mean, istd, mu, h1, h2, k, test),
+              "min_margin": mu, "loss_history": hist, "variants": list(sp.VARIANTS),
+              "network": [16, h1, h2, k]}
+    with open(os.path.join(args.out, "selector_report.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    print(json.dumps(report["test"], indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -279,13 +279,25 @@ def dense_to_csr(dense: torch.Tensor) -> HostCSR:
 FAMILIES = ("stencil", "random", "zipf", "short")
 
 
+MAX_FAMILY_NNZ = 250_000_000
+
+
+def _zipf_mean(alpha: float, max_len: int) -> float:
+    k = torch.arange(1, max_len + 1, dtype=torch.float64)
+    w = k.pow(-alpha)
+    return float((k * w).sum() / w.sum())
+
+
 def family_matrix(family: str, n_rows: int, seed: int, device="cpu") -> HostCSR:
     """One matrix of a family with randomized parameters, for selector
     training sets and batched workloads.  ``n_rows`` is a target; stencils round
-    it to a grid."""
+    it to a grid.  Parameters are clipped so that the expected number of
+    nonzeros stays below MAX_FAMILY_NNZ."""
     g = _gen(seed * 7919 + 17, "cpu")  # parameter draws are tiny: always CPU
     if family == "stencil":
         pts = [7, 27][int(torch.randint(0, 2, (1,), generator=g))]
+        if pts == 27 and 27 * n_rows > MAX_FAMILY_NNZ:
+            pts = 7
         n = max(4, round(n_rows ** (1.0 / 3.0)))
         if pts == 27:
             A = stencil_27pt(n, seed=seed, device=device)
@@ -295,10 +307,13 @@ def family_matrix(family: str, n_rows: int, seed: int, device="cpu") -> HostCSR:
         return A
     if family == "random":
         per_row = int(torch.randint(2, 65, (1,), generator=g))
-        return random_columns(n_rows, n_rows, min(per_row, n_rows), seed=seed, device=device)
+        per_row = max(1, min(per_row, n_rows, MAX_FAMILY_NNZ // n_rows))
+        return random_columns(n_rows, n_rows, per_row, seed=seed, device=device)
     if family == "zipf":
         alpha = 1.2 + 1.3 * float(torch.rand(1, generator=g, dtype=torch.float64))
         max_len = max(2, min(n_rows // 5, 200_000))
+        while max_len > 2 and n_rows * _zipf_mean(alpha, max_len) > MAX_FAMILY_NNZ:
+            max_len //= 2
         return zipf_rows(n_rows, n_rows, alpha, max_len, seed=seed, device=device)
     if family == "short":
         per = int(torch.randint(1, 5, (1,), generator=g))

@@ -1,0 +1,75 @@
+"""Conjugate gradients on the GPU against the oracle's CG (same algorithm,
+same arithmetic up to summation order): FP64 throughout, and a low-precision
+inner SpMV (FP32 / BF16 values) with FP64 residual recomputation."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1511_02494_gb300 as sp
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1511_02494_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _run(A, b, iters, inner, refine=0, graph=False, exact="subwarp"):
+    dA = sp.DeviceCSR.from_host(A)
+    Pi = sp.spmv_prepare(dA, inner)
+    Pe = sp.spmv_prepare(dA, sp.make_choice(exact))
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    res = torch.empty(iters + 1, dtype=torch.float64, device="cuda")
+    sp.spmv_cg(Pi, b.cuda(), x, iters, refine, A_exact=Pe, resid=res, use_graph=graph)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), res.cpu().numpy()
+
+
+def _close(x, r, xo, ro):
+    assert np.max(np.abs(x - xo)) <= 1e-9 * np.max(np.abs(xo))
+    assert np.all(np.abs(r - ro) <= 1e-6 * ro + 1e-12 * ro[0])
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("variant", ["subwarp", "compressed", "dynamic", "stream"])
+def test_cg_fp64_matches_oracle(variant, graph):
+    A = synth.variable_coeff_laplacian_3d(14, seed=1)
+    b = synth.uniform_vector(A.n_rows, 3)
+    x, r = _run(A, b, 60, sp.make_choice(variant), graph=graph)
+    xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 60)
+    _close(x, r, xo, ro)
+    assert r[-1] < 1e-6 * r[0]
+
+
+@pytest.mark.parametrize("vt,vkind", [(sp.VAL_F32, 1), (sp.VAL_BF16, 2)])
+@pytest.mark.parametrize("refine", [0, 10])
+def test_cg_low_precision_inner_matches_oracle(vt, vkind, refine):
+    A = synth.variable_coeff_laplacian_3d(12, seed=2)
+    b = synth.uniform_vector(A.n_rows, 4)
+    low = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
+    x, r = _run(A, b, 50, sp.make_choice("compressed", value_type=vt), refine=refine)
+    xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 50, vkind=vkind, lowval=low, refine=refine)
+    _close(x, r, xo, ro)
+
+
+def test_cg_refinement_recovers_fp64_accuracy():
+    """With BF16 values the recursive residual drifts from the true one;
+    recomputing it in FP64 every 10 iterations brings the true residual of
+    the BF16-inner solve down to the FP64 solve's level."""
+    A = synth.variable_coeff_laplacian_3d(16, seed=3)
+    b = synth.uniform_vector(A.n_rows, 5)
+    x64, _ = _run(A, b, 120, sp.make_choice("subwarp"))
+    xr, _ = _run(A, b, 120, sp.make_choice("compressed", value_type=sp.VAL_BF16), refine=10)
+    xn, _ = _run(A, b, 120, sp.make_choice("compressed", value_type=sp.VAL_BF16), refine=0)
+
+    def true_res(x):
+        return np.linalg.norm(b.numpy() - oracle.spmv(A, x)) / np.linalg.norm(b.numpy())
+
+    assert true_res(x64) < 1e-9
+    assert true_res(xr) < 1e-8
+    assert true_res(xn) > 10 * true_res(xr)

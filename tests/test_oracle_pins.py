@@ -450,7 +450,21 @@ def test_cg_lowp_with_representable_values_equals_fp64():
     x64, r64 = oracle.cg(A, b, np.zeros(A.n_rows), 40)
     x2, r2 = oracle.cg(A, b, np.zeros(A.n_rows), 40, vkind=2, lowval=oracle.round_bf16(A.val))
     assert np.array_equal(x64, x2) and np.array_equal(r64, r2)
-    # with refinement the recomputed residual equals the recursive one to rounding
-    x3, r3 = oracle.cg(A, b, np.zeros(A.n_rows), 40, vkind=1, lowval=oracle.round_f32(A.val),
-                       refine=10)
-    np.testing.assert_allclose(x3, x64, rtol=1e-9, atol=1e-12)
+
+def test_cg_refinement_converges_to_the_fp64_solution():
+    """With BF16 values and the residual recomputed in FP64 (search restarted
+    from it) every k iterations, x converges to the solution of the FP64
+    system (dense solve), which plain BF16 CG cannot reach."""
+    A = synth.variable_coeff_laplacian_3d(6, seed=1)
+    b = synth.uniform_vector(A.n_rows, 2).numpy()
+    D = np.zeros((A.n_rows, A.n_rows))
+    rp, ci, v = A.rowptr.numpy(), A.colind.numpy(), A.val.numpy()
+    for i in range(A.n_rows):
+        D[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    xs = np.linalg.solve(D, b)
+    low = oracle.round_bf16(A.val)
+    for k in (5, 10, 25):
+        x, _ = oracle.cg(A, b, np.zeros(A.n_rows), 200, vkind=2, lowval=low, refine=k)
+        np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-12)
+    xn, _ = oracle.cg(A, b, np.zeros(A.n_rows), 200, vkind=2, lowval=low, refine=0)
+    assert np.max(np.abs(xn - xs)) > 1e-5 * np.max(np.abs(xs))
