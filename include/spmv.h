@@ -334,6 +334,36 @@ spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *
  * Synchronizes `stream`. */
 spmv_status spmv_prepared_status(const spmv_prepared_t *P, spmv_stream_t stream);
 
+/* ---- batched SpMV -------------------------------------------------------------- */
+/* Many matrices of uneven size in one persistent launch.  Each matrix has a
+ * launch shape: lanes per row T (power of two, 1..32) and rows per work item
+ * (default 8 * 32 / T); the work list is every matrix's row chunks, taken by
+ * persistent warps from one atomic counter.  Matrices are borrowed (device
+ * CSR, assumed valid); the batch owns its work list and descriptor table. */
+typedef struct spmv_batch spmv_batch_t;
+
+/* threads_per_row / rows_per_item: host [count] or NULL (T from the mean row
+ * length, rows per item 8 * 32 / T).  Synchronizes `stream`. */
+spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
+                              const int32_t *threads_per_row, const int32_t *rows_per_item,
+                              spmv_batch_t **out, spmv_stream_t stream);
+/* Sets the vectors: x[m], y[m] are device pointers (host arrays of count
+ * pointers).  Must precede spmv_batch_run; synchronizes `stream`. */
+spmv_status spmv_batch_bind(spmv_batch_t *B, const double *const *x, double *const *y,
+                            spmv_stream_t stream);
+/* y[m] = A[m] x[m] for every matrix in one kernel launch.  use_graph != 0:
+ * the launch is captured once into a CUDA graph (on the first such call) and
+ * the graph is launched on `stream` from then on.  Asynchronous. */
+spmv_status spmv_batch_run(spmv_batch_t *B, int32_t use_graph, spmv_stream_t stream);
+/* Times every T in {1, 2, 4, ..., 32} on each matrix alone (reps launches
+ * each, 0 = 3) and keeps the fastest, with rows per item 8 * 32 / T.  Needs a
+ * bound batch; invalidates a captured graph.  Synchronizes `stream`. */
+spmv_status spmv_batch_autotune(spmv_batch_t *B, int32_t reps, spmv_stream_t stream);
+/* Current launch shapes (host arrays of count entries; either may be NULL). */
+spmv_status spmv_batch_config(const spmv_batch_t *B, int32_t *threads_per_row,
+                              int32_t *rows_per_item);
+void spmv_batch_free(spmv_batch_t *B);
+
 /* ---- iterative solver ---------------------------------------------------------- */
 /* Conjugate gradients for a symmetric positive definite A, the kind of
  * iterative solver in which SpMV's selection cost is amortised (Section 1).

@@ -222,6 +222,66 @@ def spmv_cg(A_inner: Prepared, b, x, iters: int, refine_every: int = 0,
                          _stream(stream)))
 
 
+class Batch:
+    """Owner of an spmv_batch_t; keeps its matrices and vectors alive."""
+
+    def __init__(self, handle, mats):
+        self.handle, self.mats, self.vecs = handle, mats, None
+
+    def free(self):
+        if self.handle:
+            lib().spmv_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spmv_batch_create(mats, threads_per_row=None, rows_per_item=None, stream=None) -> Batch:
+    import numpy as np
+    n = len(mats)
+    arr = (CSR * max(n, 1))(*[m.desc for m in mats])
+    tp = None if threads_per_row is None else np.ascontiguousarray(threads_per_row, np.int32)
+    rp = None if rows_per_item is None else np.ascontiguousarray(rows_per_item, np.int32)
+    h = C.c_void_p()
+    _check(lib().spmv_batch_create(arr, n, tp.ctypes.data_as(C.c_void_p) if tp is not None else None,
+                                   rp.ctypes.data_as(C.c_void_p) if rp is not None else None,
+                                   C.byref(h), _stream(stream)))
+    return Batch(h, list(mats))
+
+
+def spmv_batch_bind(B: Batch, xs, ys, stream=None) -> None:
+    n = len(B.mats)
+    xa = (C.c_void_p * max(n, 1))(*[x.data_ptr() for x in xs])
+    ya = (C.c_void_p * max(n, 1))(*[y.data_ptr() for y in ys])
+    B.vecs = (list(xs), list(ys))
+    _check(lib().spmv_batch_bind(B.handle, xa, ya, _stream(stream)))
+
+
+def spmv_batch_run(B: Batch, use_graph: bool = False, stream=None) -> None:
+    _check(lib().spmv_batch_run(B.handle, int(use_graph), _stream(stream)))
+
+
+def spmv_batch_autotune(B: Batch, reps: int = 3, stream=None) -> None:
+    _check(lib().spmv_batch_autotune(B.handle, int(reps), _stream(stream)))
+
+
+def spmv_batch_config(B: Batch):
+    import numpy as np
+    n = len(B.mats)
+    t = np.zeros(max(n, 1), np.int32)
+    r = np.zeros(max(n, 1), np.int32)
+    _check(lib().spmv_batch_config(B.handle, t.ctypes.data_as(C.c_void_p), r.ctypes.data_as(C.c_void_p)))
+    return t[:n], r[:n]
+
+
+def spmv_batch_free(B: Batch) -> None:
+    B.free()
+
+
 class Model:
     """Owner of an spmv_model_t (the learned selector)."""
 

@@ -98,6 +98,12 @@ def declare(lib):
         "spmv_prepared_status": (I32, [P, P]),
         "spmv_stream_noalloc": (I32, [C.POINTER(CSR), P, P, P]),
         "spmv_cg": (I32, [P, P, P, P, I32, I32, P, I32, P]),
+        "spmv_batch_create": (I32, [C.POINTER(CSR), I32, P, P, C.POINTER(P), P]),
+        "spmv_batch_bind": (I32, [P, P, P, P]),
+        "spmv_batch_run": (I32, [P, I32, P]),
+        "spmv_batch_autotune": (I32, [P, I32, P]),
+        "spmv_batch_config": (I32, [P, P, P]),
+        "spmv_batch_free": (None, [P]),
         "spmv_model_create": (I32, [I32, I32, I32, P, P, P, P, C.c_float, C.POINTER(P)]),
         "spmv_model_save": (I32, [P, C.c_char_p]),
         "spmv_model_load": (I32, [C.c_char_p, C.POINTER(P)]),

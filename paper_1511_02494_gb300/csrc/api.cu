@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -448,6 +449,28 @@ spmv_status spmv_prepare(const spmv_csr_t* A, const spmv_choice_t* c, int32_t tr
     if (st == SPMV_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "spmv_prepare");
+    }
+    if (st == SPMV_OK && A->n_rows > 0) {
+        // configure the variant's kernels now (one SpMV into scratch vectors),
+        // so that later launches, including captured ones, make no
+        // configuration call
+        double *xs = nullptr, *ys = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&xs), 8 * std::max<int64_t>(A->n_cols, 1), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ys), 8 * A->n_rows, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(xs, 0, 8 * std::max<int64_t>(A->n_cols, 1), s);
+        if (e == cudaSuccess) {
+            spmv_status rs = run_impl(P, xs, ys, s);
+            if (rs != SPMV_OK) st = rs;
+        }
+        if (xs) cudaFreeAsync(xs, s);
+        if (ys) cudaFreeAsync(ys, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess && st == SPMV_OK) st = cuda_fail(e, "spmv_prepare configure");
+        if (st == SPMV_OK && P->status) {
+            // the configuring run may not leave a timeout flag behind
+            cudaMemsetAsync(P->status, 0, sizeof(unsigned), s);
+            cudaStreamSynchronize(s);
+        }
     }
     if (st != SPMV_OK) {
         cudaStreamSynchronize(s);

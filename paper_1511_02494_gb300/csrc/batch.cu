@@ -1,0 +1,311 @@
+// Batched SpMV: many matrices of uneven size in one persistent launch.
+//
+// A batch holds, per matrix, its CSR arrays, its bound x and y and its
+// launch shape (lanes per row T, rows per work item).  The work list is the
+// concatenation of every matrix's row chunks; persistent warps take items
+// from one atomic counter (the last warp resets it), so small and large
+// matrices share the GPU without one launch per matrix.  An item of matrix m
+// covers rows_per_item[m] consecutive rows, 32/T rows at a time, each row by T
+// lanes with one DFMA per nonzero (row_partial).  A run is a single kernel
+// launch with no host work, so it can be replayed from a CUDA graph.
+//
+// Autotuning (spmv_batch_autotune) times every T in {1,...,32} on each matrix
+// alone and keeps the fastest; without it T comes from the mean row length.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "rowdot.cuh"
+
+struct BatchMat {
+    const int* rp;
+    const int* ci;
+    const double* v;
+    const double* x;
+    double* y;
+    int64_t n_rows;
+};
+
+struct BatchItem {
+    int32_t m, r0, r1, lg;  // matrix, rows [r0, r1), log2 of lanes per row
+};
+
+struct spmv_batch {
+    int device = -1;
+    int sm_count = 0;
+    std::vector<spmv_csr_t> mats;
+    std::vector<int32_t> tpr, rpi;   // lanes per row, rows per item
+    std::vector<const double*> xs;
+    std::vector<double*> ys;
+    BatchMat* d_mats = nullptr;
+    BatchItem* d_items = nullptr;
+    int64_t n_items = 0;
+    unsigned* d_counter = nullptr;
+    bool bound = false;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace spmvlib {
+namespace {
+
+using namespace dev;
+constexpr int kBT = 256;
+
+template <int T>
+__device__ __forceinline__ void batch_rows(const BatchMat& M, int r0, int r1, int lane)
+{
+    const ColPlain<int> col{M.ci};
+    for (int base = r0; base < r1; base += 32 / T) {
+        const int row = base + lane / T;
+        int64_t b = 0, e = 0;
+        if (row < r1) { b = M.rp[row]; e = M.rp[row + 1]; }
+        const double s = group_sum(row_partial<T, 4>(b, e, lane & (T - 1), col, M.v, M.x), T);
+        if ((lane & (T - 1)) == 0 && row < r1) M.y[row] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int64_t n_items,
+        unsigned* __restrict__ counter)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned total_warps = gridDim.x * (kBT / 32);
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if ((int64_t)it >= n_items) break;
+        const BatchItem I = items[it];
+        const BatchMat M = mats[I.m];
+        switch (I.lg) {
+            case 0: batch_rows<1>(M, I.r0, I.r1, lane); break;
+            case 1: batch_rows<2>(M, I.r0, I.r1, lane); break;
+            case 2: batch_rows<4>(M, I.r0, I.r1, lane); break;
+            case 3: batch_rows<8>(M, I.r0, I.r1, lane); break;
+            case 4: batch_rows<16>(M, I.r0, I.r1, lane); break;
+            default: batch_rows<32>(M, I.r0, I.r1, lane); break;
+        }
+    }
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(counter + 1, 1u) == total_warps - 1) {
+            counter[0] = 0u;
+            counter[1] = 0u;
+        }
+    }
+}
+
+int lg2(int t)
+{
+    int l = 0;
+    while ((1 << l) < t) ++l;
+    return l;
+}
+
+spmv_status build_items(spmv_batch* B, cudaStream_t s)
+{
+    std::vector<BatchItem> items;
+    for (size_t m = 0; m < B->mats.size(); ++m) {
+        const int n = (int)B->mats[m].n_rows;
+        const int r = B->rpi[m];
+        for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(B->tpr[m])});
+    }
+    if (B->d_items) cudaFree(B->d_items);
+    B->d_items = nullptr;
+    B->n_items = (int64_t)items.size();
+    if (items.empty()) return SPMV_OK;
+    SPMV_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&B->d_items), sizeof(BatchItem) * items.size()));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(B->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                                  cudaMemcpyHostToDevice, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+    return SPMV_OK;
+}
+
+cudaError_t launch_batch(const spmv_batch* B, const BatchMat* mats, const BatchItem* items,
+                         int64_t n_items, cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    static LaunchCache cache;
+    int per_sm = 0;
+    cudaError_t e = cached_occupancy(cache, k_batch, kBT, 0, &per_sm);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)B->sm_count * per_sm;
+    const int64_t need = (n_items + kBT / 32 - 1) / (kBT / 32);
+    if (grid > need) grid = need;
+    k_batch<<<(unsigned)grid, kBT, 0, s>>>(mats, items, n_items, B->d_counter);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace spmvlib
+
+using namespace spmvlib;
+
+extern "C" {
+
+spmv_status spmv_batch_create(const spmv_csr_t* mats, int32_t count, const int32_t* threads_per_row,
+                              const int32_t* rows_per_item, spmv_batch_t** out,
+                              spmv_stream_t stream)
+{
+    clear_error();
+    if (!out || count < 0 || (count > 0 && !mats))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_create: bad argument");
+    *out = nullptr;
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spmv_batch* B = new (std::nothrow) spmv_batch();
+    if (!B) return fail(SPMV_ERR_NOMEM, "host allocation failed");
+    B->device = dev.device;
+    B->sm_count = dev.sm_count;
+    for (int m = 0; m < count; ++m) {
+        if ((st = check_csr_args(&mats[m])) != SPMV_OK) { spmv_batch_free(B); return st; }
+        const int t = threads_per_row ? threads_per_row[m] : 0;
+        if (t != 0 && (t < 1 || t > 32 || (t & (t - 1)))) {
+            spmv_batch_free(B);
+            return fail(SPMV_ERR_INVALID_ARG, "threads_per_row must be a power of two in 1..32");
+        }
+        const double mean = mats[m].n_rows ? (double)mats[m].nnz / (double)mats[m].n_rows : 1.0;
+        const int T = t ? t : auto_threads_per_row(mean / 7.0);
+        const int r = rows_per_item && rows_per_item[m] > 0 ? rows_per_item[m] : 8 * (32 / T);
+        B->mats.push_back(mats[m]);
+        B->tpr.push_back(T);
+        B->rpi.push_back(r);
+    }
+    B->xs.assign(count, nullptr);
+    B->ys.assign(count, nullptr);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&B->d_counter), 8);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, 8, s);
+    if (e == cudaSuccess && count > 0)
+        e = cudaMalloc(reinterpret_cast<void**>(&B->d_mats), sizeof(BatchMat) * count);
+    if (e != cudaSuccess) { spmv_batch_free(B); return cuda_fail(e, "spmv_batch_create"); }
+    if ((st = build_items(B, s)) != SPMV_OK) { spmv_batch_free(B); return st; }
+    *out = B;
+    return SPMV_OK;
+}
+
+spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* const* y,
+                            spmv_stream_t stream)
+{
+    clear_error();
+    if (!B || (!B->mats.empty() && (!x || !y)))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_bind: NULL argument");
+    std::vector<BatchMat> h(B->mats.size());
+    for (size_t m = 0; m < B->mats.size(); ++m) {
+        const spmv_csr_t& A = B->mats[m];
+        h[m] = {A.rowptr, A.colind, A.val, x[m], y[m], A.n_rows};
+        B->xs[m] = x[m];
+        B->ys[m] = y[m];
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!h.empty()) {
+        SPMV_CUDA_TRY(cudaMemcpyAsync(B->d_mats, h.data(), sizeof(BatchMat) * h.size(),
+                                      cudaMemcpyHostToDevice, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    B->bound = true;
+    return SPMV_OK;
+}
+
+spmv_status spmv_batch_run(spmv_batch_t* B, int32_t use_graph, spmv_stream_t stream)
+{
+    if (!B) return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_run: NULL batch");
+    if (!B->bound) return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_run: call spmv_batch_bind first");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!use_graph) {
+        cudaError_t e = launch_batch(B, B->d_mats, B->d_items, B->n_items, s);
+        return e == cudaSuccess ? SPMV_OK : cuda_fail(e, "spmv_batch_run");
+    }
+    if (!B->graph) {
+        // capture once on a private stream, replay on any stream afterwards
+        cudaStream_t cs;
+        SPMV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = launch_batch(B, B->d_mats, B->d_items, B->n_items, cs);
+            e = cudaStreamEndCapture(cs, &g);
+            if (e == cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            B->graph = nullptr;
+            return cuda_fail(e, "spmv_batch_run graph capture");
+        }
+    }
+    SPMV_CUDA_TRY(cudaGraphLaunch(B->graph, s));
+    return SPMV_OK;
+}
+
+spmv_status spmv_batch_autotune(spmv_batch_t* B, int32_t reps, spmv_stream_t stream)
+{
+    clear_error();
+    if (!B || !B->bound) return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_autotune: bind first");
+    if (reps <= 0) reps = 3;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    SPMV_CUDA_TRY(cudaEventCreate(&e0));
+    SPMV_CUDA_TRY(cudaEventCreate(&e1));
+    BatchItem* d_tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (size_t m = 0; m < B->mats.size() && e == cudaSuccess; ++m) {
+        const int n = (int)B->mats[m].n_rows;
+        if (n == 0) continue;
+        float best = 1e30f;
+        int best_t = B->tpr[m];
+        for (int T = 1; T <= 32 && e == cudaSuccess; T <<= 1) {
+            const int r = 8 * (32 / T);
+            std::vector<BatchItem> items;
+            for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(T)});
+            if (d_tmp) cudaFreeAsync(d_tmp, s);
+            e = cudaMallocAsync(reinterpret_cast<void**>(&d_tmp), sizeof(BatchItem) * items.size(), s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_tmp, items.data(), sizeof(BatchItem) * items.size(),
+                                    cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = launch_batch(B, B->d_mats, d_tmp, (int64_t)items.size(), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int k = 0; k < reps && e == cudaSuccess; ++k)
+                e = launch_batch(B, B->d_mats, d_tmp, (int64_t)items.size(), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) { best = ms; best_t = T; }
+        }
+        B->tpr[m] = best_t;
+        B->rpi[m] = 8 * (32 / best_t);
+    }
+    if (d_tmp) cudaFreeAsync(d_tmp, s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_batch_autotune");
+    return build_items(B, s);
+}
+
+spmv_status spmv_batch_config(const spmv_batch_t* B, int32_t* threads_per_row, int32_t* rows_per_item)
+{
+    clear_error();
+    if (!B) return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_config: NULL batch");
+    for (size_t m = 0; m < B->mats.size(); ++m) {
+        if (threads_per_row) threads_per_row[m] = B->tpr[m];
+        if (rows_per_item) rows_per_item[m] = B->rpi[m];
+    }
+    return SPMV_OK;
+}
+
+void spmv_batch_free(spmv_batch_t* B)
+{
+    if (!B) return;
+    cudaDeviceSynchronize();
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->d_items) cudaFree(B->d_items);
+    if (B->d_mats) cudaFree(B->d_mats);
+    if (B->d_counter) cudaFree(B->d_counter);
+    delete B;
+}
+
+}  // extern "C"

@@ -211,11 +211,18 @@ extern "C" spmv_status spmv_cg(const spmv_prepared_t* A_inner, const spmv_prepar
     SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.st), sizeof(CgState), s));
     SPMV_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(CgState), s));
     if (use_graph) {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured), then launch on the caller's
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        SPMV_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = enqueue_cg(Pi, Pe, b, x, iters, refine_every, resid, w, grid, s);
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        cudaStream_t cs = nullptr;
+        SPMV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = enqueue_cg(Pi, Pe, b, x, iters, refine_every, resid, w, grid, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        cudaStreamDestroy(cs);
         if (st != SPMV_OK) {
             if (graph) cudaGraphDestroy(graph);
             return st;

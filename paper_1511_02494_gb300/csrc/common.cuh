@@ -125,4 +125,32 @@ spmv_status run_feature_pass(const spmv_csr_t* A, int32_t line_bytes,
 // Default lanes per row for a mean row length.
 int auto_threads_per_row(double mean_nnz);
 
+// Per-device cache of a kernel's launch configuration (dynamic shared memory
+// attribute set, resident blocks per SM), filled outside any stream capture
+// by the variant's configure step at prepare time so that later launches --
+// including launches captured into a CUDA graph -- make no other API call.
+struct LaunchCache {
+    int per_sm[64] = {};
+};
+template <typename K>
+cudaError_t cached_occupancy(LaunchCache& c, K kernel, int threads, size_t smem, int* per_sm)
+{
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    if (c.per_sm[d] == 0) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+        if (e != cudaSuccess) return e;
+        c.per_sm[d] = n > 0 ? n : -1;
+    }
+    *per_sm = c.per_sm[d];
+    return *per_sm > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 }  // namespace spmvlib

@@ -174,10 +174,10 @@ __global__ void k_dyn_fixup(int n_long, const int* __restrict__ lrow, const int*
 template <int TS>
 cudaError_t launch_dyn_t(const DynArgs& a, int sm_count, cudaStream_t s)
 {
+    static LaunchCache cache;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dyn<TS>, kDB, 0);
+    cudaError_t e = cached_occupancy(cache, k_dyn<TS>, kDB, 0, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     k_dyn<TS><<<(unsigned)(sm_count * per_sm), kDB, 0, s>>>(a);
     return cudaGetLastError();
 }

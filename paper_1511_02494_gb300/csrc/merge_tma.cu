@@ -251,15 +251,11 @@ cudaError_t launch_tma_cfg(const spmv_csr_t& A, const int32_t* mrow, const int32
                            unsigned* status, int sm_count, const double* x, double* y,
                            cudaStream_t s)
 {
+    static LaunchCache cache;
     const size_t smem = sizeof(TileSmem<IPT, STAGES>);
-    cudaError_t e = cudaFuncSetAttribute(k_merge_tma<IPT, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_tma<IPT, STAGES>, kThreads,
-                                                      smem);
+    cudaError_t e = cached_occupancy(cache, k_merge_tma<IPT, STAGES>, kThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * per_sm;
     if (grid > n_tiles) grid = n_tiles;
     k_merge_tma<IPT, STAGES><<<(unsigned)grid, kThreads, smem, s>>>(

@@ -411,8 +411,10 @@ cudaError_t launch_stream(const spmv_csr_t& A, const int32_t* blocks, int64_t n_
     if (A.n_rows == 0) return cudaSuccess;
     const int cap = 2 * block_nnz;
     const size_t smem = (size_t)cap * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // the largest window (8192 -> 128 KB) is enabled once per device
+    static LaunchCache cache;
+    int per_sm = 0;
+    cudaError_t e = cached_occupancy(cache, k_stream, kBlock, 2 * 8192 * sizeof(double), &per_sm);
     if (e != cudaSuccess) return e;
     k_stream<<<(unsigned)n_blocks, kBlock, smem, s>>>(A.rowptr, A.colind, A.val, x, y, blocks, cap);
     return cudaGetLastError();

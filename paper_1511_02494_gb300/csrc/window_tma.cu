@@ -232,14 +232,11 @@ cudaError_t launch_win_cfg(const spmv_csr_t& A, const int32_t* blocks, int64_t n
                            int32_t* carry_row, double* carry_val, unsigned* status,
                            int sm_count, const double* x, double* y, cudaStream_t s)
 {
+    static LaunchCache cache;
     const size_t smem = sizeof(WinSmem<B, STAGES>);
-    cudaError_t e = cudaFuncSetAttribute(k_window<B, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_window<B, STAGES>, kWT, smem);
+    cudaError_t e = cached_occupancy(cache, k_window<B, STAGES>, kWT, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * per_sm;
     if (grid > n_win) grid = n_win;
     k_window<B, STAGES><<<(unsigned)grid, kWT, smem, s>>>(n_win, (int)A.nnz, (int)A.n_rows,

@@ -37,7 +37,7 @@ __all__ = [
     "HostCSR", "laplacian_2d_5pt", "laplacian_3d_7pt", "stencil_27pt",
     "random_columns", "zipf_rows", "short_rows", "random_csr",
     "uniform_vector", "variable_coeff_laplacian_3d", "family_matrix",
-    "FAMILIES", "four_class_set", "dense_to_csr",
+    "FAMILIES", "four_class_set", "dense_to_csr", "batch_matrices",
 ]
 
 
@@ -323,9 +323,10 @@ def family_matrix(family: str, n_rows: int, seed: int, device="cpu") -> HostCSR:
         gg = _gen(seed, device)
         lengths = torch.full((n_rows,), per, dtype=torch.int64, device=device)
         # banded: columns drawn from a window of width `band` around the row
+        width = min(max(band, per), n_rows)
+        lengths = torch.clamp(lengths, max=width)
         i = torch.arange(n_rows, device=device)
-        lo = torch.clamp(i - band // 2, 0, max(0, n_rows - band))
-        width = min(band, n_rows)
+        lo = torch.clamp(i - width // 2, 0, max(0, n_rows - width))
         cols = _distinct_sorted_columns(lengths, width, gg, device).to(torch.int64)
         cols = cols + torch.repeat_interleave(lo, lengths)
         val = _uniform(cols.numel(), gg, device)
@@ -345,3 +346,42 @@ def four_class_set(device="cpu", scale: int = 0):
         zipf_rows((1 << 20) // s, None, 1.8, max(2, 200_000 // s), seed=0, device=device),
         short_rows((1 << 23) // s, 8, seed=0, device=device),
     ]
+
+
+def batch_matrices(count: int = 512, seed: int = 0, lo: float = 1e3, hi: float = 1e5,
+                   device="cpu"):
+    """A batch of uneven matrices: rows log-uniform in [lo, hi], families
+    mixed in turn, row lengths within 2..200 (stencils of 7 or 27 points,
+    2-64 random columns per row, Zipf lengths capped at 200, banded rows of
+    2-4 nonzeros)."""
+    g = _gen(seed, "cpu")
+    out = []
+    for i in range(count):
+        n = int(round(10 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo))
+                             * float(torch.rand(1, generator=g, dtype=torch.float64)))))
+        fam = FAMILIES[i % 4]
+        s = seed * 100_003 + i
+        if fam == "stencil":
+            m = max(4, round(n ** (1 / 3)))
+            A = stencil_27pt(m, seed=s, device=device) if i % 8 == 0 else laplacian_3d_7pt(m, device=device)
+            if i % 8 != 0:
+                A.val = _uniform(A.nnz, _gen(s, device), device)
+        elif fam == "random":
+            per = int(torch.randint(2, 65, (1,), generator=g))
+            A = random_columns(n, n, min(per, n), seed=s, device=device)
+        elif fam == "zipf":
+            alpha = 1.5 + float(torch.rand(1, generator=g, dtype=torch.float64))
+            A = zipf_rows(n, n, alpha, min(200, n), seed=s, device=device)
+        else:
+            per = int(torch.randint(2, 5, (1,), generator=g))
+            gg = _gen(s, device)
+            lengths = torch.full((n,), per, dtype=torch.int64, device=device)
+            band = min(32, n)
+            i_ = torch.arange(n, device=device)
+            lo_ = torch.clamp(i_ - band // 2, 0, max(0, n - band))
+            cols = _distinct_sorted_columns(lengths, band, gg, device).to(torch.int64)
+            cols = cols + torch.repeat_interleave(lo_, lengths)
+            A = HostCSR(n, n, _rowptr_from_lengths(lengths), cols.to(torch.int32),
+                        _uniform(cols.numel(), gg, device), f"banded_{n}x{per}")
+        out.append(A)
+    return out

@@ -1,0 +1,80 @@
+"""Batched persistent SpMV against the oracle, plain and graph launches,
+before and after autotuning."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1511_02494_gb300 as sp
+import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1511_02494_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module")
+def batch_case():
+    mats = synth.batch_matrices(48, seed=1, lo=1e3, hi=2e4)
+    mats.append(synth.random_csr(0, 5, 2))          # an empty matrix
+    mats.append(synth.random_csr(700, 300, 0, seed=2))  # rows all empty
+    dev = [sp.DeviceCSR.from_host(A) for A in mats]
+    xs = [synth.uniform_vector(A.n_cols, 10 + i).cuda() for i, A in enumerate(mats)]
+    ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats]
+    return mats, dev, xs, ys
+
+
+def _check(mats, xs, ys):
+    for A, x, y in zip(mats, xs, ys):
+        ref, scale = oracle.spmv_ref(A, x.cpu())
+        got = y.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= RTOL * scale), A.name
+        assert np.all(got[scale == 0] == 0.0)
+
+
+def test_batch_matches_oracle_plain_graph_and_autotuned(batch_case):
+    mats, dev, xs, ys = batch_case
+    B = sp.spmv_batch_create(dev)
+    sp.spmv_batch_bind(B, xs, ys)
+    sp.spmv_batch_run(B)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    for y in ys:
+        y.fill_(float("nan"))
+    for _ in range(3):
+        sp.spmv_batch_run(B, use_graph=True)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    first = [y.clone() for y in ys]
+    sp.spmv_batch_autotune(B, reps=2)
+    t, r = sp.spmv_batch_config(B)
+    assert set(t.tolist()) <= {1, 2, 4, 8, 16, 32}
+    assert np.all(r == 8 * (32 // t))
+    for y in ys:
+        y.fill_(float("nan"))
+    sp.spmv_batch_run(B, use_graph=True)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    B.free()
+
+
+def test_batch_explicit_shapes(batch_case):
+    mats, dev, xs, ys = batch_case
+    n = len(mats)
+    for T in (1, 4, 32):
+        B = sp.spmv_batch_create(dev, threads_per_row=[T] * n, rows_per_item=[37] * n)
+        sp.spmv_batch_bind(B, xs, ys)
+        for y in ys:
+            y.fill_(float("nan"))
+        sp.spmv_batch_run(B)
+        torch.cuda.synchronize()
+        _check(mats, xs, ys)
+        B.free()
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_batch_create(dev, threads_per_row=[3] * n)
