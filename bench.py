@@ -227,6 +227,8 @@ def run_ours(args):
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    model_path = os.path.join(ROOT, "paper_1511_02494_gb300", "data", "selector_mlp.bin")
+    model = sp.spmv_model_load(model_path) if os.path.exists(model_path) else None
     per = []
     candidates = [("scalar", {}), ("subwarp", {}), ("stream", {}), ("merge", {}),
                   ("dynamic", {}), ("latency", {}), ("compressed", {})]
@@ -237,20 +239,23 @@ def run_ours(args):
         t_plain = time_spmv(P0, x, y)
         rec["plain_ms"] = t_plain
         rec["min_bytes"] = P0.info().min_bytes
-        # feature extraction cost
+        # feature extraction + learned selector (the paper's lightweight path)
         sp.spmv_features(dA)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         f = sp.spmv_features(dA)
+        ch_model = sp.spmv_select_model(f, model) if model is not None else None
         rec["features_ms"] = (time.perf_counter() - t0) * 1e3
-        # profiling runs + rule
+        # profiling runs + rule (Section 3.2.1)
         t0 = time.perf_counter()
         prof = sp.spmv_profile(dA, x, reps=3)
-        ch = sp.spmv_select(features=f, profile=prof)
+        ch_rule = sp.spmv_select(features=f, profile=prof)
         rec["profile_select_ms"] = (time.perf_counter() - t0) * 1e3
         rec["profile"] = {k: round(v, 4) if isinstance(v, float) else v
                           for k, v in prof.as_dict().items()}
-        rec["class"] = sp.CLASSES[ch.cls]
+        rec["class"] = sp.CLASSES[ch_rule.cls]
+        rec["variant_rule"] = sp.VARIANTS[ch_rule.variant]
+        ch = ch_model if ch_model is not None else ch_rule
         rec["variant"] = sp.VARIANTS[ch.variant]
         t0 = time.perf_counter()
         P = sp.spmv_prepare(dA, ch)
@@ -330,6 +335,7 @@ def run_ours(args):
     for r, km, s in zip(per, kern_ms, speedups):
         matrices.append({
             "matrix": r["matrix"], "class": r["class"], "variant": r["variant"],
+            "variant_rule": r["variant_rule"],
             "best_variant": r["best_variant"], "ms": round(km, 5),
             "gbs": round(r["min_bytes"] / (km * 1e-3) / 1e9, 1),
             "frac_hbm": round(r["min_bytes"] / (km * 1e-3) / 1e9 / peak, 4),
@@ -347,7 +353,8 @@ def run_ours(args):
         "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.scale == 0 else WORKLOAD + f" (rows / 2^{args.scale})",
-                   "selection": "profiling-based rule (Section 3.2.1)",
+                   "selection": ("learned selector on Table 1 features" if model is not None
+                                 else "profiling-based rule (Section 3.2.1)"),
                    "l2": "no flush: every matrix (>= 369 MB) is larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "frac_of_hbm_peak": round(value / peak, 4),
@@ -355,8 +362,9 @@ def run_ours(args):
         "speedup_vs_plain_csr": round(plain_total / sel_total, 3),
         "speedup_geomean": round(math.exp(sum(map(math.log, speedups)) / len(speedups)), 3),
         "selector_cost_spmvs": {
-            "features": round(sum(r["features_ms"] / r["plain_ms"] for r in per) / len(per), 2),
-            "profile": round(sum(r["profile_select_ms"] / r["plain_ms"] for r in per) / len(per), 1)},
+            "features_and_model": round(sum(r["features_ms"] / r["plain_ms"] for r in per) / len(per), 2),
+            "profile_and_rule": round(sum(r["profile_select_ms"] / r["plain_ms"] for r in per) / len(per), 1),
+            "unit": "plain-CSR SpMVs of the same matrix, mean over the four"},
         "roofline": {"bound": "hbm", "kernel": f"{per[dom]['variant']} on {per[dom]['matrix']}",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
@@ -404,6 +412,150 @@ def run_single(args):
     return 0
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_ms(fn, reps=10, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_cg(args):
+    """Mixed precision: compressed SpMV throughput with FP32/BF16 values, and
+    300 CG iterations on the SPD 7-point Laplacian 128^3 (variable
+    coefficients) with an FP64, FP32 or BF16 inner SpMV and FP64 residual
+    recomputation; errors are against the FP64 GPU solve."""
+    import torch
+    import paper_1511_02494_gb300 as sp
+    import synth
+    from paper_1511_02494_gb300.build import build
+    build()
+    out = {"mode": "mixed_precision", "spmv": [], "cg": []}
+    for A in (synth.stencil_27pt(128), synth.random_columns()):
+        dA = sp.DeviceCSR.from_host(A)
+        x = synth.uniform_vector(A.n_cols, 0).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        yref = torch.empty_like(y)
+        P64 = sp.spmv_prepare(dA, sp.make_choice("subwarp"))
+        sp.spmv(P64, x, yref)
+        for name, vt in (("f64", sp.VAL_F64), ("f32", sp.VAL_F32), ("bf16", sp.VAL_BF16)):
+            P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt))
+            ms = _time_ms(lambda: sp.spmv(P, x, y))
+            sp.spmv(P, x, y)
+            scale = torch.linalg.vector_norm(yref, float("inf")).item()
+            err = (torch.linalg.vector_norm(y - yref, float("inf")) / scale).item()
+            mb = P.info().min_bytes
+            out["spmv"].append({"matrix": A.name, "values": name, "ms": round(ms, 5),
+                                "min_bytes": mb, "gbs": round(mb / ms / 1e6, 1),
+                                "rel_err_vs_f64": err, "wide_rows": P.info().n_wide_rows})
+            P.free()
+        P64.free()
+    A = synth.variable_coeff_laplacian_3d(128, seed=0)
+    dA = sp.DeviceCSR.from_host(A)
+    b = synth.uniform_vector(A.n_rows, 1).cuda()
+    exact = sp.spmv_prepare(dA, sp.make_choice("subwarp"))
+    iters = 300
+    xs = {}
+    for name, vt, refine in (("f64", None, 0), ("f32", sp.VAL_F32, 10), ("bf16", sp.VAL_BF16, 10),
+                             ("bf16_no_refine", sp.VAL_BF16, 0)):
+        inner = exact if vt is None else sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt))
+        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        res = torch.empty(iters + 1, dtype=torch.float64, device="cuda")
+        sp.spmv_cg(inner, b, x, iters, refine, A_exact=exact, resid=res, use_graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        x.zero_()
+        e0.record()
+        sp.spmv_cg(inner, b, x, iters, refine, A_exact=exact, resid=res, use_graph=True)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = torch.empty_like(b)
+        sp.spmv(exact, x, r)
+        true_res = (torch.linalg.vector_norm(b - r) / torch.linalg.vector_norm(b)).item()
+        xs[name] = x.clone()
+        out["cg"].append({"inner": name, "refine_every": refine, "iters": iters,
+                          "ms_total": round(ms, 3), "ms_per_iter": round(ms / iters, 5),
+                          "true_rel_residual": true_res,
+                          "recursive_rel_residual": (res[-1] / res[0]).item()})
+    for rec in out["cg"]:
+        d = xs[rec["inner"]] - xs["f64"]
+        rec["rel_err_vs_f64_solution"] = (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(xs["f64"])).item()
+    out["cg_matrix"] = {"name": A.name, "n_rows": A.n_rows, "nnz": A.nnz}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """512 uneven matrices: one launch per matrix with each matrix's own
+    selected variant, against one persistent launch (plain, graph, autotuned)."""
+    import numpy as np
+    import torch
+    import paper_1511_02494_gb300 as sp
+    import synth
+    from paper_1511_02494_gb300.build import build
+    build()
+    mats = synth.batch_matrices(512, seed=0)
+    dev = [sp.DeviceCSR.from_host(A) for A in mats]
+    xs = [synth.uniform_vector(A.n_cols, i).cuda() for i, A in enumerate(mats)]
+    ys = [torch.empty(A.n_rows, dtype=torch.float64, device="cuda") for A in mats]
+    total_bytes = sum(A.min_bytes() for A in mats)
+    model_path = os.path.join(ROOT, "paper_1511_02494_gb300", "data", "selector_mlp.bin")
+    model = sp.spmv_model_load(model_path) if os.path.exists(model_path) else None
+    t0 = time.perf_counter()
+    choices = []
+    for dA in dev:
+        f = sp.spmv_features(dA)
+        if model is not None:
+            choices.append(sp.spmv_select_model(f, model).variant)
+        else:
+            choices.append(sp.VARIANT_IDS["subwarp"])
+    select_s = time.perf_counter() - t0
+    preps = [sp.spmv_prepare(dA, sp.make_choice(int(v)), trusted=True) for dA, v in zip(dev, choices)]
+
+    def per_matrix():
+        for P, x, y in zip(preps, xs, ys):
+            sp.spmv(P, x, y)
+    ms_sep = _time_ms(per_matrix, reps=5, warm=2)
+    # batch lanes per row: from each matrix's selected variant's prepared shape
+    tpr = [max(1, P.info().threads_per_row) for P in preps]
+    B = sp.spmv_batch_create(dev, threads_per_row=tpr)
+    sp.spmv_batch_bind(B, xs, ys)
+    ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)
+    ms_graph = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
+    t0 = time.perf_counter()
+    sp.spmv_batch_autotune(B, reps=3)
+    tune_s = time.perf_counter() - t0
+    ms_tuned = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
+    t, _ = sp.spmv_batch_config(B)
+    out = {"mode": "batched", "matrices": len(mats), "nnz": int(sum(A.nnz for A in mats)),
+           "rows_range": [min(A.n_rows for A in mats), max(A.n_rows for A in mats)],
+           "min_bytes": total_bytes,
+           "selection": "learned selector" if model is not None else "sub-warp default",
+           "selection_s": round(select_s, 3),
+           "variant_counts": {sp.VARIANTS[v]: int(c) for v, c in
+                              zip(*np.unique(np.array(choices), return_counts=True))},
+           "ms_one_launch_per_matrix": round(ms_sep, 4),
+           "ms_persistent": round(ms_plain, 4), "ms_persistent_graph": round(ms_graph, 4),
+           "ms_persistent_graph_autotuned": round(ms_tuned, 4), "autotune_s": round(tune_s, 2),
+           "gbs_one_launch_per_matrix": round(total_bytes / ms_sep / 1e6, 1),
+           "gbs_persistent_graph_autotuned": round(total_bytes / ms_tuned / 1e6, 1),
+           "autotuned_lanes_per_row_counts": {int(k): int(c) for k, c in
+                                              zip(*np.unique(t, return_counts=True))}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,11 +570,17 @@ def main():
     ap.add_argument("--single", default=None,
                     help="VARIANT[:k=v,...]: run only this variant on --matrix (for ncu)")
     ap.add_argument("--matrix", default="stencil", choices=["stencil", "random", "zipf", "short"])
+    ap.add_argument("--cg", action="store_true", help="mixed-precision SpMV and CG report")
+    ap.add_argument("--batch", action="store_true", help="batched persistent SpMV report")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.single:
         return run_single(args)
+    if args.cg:
+        return run_cg(args)
+    if args.batch:
+        return run_batch(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 
