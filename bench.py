@@ -431,8 +431,8 @@ def _time_ms(fn, reps=10, warm=3):
 
 
 def run_cg(args):
-    """Mixed precision: compressed SpMV throughput with FP32/BF16 values, and
-    300 CG iterations on the SPD 7-point Laplacian 128^3 (variable
+    """Mixed precision: compressed SpMV throughput with FP32/BF16 values (FP32
+    or FP64 accumulation), and 300 CG iterations on the SPD 7-point Laplacian 128^3 (variable
     coefficients) with an FP64, FP32 or BF16 inner SpMV and FP64 residual
     recomputation; errors are against the FP64 GPU solve."""
     import torch
@@ -448,8 +448,10 @@ def run_cg(args):
         yref = torch.empty_like(y)
         P64 = sp.spmv_prepare(dA, sp.make_choice("subwarp"))
         sp.spmv(P64, x, yref)
-        for name, vt in (("f64", sp.VAL_F64), ("f32", sp.VAL_F32), ("bf16", sp.VAL_BF16)):
-            P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt))
+        for name, vt, acc in (("f64", sp.VAL_F64, sp.ACC_F64), ("f32", sp.VAL_F32, sp.ACC_F32),
+                              ("bf16", sp.VAL_BF16, sp.ACC_F32), ("f32_acc64", sp.VAL_F32, sp.ACC_F64),
+                              ("bf16_acc64", sp.VAL_BF16, sp.ACC_F64)):
+            P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt, accumulate=acc))
             ms = _time_ms(lambda: sp.spmv(P, x, y))
             sp.spmv(P, x, y)
             scale = torch.linalg.vector_norm(yref, float("inf")).item()

@@ -155,6 +155,13 @@ typedef struct {
  *   block_nnz       : DYNAMIC nonzeros per segment of a long row (power of two,
  *                     256..2^20; default 2048)
  *   value_type      : COMPRESSED value storage (spmv_value_type)
+ *   accumulate      : COMPRESSED arithmetic.  FP32 (the default for FP32/BF16
+ *                     values) rounds x to an FP32 copy owned by the prepared
+ *                     object once per call and sums in FP32 (no FP64
+ *                     instruction per nonzero; relative error ~1e-7 against
+ *                     the same values in FP64); spmv calls on one such object
+ *                     must not overlap.  FP64 converts each value and sums in
+ *                     FP64.
  * Filled by spmv_select: cls (or -1), margin (model logit gap, or 0),
  * used_fallback (1 when the model deferred to the profile rule), source
  * (0 explicit, 1 profile rule, 2 model). */
@@ -168,6 +175,8 @@ typedef struct {
     float margin;
     int32_t used_fallback;
     int32_t source;
+    int32_t accumulate;  /* COMPRESSED: 0 by value type (FP64 values -> FP64,
+                            FP32/BF16 values -> FP32), 1 FP64, 2 FP32 */
 } spmv_choice_t;
 
 /* A matrix prepared for one variant (opaque).  It borrows A's arrays and owns
@@ -184,6 +193,7 @@ typedef struct {
     int64_t min_bytes;     /* minimum traffic of one spmv() with this format    */
     int32_t tile_items;    /* MERGE: merge-path items per tile as prepared      */
     int32_t bulk_copy;     /* 1 when the pipelined bulk-copy kernel is used     */
+    int32_t accumulate;    /* 1 FP64, 2 FP32 (COMPRESSED with FP32 accumulation) */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */

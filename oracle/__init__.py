@@ -72,6 +72,7 @@ def _load():
                 "orc_spmv": (None, [i64, P, P, P, P, P]),
                 "orc_spmv_ref": (None, [i64, P, P, P, P, i64, P, P, P]),
                 "orc_spmv_lowp": (None, [i64, P, P, i32, P, P, P]),
+                "orc_spmv_lowp32": (None, [i64, P, P, i32, P, P, P]),
                 "orc_round_bf16": (C.c_uint16, [C.c_double]),
                 "orc_round_bf16_array": (None, [i64, P, P]),
                 "orc_round_f32_array": (None, [i64, P, P]),
@@ -145,6 +146,17 @@ def spmv_lowp(A, x, vkind: int, lowval) -> np.ndarray:
     lv = _np(lowval, np.float32 if vkind == 1 else np.uint16)
     y = np.empty(A.n_rows, np.float64)
     _load().orc_spmv_lowp(A.n_rows, _p(rp), _p(ci), vkind, _p(lv), _p(x), _p(y))
+    return y
+
+
+def spmv_lowp32(A, x, vkind: int, lowval) -> np.ndarray:
+    """y = A x in FP32 arithmetic: float32 (vkind=1) or bfloat16-bit
+    (vkind=2) values, x rounded to float, fmaf accumulation per row."""
+    rp, ci, _ = _csr(A)
+    x = _np(x, np.float64)
+    lv = _np(lowval, np.float32 if vkind == 1 else np.uint16)
+    y = np.empty(A.n_rows, np.float64)
+    _load().orc_spmv_lowp32(A.n_rows, _p(rp), _p(ci), vkind, _p(lv), _p(x), _p(y))
     return y
 
 

@@ -100,6 +100,23 @@ void orc_spmv_lowp(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
     }
 }
 
+/* The same product with FP32 arithmetic: x rounded to float once, every
+ * product accumulated by fmaf in column order, the row sum rounded to double
+ * (the compressed variant's FP32-accumulation mode).                          */
+void orc_spmv_lowp32(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                     int32_t vkind, const void *val, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        float s = 0.0f;
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+            float a = vkind == 1 ? ((const float *)val)[j]
+                                 : (float)bf16_to_double(((const uint16_t *)val)[j]);
+            s = fmaf(a, (float)x[colind[j]], s);
+        }
+        y[i] = (double)s;
+    }
+}
+
 /* IEEE round-to-nearest-even of a double to bfloat16 (8 significant bits,
  * float32 exponent range), done in one rounding step: scale by a power of two
  * so that one bfloat16 quantum becomes 1, round with nearbyint (ties to even

@@ -141,13 +141,17 @@ def spmv_select(features: Features | None = None, profile: Profile | None = None
     return out
 
 
+ACC_DEFAULT, ACC_F64, ACC_F32 = 0, 1, 2
+
+
 def make_choice(variant, threads_per_row=0, block_nnz=0, items_per_warp=0,
-                value_type=VAL_F64) -> Choice:
+                value_type=VAL_F64, accumulate=ACC_DEFAULT) -> Choice:
     v = VARIANT_IDS[variant] if isinstance(variant, str) else int(variant)
     c = Choice()
     c.variant, c.cls = v, -1
     c.threads_per_row, c.block_nnz, c.items_per_warp = threads_per_row, block_nnz, items_per_warp
     c.value_type = value_type
+    c.accumulate = accumulate
     return c
 
 

@@ -59,7 +59,7 @@ class Choice(C.Structure):
     _fields_ = [("variant", C.c_int32), ("cls", C.c_int32), ("threads_per_row", C.c_int32),
                 ("block_nnz", C.c_int32), ("items_per_warp", C.c_int32),
                 ("value_type", C.c_int32), ("margin", C.c_float), ("used_fallback", C.c_int32),
-                ("source", C.c_int32)]
+                ("source", C.c_int32), ("accumulate", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,7 +70,7 @@ class PreparedInfo(C.Structure):
                                          "items_per_warp", "value_type")] + \
         [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_blocks", "n_wide_rows",
                                   "owned_bytes", "min_bytes")] + \
-        [("tile_items", C.c_int32), ("bulk_copy", C.c_int32)]
+        [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

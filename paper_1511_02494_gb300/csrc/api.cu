@@ -126,7 +126,7 @@ void release(spmv_prepared_t* P)
 {
     void* ptrs[] = {P->blocks, P->merge_nz, P->carry_row, P->carry_val, P->counter,
                     P->rowbase, P->off16, P->lowval, P->x_stage, P->y_stage, P->status,
-                    P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial};
+                    P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -137,10 +137,12 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
     const int64_t vec = 8 * A.n_cols + 8 * A.n_rows + 4 * (A.n_rows + 1);
     if (P->c.variant != SPMV_V6_COMPRESSED) return 12 * A.nnz + vec;
     const int vb = P->c.value_type == SPMV_VAL_F64 ? 8 : P->c.value_type == SPMV_VAL_F32 ? 4 : 2;
-    if (P->off16 == nullptr) return (int64_t)(vb + 4) * A.nnz + vec;  // every row wide
+    // FP32 accumulation: x converted once (8 + 4 bytes per column), then read as float
+    const int64_t xconv = P->c.accumulate == 2 ? 4 * A.n_cols + 4 * A.n_cols : 0;
+    if (P->off16 == nullptr) return (int64_t)(vb + 4) * A.nnz + vec + xconv;  // every row wide
     // 2-byte offsets + a 4-byte rowbase per row (wide rows' 4-byte columns
     // counted at 2 bytes here: a lower bound for mixed matrices)
-    return (int64_t)(vb + 2) * A.nnz + 4 * A.n_rows + vec;
+    return (int64_t)(vb + 2) * A.nnz + 4 * A.n_rows + vec + xconv;
 }
 
 spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
@@ -215,6 +217,9 @@ spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
         }
         case SPMV_V6_COMPRESSED: {
             if (c.threads_per_row == 0) c.threads_per_row = auto_threads_per_row(mean / 7.0);
+            if (c.accumulate == 0) c.accumulate = c.value_type == SPMV_VAL_F64 ? 1 : 2;
+            if (c.accumulate == 2 && (st = dev_alloc(P, &P->x32, std::max<int64_t>(A.n_cols, 1))) != SPMV_OK)
+                return st;
             if ((st = dev_alloc(P, &P->rowbase, A.n_rows)) != SPMV_OK) return st;
             unsigned long long* d_wide = nullptr;
             SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_wide), 8, s));
@@ -276,6 +281,10 @@ spmv_status check_choice(const spmv_choice_t* c)
         return fail(SPMV_ERR_INVALID_ARG, "value_type out of range");
     if (c->value_type != SPMV_VAL_F64 && c->variant != SPMV_V6_COMPRESSED)
         return fail(SPMV_ERR_UNSUPPORTED, "low-precision values only in the COMPRESSED variant");
+    if (c->accumulate < 0 || c->accumulate > 2)
+        return fail(SPMV_ERR_INVALID_ARG, "accumulate must be 0 (by value type), 1 (FP64) or 2 (FP32)");
+    if (c->accumulate == 2 && (c->variant != SPMV_V6_COMPRESSED || c->value_type == SPMV_VAL_F64))
+        return fail(SPMV_ERR_UNSUPPORTED, "FP32 accumulation needs COMPRESSED with FP32 or BF16 values");
     return SPMV_OK;
 }
 
@@ -307,8 +316,12 @@ spmv_status run_impl(const spmv_prepared_t* P, const double* x, double* y, cudaS
             e = launch_latency(A, c.threads_per_row, x, y, P->l2_window_bytes, s);
             break;
         case SPMV_V6_COMPRESSED:
-            e = launch_compressed(A, c.threads_per_row, c.value_type, P->rowbase, P->off16,
-                                  P->lowval, P->off16 == nullptr, x, y, s);
+            if (c.accumulate == 2)
+                e = launch_compressed32(A, c.threads_per_row, c.value_type, P->rowbase, P->off16,
+                                        P->lowval, P->off16 == nullptr, x, P->x32, y, s);
+            else
+                e = launch_compressed(A, c.threads_per_row, c.value_type, P->rowbase, P->off16,
+                                      P->lowval, P->off16 == nullptr, x, y, s);
             break;
         default: return fail(SPMV_ERR_INVALID_ARG, "unknown variant");
     }
@@ -530,6 +543,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.min_bytes = min_bytes_of(P);
     i.tile_items = P->tile_items;
     i.bulk_copy = P->bulk ? 1 : 0;
+    i.accumulate = P->c.variant == SPMV_V6_COMPRESSED ? P->c.accumulate : 1;
     *info = i;
     return SPMV_OK;
 }

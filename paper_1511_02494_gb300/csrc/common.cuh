@@ -77,6 +77,7 @@ struct spmv_prepared {
     bool bulk = false;             // STREAM / MERGE: pipelined bulk-copy kernel in use
     unsigned* status = nullptr;    // device status word (bounded-wait timeouts)
     DynPlan dyn;
+    float* x32 = nullptr;          // COMPRESSED with FP32 accumulation: FP32 copy of x
 };
 
 namespace spmvlib {
@@ -110,6 +111,9 @@ cudaError_t launch_latency(const spmv_csr_t& A, int T, const double* x, double* 
 cudaError_t launch_compress(const spmv_csr_t& A, int32_t* rowbase, uint16_t* off16,
                             unsigned long long* n_wide, int value_type, void* lowval,
                             cudaStream_t s);
+cudaError_t launch_compressed32(const spmv_csr_t& A, int T, int value_type, const int32_t* rowbase,
+                                const uint16_t* off16, const void* lowval, bool all_wide,
+                                const double* x, float* x32, double* y, cudaStream_t s);
 cudaError_t launch_compressed(const spmv_csr_t& A, int T, int value_type,
                               const int32_t* rowbase, const uint16_t* off16,
                               const void* lowval, bool all_wide, const double* x, double* y,

@@ -94,5 +94,40 @@ __device__ __forceinline__ double row_partial(int64_t b, int64_t e, int lane, co
     return acc;
 }
 
+// FP32 form for low-precision values: x comes from an FP32 copy, products
+// and sums are FP32 FMAs (the FP32 pipe is ~60x wider than FP64's on this
+// GPU), so the row costs no FP64 instruction at all.
+__device__ __forceinline__ float ldval32(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldval32(const __nv_bfloat16* p) {
+    const unsigned short b = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(((unsigned)b) << 16);
+}
+
+template <int T, int U, typename COL, typename VT>
+__device__ __forceinline__ float row_partial32(int64_t b, int64_t e, int lane, const COL& col,
+                                               const VT* __restrict__ v,
+                                               const float* __restrict__ x)
+{
+    float acc = 0.f;
+    int64_t j = b + lane;
+    for (; j + (int64_t)(U - 1) * T < e; j += (int64_t)U * T) {
+        int64_t c[U];
+        float a[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { c[u] = col(j + u * T); a[u] = ldval32(v + j + u * T); }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc = fmaf(a[u], xv[u], acc);
+    }
+    for (; j < e; j += T) acc = fmaf(ldval32(v + j), __ldg(x + col(j)), acc);
+    return acc;
+}
+
+__device__ __forceinline__ float group_sum32(float s, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    return s;
+}
+
 }  // namespace dev
 }  // namespace spmvlib

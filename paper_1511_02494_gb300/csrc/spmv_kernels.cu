@@ -362,6 +362,37 @@ k_compressed(int64_t n_rows, const int* __restrict__ rp, const int32_t* __restri
     if (lane == 0 && row < n_rows) y[row] = s;
 }
 
+// FP32-accumulation form of the compressed variant
+__global__ void k_x_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ x32)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x32[i] = __double2float_rn(x[i]);
+}
+
+template <int T, typename VT, bool ALL_WIDE>
+__global__ void __launch_bounds__(kBlock)
+k_compressed32(int64_t n_rows, const int* __restrict__ rp, const int32_t* __restrict__ rowbase,
+               const uint16_t* __restrict__ off, const int* __restrict__ ci,
+               const VT* __restrict__ v, const float* __restrict__ x32, double* __restrict__ y)
+{
+    const int64_t row = (int64_t)blockIdx.x * (kBlock / T) + threadIdx.x / T;
+    const int lane = threadIdx.x & (T - 1);
+    int64_t b = 0, e = 0;
+    int base = -1;
+    if (row < n_rows) {
+        b = rp[row];
+        e = rp[row + 1];
+        if (!ALL_WIDE) base = rowbase[row];
+    }
+    float p;
+    if (ALL_WIDE || base < 0)
+        p = row_partial32<T, 4>(b, e, lane, ColPlain<int>{ci}, v, x32);
+    else
+        p = row_partial32<T, 4>(b, e, lane, ColOff16{off, base}, v, x32);
+    const float s = group_sum32(p, T);
+    if (lane == 0 && row < n_rows) y[row] = (double)s;
+}
+
 inline unsigned grid_for(int64_t threads) {
     return (unsigned)((threads + kBlock - 1) / kBlock);
 }
@@ -540,6 +571,43 @@ cudaError_t launch_compressed(const spmv_csr_t& A, int T, int value_type, const 
     }
 #undef SPMV_CMP_T
 #undef SPMV_CMP_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compressed32(const spmv_csr_t& A, int T, int value_type, const int32_t* rowbase,
+                                const uint16_t* off16, const void* lowval, bool all_wide,
+                                const double* x, float* x32, double* y, cudaStream_t s)
+{
+    if (A.n_rows == 0) return cudaSuccess;
+    if (A.n_cols > 0) {
+        k_x_to_f32<<<grid_for(A.n_cols), kBlock, 0, s>>>(A.n_cols, x, x32);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned grid = grid_for(A.n_rows * (int64_t)T);
+    const int64_t n = A.n_rows;
+#define SPMV_C32_LAUNCH(TT, VT, AW)                                                            \
+    k_compressed32<TT, VT, AW><<<grid, kBlock, 0, s>>>(n, A.rowptr, rowbase, off16, A.colind,  \
+                                                       static_cast<const VT*>(lowval), x32, y)
+#define SPMV_C32_T(VT, AW)                                   \
+    switch (T) {                                             \
+        case 1: SPMV_C32_LAUNCH(1, VT, AW); break;           \
+        case 2: SPMV_C32_LAUNCH(2, VT, AW); break;           \
+        case 4: SPMV_C32_LAUNCH(4, VT, AW); break;           \
+        case 8: SPMV_C32_LAUNCH(8, VT, AW); break;           \
+        case 16: SPMV_C32_LAUNCH(16, VT, AW); break;         \
+        case 32: SPMV_C32_LAUNCH(32, VT, AW); break;         \
+        default: return cudaErrorInvalidValue;               \
+    }
+    if (value_type == SPMV_VAL_F32) {
+        if (all_wide) { SPMV_C32_T(float, true) } else { SPMV_C32_T(float, false) }
+    } else if (value_type == SPMV_VAL_BF16) {
+        if (all_wide) { SPMV_C32_T(__nv_bfloat16, true) } else { SPMV_C32_T(__nv_bfloat16, false) }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef SPMV_C32_T
+#undef SPMV_C32_LAUNCH
     return cudaGetLastError();
 }
 

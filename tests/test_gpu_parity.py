@@ -325,12 +325,83 @@ def test_compressed_value_rounding_bit_exact():
 @pytest.mark.parametrize("vt", [sp.VAL_F32, sp.VAL_BF16])
 @pytest.mark.parametrize("name,A", [MATS[0], MATS[2], MATS[6]], ids=["laplacian", "zipf", "wide"])
 def test_compressed_low_precision_parity(vt, name, A):
+    """FP64 accumulation of the rounded values: within the FP64 bound."""
     lowval = oracle.round_f32(A.val) if vt == sp.VAL_F32 else oracle.round_bf16(A.val)
-    y, x = _run(A, sp.make_choice("compressed", value_type=vt))
+    P_choice = sp.make_choice("compressed", value_type=vt, accumulate=sp.ACC_F64)
+    y, x = _run(A, P_choice)
     ref = oracle.spmv_lowp(A, x, 1 if vt == sp.VAL_F32 else 2, lowval)
     _, scale = oracle.spmv_ref(A, x)
     err = np.abs(y.cpu().numpy() - ref)
     assert np.all(err <= RTOL * scale * 1.01)
+
+
+def _lowp32_bound(A, x, lowval, vkind):
+    """Two FP32 sums of the same rounded products in different orders
+    differ by at most 2 * gamma_(n+5) * sum |a_j x_j| with u = 2^-24
+    (n = row length; the 5 covers the lane-shuffle levels)."""
+    rp = A.rowptr.numpy().astype(np.int64)
+    a = np.abs(lowval.astype(np.float64) if vkind == 1
+               else (lowval.astype(np.uint32) << 16).view(np.float32).astype(np.float64))
+    xf = np.abs(x.cpu().numpy().astype(np.float32).astype(np.float64))
+    prod = a * xf[A.colind.numpy()]
+    s = np.add.reduceat(np.concatenate([prod, [0.0]]), np.minimum(rp[:-1], A.nnz))
+    s[rp[1:] == rp[:-1]] = 0.0
+    n = (rp[1:] - rp[:-1]).astype(np.float64) + 5
+    u = 2.0 ** -24
+    return 2 * (n * u / (1 - n * u)) * s
+
+
+@pytest.mark.parametrize("vt", [sp.VAL_F32, sp.VAL_BF16])
+@pytest.mark.parametrize("tpr", [0, 1, 8, 32])
+@pytest.mark.parametrize("name,A", [MATS[0], MATS[2], MATS[6]], ids=["laplacian", "zipf", "wide"])
+def test_compressed_fp32_accumulation_parity(vt, tpr, name, A):
+    """FP32 accumulation (the default for FP32/BF16 values) against the
+    oracle's FP32 form: same rounded x and values, FP32 fused multiply-adds,
+    equal up to summation order."""
+    vkind = 1 if vt == sp.VAL_F32 else 2
+    lowval = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt, threads_per_row=tpr))
+    assert P.info().accumulate == sp.ACC_F32
+    x = synth.uniform_vector(A.n_cols, 11).cuda()
+    y = torch.full((A.n_rows,), np.nan, dtype=torch.float64, device="cuda")
+    sp.spmv(P, x, y)
+    sp.spmv(P, x, y)  # the FP32 copy of x is rewritten each call
+    ref = oracle.spmv_lowp32(A, x.cpu(), vkind, lowval)
+    err = np.abs(y.cpu().numpy() - ref)
+    bound = _lowp32_bound(A, x, lowval, vkind)
+    assert np.all(err <= bound), float(np.max(err - bound))
+    # outputs are FP32 values widened to FP64
+    yn = y.cpu().numpy()
+    assert np.array_equal(yn, yn.astype(np.float32).astype(np.float64))
+
+
+def test_compressed_fp32_accumulation_exact_on_small_integers():
+    A = synth.random_csr(3000, 2000, 12, seed=21)
+    g = np.random.default_rng(4)
+    A.val = torch.from_numpy(g.integers(-8, 9, A.nnz).astype(np.float64))
+    x = torch.from_numpy(g.integers(-16, 17, A.n_cols).astype(np.float64))
+    dA = sp.DeviceCSR.from_host(A)
+    for vt, vkind in ((sp.VAL_F32, 1), (sp.VAL_BF16, 2)):
+        lowval = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
+        P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt))
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        sp.spmv(P, x.cuda(), y)
+        assert np.array_equal(y.cpu().numpy(), oracle.spmv_lowp32(A, x, vkind, lowval))
+        assert np.array_equal(y.cpu().numpy(), oracle.spmv(A, x))
+
+
+def test_accumulate_choice_validation():
+    A = synth.laplacian_2d_5pt(20)
+    dA = sp.DeviceCSR.from_host(A)
+    assert sp.spmv_prepare(dA, sp.make_choice("compressed")).info().accumulate == sp.ACC_F64
+    assert sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=sp.VAL_F32,
+                                              accumulate=sp.ACC_F64)).info().accumulate == sp.ACC_F64
+    for bad in (sp.make_choice("compressed", accumulate=sp.ACC_F32),
+                sp.make_choice("subwarp", accumulate=sp.ACC_F32),
+                sp.make_choice("compressed", value_type=sp.VAL_BF16, accumulate=3)):
+        with pytest.raises(sp.SpmvError):
+            sp.spmv_prepare(dA, bad)
 
 
 # ----------------------------------------------------------------- profile + select

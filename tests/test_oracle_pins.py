@@ -126,6 +126,24 @@ def test_spmv_lowp_equals_fp64_on_representable_values():
     assert np.array_equal(oracle.spmv_lowp(A, x, 2, oracle.round_bf16(A.val)), ref)
 
 
+def test_spmv_lowp32_exact_on_small_integers_and_bounded_otherwise():
+    A = synth.random_csr(80, 60, 20, seed=4)
+    g = np.random.default_rng(4)
+    # values and x with few bits: every float operation is exact
+    A.val = torch.from_numpy(g.integers(-16, 17, A.nnz).astype(np.float64))
+    x = g.integers(-16, 17, 60).astype(np.float64)
+    assert np.array_equal(oracle.spmv_lowp32(A, x, 1, oracle.round_f32(A.val)), oracle.spmv(A, x))
+    # general values: within the FP32 rounding bound of the float-valued product
+    A.val = torch.from_numpy(g.standard_normal(A.nnz))
+    xr = synth.uniform_vector(60, 6)
+    low = oracle.round_bf16(A.val)
+    exact = oracle.spmv_lowp(A, oracle.round_f32(xr).astype(np.float64), 2, low)
+    _, scale = oracle.spmv_ref(A, xr)
+    k = np.diff(A.rowptr.numpy())
+    got = oracle.spmv_lowp32(A, xr, 2, low)
+    assert np.all(np.abs(got - exact) <= (k + 1) * 2.0 ** -23 * scale * 1.01 + 1e-300)
+
+
 # --------------------------------------------------------------- rounding
 def test_bf16_rounding_golden(golden_dir):
     d = json.load(open(os.path.join(golden_dir, "bf16_rounding.json")))
