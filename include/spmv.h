@@ -305,6 +305,17 @@ spmv_status spmv_mlp_loss_grad(const float *params, int32_t h1, int32_t h2, int3
                                const float *z, const int32_t *labels, int32_t n, float *grad,
                                float *loss, spmv_stream_t stream);
 
+/* The same loss against a target distribution per sample: q (device,
+ * [n][k] float) replaces the labels; loss = mean over samples of
+ * -sum_o q_o log softmax(logits)_o.  With q = exp(-beta * log(t_o / t_best))
+ * normalised (t_o: measured time of variant o) the loss is cost-sensitive:
+ * a slightly slower variant is a small error, a much slower one a large one.
+ * Rows of q need not sum to 1 (the gradient is exact for any non-negative
+ * weights).  Otherwise as spmv_mlp_loss_grad. */
+spmv_status spmv_mlp_loss_grad_soft(const float *params, int32_t h1, int32_t h2, int32_t k,
+                                    const float *z, const float *q, int32_t n, float *grad,
+                                    float *loss, spmv_stream_t stream);
+
 /* One Adam step on n device floats (step counts from 1):
  *   m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
  *   p -= lr (m/c1 / (sqrt(v/c2) + eps) + weight_decay p),

@@ -86,6 +86,7 @@ def _load():
                 "orc_mlp_forward_f32": (None, [i32, i32, i32] + [P] * 10),
                 "orc_argmax": (i32, [i32, P, P]),
                 "orc_mlp_loss_grad_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
+                "orc_mlp_loss_grad_soft_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -264,6 +265,20 @@ def mlp_loss_grad_f64(params: dict, z, labels):
     loss = _load().orc_mlp_loss_grad_f64(
         h1, h2, k, z.shape[0], *[_p(P64[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")],
         _p(z), _p(lab), *[_p(G[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    return float(loss), G
+
+
+def mlp_loss_grad_soft_f64(params: dict, z, q):
+    """FP64 mean cross-entropy against per-sample target distributions
+    q (batch x K) and its gradients."""
+    P64 = {n: _np(params[n], np.float64) for n in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    h1, h2, k = P64["W1"].shape[0], P64["W2"].shape[0], P64["W3"].shape[0]
+    z = _np(z, np.float64).reshape(-1, 16)
+    q = _np(q, np.float64).reshape(z.shape[0], k)
+    G = {n: np.empty_like(a) for n, a in P64.items()}
+    loss = _load().orc_mlp_loss_grad_soft_f64(
+        h1, h2, k, z.shape[0], *[_p(P64[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")],
+        _p(z), _p(q), *[_p(G[n]) for n in ("W1", "b1", "W2", "b2", "W3", "b3")])
     return float(loss), G
 
 

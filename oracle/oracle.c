@@ -422,12 +422,17 @@ int32_t orc_argmax(int32_t k, const float *logits, float *margin)
  * given standardized inputs z[B][16] and labels.  Gradients are written to
  * g* (same layouts as the weights); returns the loss.  Textbook
  * backpropagation, written out loop by loop.                                  */
-double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
-                             const double *W1, const double *b1, const double *W2,
-                             const double *b2, const double *W3, const double *b3,
-                             const double *z, const int32_t *label,
-                             double *gW1, double *gb1, double *gW2, double *gb2,
-                             double *gW3, double *gb3)
+/* Shared by the hard-label and soft-target forms: with q == NULL the target
+ * of sample s is the one-hot vector of label[s]; otherwise it is the row
+ * q[s*k .. s*k+k-1].  Loss per sample: -sum_o q_o log p_o with p = softmax
+ * of the logits; its derivative with respect to logit o is p_o * S - q_o,
+ * S = sum_o q_o (S = 1 for a distribution). */
+static double mlp_loss_grad(int32_t h1, int32_t h2, int32_t k, int32_t batch,
+                            const double *W1, const double *b1, const double *W2,
+                            const double *b2, const double *W3, const double *b3,
+                            const double *z, const int32_t *label, const double *q,
+                            double *gW1, double *gb1, double *gW2, double *gb2,
+                            double *gW3, double *gb3)
 {
     memset(gW1, 0, sizeof(double) * h1 * 16); memset(gb1, 0, sizeof(double) * h1);
     memset(gW2, 0, sizeof(double) * h2 * h1); memset(gb2, 0, sizeof(double) * h2);
@@ -454,11 +459,16 @@ double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
             if (acc > mx) mx = acc;
         }
         double den = 0.0;
-        for (int o = 0; o < k; ++o) { p[o] = exp(p[o] - mx); den += p[o]; }
-        for (int o = 0; o < k; ++o) p[o] /= den;
-        loss += -log(p[label[s]]);
-        /* dL/dlogit = (p - onehot) / B */
-        for (int o = 0; o < k; ++o) p[o] = (p[o] - (o == label[s] ? 1.0 : 0.0)) / batch;
+        for (int o = 0; o < k; ++o) den += exp(p[o] - mx);
+        const double lse = mx + log(den);  /* log sum_o exp(logit_o) */
+        double tq[256], S = 0.0;
+        for (int o = 0; o < k; ++o) {
+            tq[o] = q ? q[(int64_t)s * k + o] : (o == label[s] ? 1.0 : 0.0);
+            S += tq[o];
+        }
+        for (int o = 0; o < k; ++o) loss += -tq[o] * (p[o] - lse);  /* log p_o = logit_o - lse */
+        /* dL/dlogit = (p S - q) / B */
+        for (int o = 0; o < k; ++o) p[o] = (exp(p[o] - lse) * S - tq[o]) / batch;
         for (int i = 0; i < h2; ++i) d2[i] = 0.0;
         for (int o = 0; o < k; ++o) {
             gb3[o] += p[o];
@@ -477,6 +487,32 @@ double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
         }
     }
     return loss / batch;
+}
+
+/* Mean softmax cross-entropy over a batch with integer labels and its
+ * gradient by backpropagation, in FP64. */
+double orc_mlp_loss_grad_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
+                             const double *W1, const double *b1, const double *W2,
+                             const double *b2, const double *W3, const double *b3,
+                             const double *z, const int32_t *label,
+                             double *gW1, double *gb1, double *gW2, double *gb2,
+                             double *gW3, double *gb3)
+{
+    return mlp_loss_grad(h1, h2, k, batch, W1, b1, W2, b2, W3, b3, z, label, NULL,
+                         gW1, gb1, gW2, gb2, gW3, gb3);
+}
+
+/* The same with a target distribution per sample (q: batch x k, row-major):
+ * cross-entropy against soft targets, used to make training cost-sensitive. */
+double orc_mlp_loss_grad_soft_f64(int32_t h1, int32_t h2, int32_t k, int32_t batch,
+                                  const double *W1, const double *b1, const double *W2,
+                                  const double *b2, const double *W3, const double *b3,
+                                  const double *z, const double *q,
+                                  double *gW1, double *gb1, double *gW2, double *gb2,
+                                  double *gW3, double *gb3)
+{
+    return mlp_loss_grad(h1, h2, k, batch, W1, b1, W2, b2, W3, b3, z, NULL, q,
+                         gW1, gb1, gW2, gb2, gW3, gb3);
 }
 
 /* One Adam step in float, each operation rounded as written:

@@ -363,6 +363,12 @@ def spmv_mlp_loss_grad(params, h1, h2, k, z, labels, grad, loss, stream=None) ->
                                     int(z.shape[0]), _ptr(grad), _ptr(loss), _stream(stream)))
 
 
+def spmv_mlp_loss_grad_soft(params, h1, h2, k, z, q, grad, loss, stream=None) -> None:
+    """Cross-entropy against per-sample target distributions q ([n][k] float32)."""
+    _check(lib().spmv_mlp_loss_grad_soft(_ptr(params), h1, h2, k, _ptr(z), _ptr(q),
+                                         int(z.shape[0]), _ptr(grad), _ptr(loss), _stream(stream)))
+
+
 def spmv_mlp_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                   weight_decay=0.0, stream=None) -> None:
     _check(lib().spmv_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),

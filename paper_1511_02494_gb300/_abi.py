@@ -113,6 +113,7 @@ def declare(lib):
                                     C.POINTER(Thresholds), C.POINTER(Choice)]),
         "spmv_mlp_forward": (I32, [P, P, P, I32, I32, I32, P, I32, P, P]),
         "spmv_mlp_loss_grad": (I32, [P, I32, I32, I32, P, P, I32, P, P, P]),
+        "spmv_mlp_loss_grad_soft": (I32, [P, I32, I32, I32, P, P, I32, P, P, P]),
         "spmv_mlp_adam": (I32, [P, P, P, P, I64, I32, C.c_float, C.c_float, C.c_float,
                                 C.c_float, C.c_float, P]),
         "spmv_prepared_free": (None, [P]),

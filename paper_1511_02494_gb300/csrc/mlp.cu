@@ -133,8 +133,9 @@ struct __align__(16) TrainSmem {
 
 __global__ void __launch_bounds__(kMT)
 k_mlp_loss_grad(const float* __restrict__ params, int h1, int h2, int k,
-                const float* __restrict__ z, const int32_t* __restrict__ labels, int n,
-                float* __restrict__ part, float* __restrict__ part_loss)
+                const float* __restrict__ z, const int32_t* __restrict__ labels,
+                const float* __restrict__ q, int n, float* __restrict__ part,
+                float* __restrict__ part_loss)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -165,18 +166,35 @@ k_mlp_loss_grad(const float* __restrict__ params, int h1, int h2, int k,
         sm.d3[s][o] = acc;  // logits for now
     }
     __syncthreads();
-    // softmax cross-entropy per sample; d3 = (p - onehot) / n
+    // softmax cross-entropy per sample; d3 = (p - onehot) / n, or with a
+    // target distribution q: loss = -sum q_o log p_o, d3 = (p S - q) / n
+    // where S = sum q_o
     if (tid < ns) {
         const int s = tid;
         float mx = -INFINITY;
         for (int o = 0; o < k; ++o) mx = fmaxf(mx, sm.d3[s][o]);
         float den = 0.f;
         for (int o = 0; o < k; ++o) den += expf(sm.d3[s][o] - mx);
-        const int y = labels[s0 + s];
-        sm.loss[s] = -(sm.d3[s][y] - mx - logf(den));
-        for (int o = 0; o < k; ++o) {
-            const float p = expf(sm.d3[s][o] - mx) / den;
-            sm.d3[s][o] = (p - (o == y ? 1.f : 0.f)) / (float)n;
+        if (q == nullptr) {
+            const int y = labels[s0 + s];
+            sm.loss[s] = -(sm.d3[s][y] - mx - logf(den));
+            for (int o = 0; o < k; ++o) {
+                const float p = expf(sm.d3[s][o] - mx) / den;
+                sm.d3[s][o] = (p - (o == y ? 1.f : 0.f)) / (float)n;
+            }
+        } else {
+            const float* qs = q + (int64_t)(s0 + s) * k;
+            const float lse = mx + logf(den);
+            float S = 0.f, l = 0.f;
+            for (int o = 0; o < k; ++o) {
+                S += qs[o];
+                l -= qs[o] * (sm.d3[s][o] - lse);
+            }
+            sm.loss[s] = l;
+            for (int o = 0; o < k; ++o) {
+                const float p = expf(sm.d3[s][o] - lse);
+                sm.d3[s][o] = (p * S - qs[o]) / (float)n;
+            }
         }
     }
     __syncthreads();
@@ -425,14 +443,15 @@ spmv_status spmv_mlp_forward(const float* params, const float* mean, const float
     return SPMV_OK;
 }
 
-spmv_status spmv_mlp_loss_grad(const float* params, int32_t h1, int32_t h2, int32_t k,
-                               const float* z, const int32_t* labels, int32_t n, float* grad,
-                               float* loss, spmv_stream_t stream)
+namespace {
+spmv_status loss_grad_impl(const float* params, int32_t h1, int32_t h2, int32_t k,
+                           const float* z, const int32_t* labels, const float* q, int32_t n,
+                           float* grad, float* loss, spmv_stream_t stream)
 {
     clear_error();
     if (!shape_ok(h1, h2, k, kTrainMaxH) || n <= 0)
         return fail(SPMV_ERR_INVALID_ARG, "bad MLP training shape (hidden <= 128, k <= 32)");
-    if (!params || !z || !labels || !grad || !loss)
+    if (!params || !z || (!labels && !q) || !grad || !loss)
         return fail(SPMV_ERR_INVALID_ARG, "spmv_mlp_loss_grad: NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int parts = (n + kSlice - 1) / kSlice;
@@ -444,7 +463,7 @@ spmv_status spmv_mlp_loss_grad(const float* params, int32_t h1, int32_t h2, int3
     cudaError_t e = cudaFuncSetAttribute(k_mlp_loss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) {
-        k_mlp_loss_grad<<<parts, kMT, smem, s>>>(params, h1, h2, k, z, labels, n, part,
+        k_mlp_loss_grad<<<parts, kMT, smem, s>>>(params, h1, h2, k, z, labels, q, n, part,
                                                  part + (size_t)parts * P);
         e = cudaGetLastError();
     }
@@ -457,6 +476,29 @@ spmv_status spmv_mlp_loss_grad(const float* params, int32_t h1, int32_t h2, int3
     if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) return cuda_fail(e, "spmv_mlp_loss_grad");
     return SPMV_OK;
+}
+}  // namespace
+
+spmv_status spmv_mlp_loss_grad(const float* params, int32_t h1, int32_t h2, int32_t k,
+                               const float* z, const int32_t* labels, int32_t n, float* grad,
+                               float* loss, spmv_stream_t stream)
+{
+    if (!labels) {
+        clear_error();
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_mlp_loss_grad: NULL argument");
+    }
+    return loss_grad_impl(params, h1, h2, k, z, labels, nullptr, n, grad, loss, stream);
+}
+
+spmv_status spmv_mlp_loss_grad_soft(const float* params, int32_t h1, int32_t h2, int32_t k,
+                                    const float* z, const float* q, int32_t n, float* grad,
+                                    float* loss, spmv_stream_t stream)
+{
+    if (!q) {
+        clear_error();
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_mlp_loss_grad_soft: NULL argument");
+    }
+    return loss_grad_impl(params, h1, h2, k, z, nullptr, q, n, grad, loss, stream);
 }
 
 spmv_status spmv_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t n,

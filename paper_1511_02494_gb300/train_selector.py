@@ -11,8 +11,10 @@ labels with its profiling classifier).  For every matrix it records the
 their rule's choice, and the cost of feature extraction and profiling.
 
 Training: a 16-64-64-K ReLU network, full-batch Adam on the GPU
-(spmv_mlp_loss_grad + spmv_mlp_adam), 80/20 split by seed.  The fallback
-margin is chosen on the training split.  Outputs (in --out):
+(spmv_mlp_loss_grad_soft + spmv_mlp_adam), 80/20 split by seed.  Targets are
+cost-sensitive distributions over the variants built from the measured times
+(soft_targets); their sharpness beta is picked on a validation quarter of
+the training split.  The fallback margin is chosen on the training split.  Outputs (in --out):
 selector_dataset.npz, selector_mlp.bin, selector_report.json.
 
     python -m paper_1511_02494_gb300.train_selector --out DIR [--n 2000]
@@ -126,19 +128,36 @@ def init_params(h1, h2, k, seed=0):
     return np.concatenate(parts)
 
 
-def train(z: np.ndarray, labels: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000, lr=3e-3,
+def soft_targets(times: np.ndarray, beta: float) -> np.ndarray:
+    """Cost-sensitive targets: q_v proportional to (t_best / t_v)^beta, so a
+    variant 5 % slower than the best keeps weight 1.05^-beta and a variant
+    twice as slow almost none.  beta = inf gives the one-hot best label."""
+    r = times / times.min(1, keepdims=True)
+    if not np.isfinite(beta):
+        q = (r == 1.0).astype(np.float64)
+    else:
+        q = r ** -beta
+    return (q / q.sum(1, keepdims=True)).astype(np.float32)
+
+
+def train(z: np.ndarray, targets: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000, lr=3e-3,
           wd=1e-4, seed=0, log=print):
-    """Full-batch Adam with the library's loss/gradient and Adam kernels."""
+    """Full-batch Adam with the library's loss/gradient and Adam kernels;
+    targets are integer labels [n] or target distributions [n][k]."""
     p = torch.from_numpy(init_params(h1, h2, k, seed)).cuda()
     g = torch.zeros_like(p)
     m = torch.zeros_like(p)
     v = torch.zeros_like(p)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     dz = torch.from_numpy(np.ascontiguousarray(z, np.float32)).cuda()
-    dl = torch.from_numpy(np.ascontiguousarray(labels, np.int32)).cuda()
+    soft = targets.ndim == 2
+    dl = torch.from_numpy(np.ascontiguousarray(targets, np.float32 if soft else np.int32)).cuda()
     hist = []
     for step in range(1, steps + 1):
-        sp.spmv_mlp_loss_grad(p, h1, h2, k, dz, dl, g, loss)
+        if soft:
+            sp.spmv_mlp_loss_grad_soft(p, h1, h2, k, dz, dl, g, loss)
+        else:
+            sp.spmv_mlp_loss_grad(p, h1, h2, k, dz, dl, g, loss)
         sp.spmv_mlp_adam(p, g, m, v, step, lr=lr, weight_decay=wd)
         if step % 500 == 0 or step == 1:
             hist.append((step, float(loss.item())))
@@ -207,6 +226,7 @@ def main():
     ap.add_argument("--n", type=int, default=2000)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--no-resume", action="store_true")
+    ap.add_argument("--betas", type=float, nargs="+", default=[2.0, 4.0, 8.0, 16.0, 32.0, math.inf])
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     from paper_1511_02494_gb300.build import build
@@ -221,9 +241,25 @@ def main():
     sd = vec[tr].std(0)
     istd = np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 0.0).astype(np.float32)
     z = ((vec - mean) * istd).astype(np.float32)
-    labels = d["times"].argmin(1).astype(np.int32)
     h1, h2, k = 64, 64, N_VAR
-    params, hist = train(z[tr], labels[tr], h1, h2, k, steps=args.steps)
+    # beta of the cost-sensitive targets, chosen on a validation part of the
+    # training split (seed % 5 == 4), then the network is trained on all of it
+    fit = np.where((seeds % 5 != 0) & (seeds % 5 != 4))[0]
+    val = np.where(seeds % 5 == 4)[0]
+    mean_f = vec[fit].mean(0).astype(np.float32)
+    sd_f = vec[fit].std(0)
+    istd_f = np.where(sd_f > 1e-6, 1.0 / np.maximum(sd_f, 1e-6), 0.0).astype(np.float32)
+    z_f = ((vec - mean_f) * istd_f).astype(np.float32)
+    beta_scores = {}
+    for beta in args.betas:
+        pf, _ = train(z_f[fit], soft_targets(d["times"][fit], beta), h1, h2, k, steps=args.steps,
+                      log=lambda *_: None)
+        lg = logits_of(pf, mean_f, istd_f, vec[val], h1, h2, k)
+        t_val = d["times"][val]
+        beta_scores[str(beta)] = geomean(t_val[np.arange(len(val)), lg.argmax(1)] / t_val.min(1))
+        print(f"beta {beta}: validation slowdown {beta_scores[str(beta)]:.4f}", flush=True)
+    beta = float(min(args.betas, key=lambda b_: beta_scores[str(b_)]))
+    params, hist = train(z[tr], soft_targets(d["times"][tr], beta), h1, h2, k, steps=args.steps)
     # fallback margin: smallest value whose training slowdown is within 0.5 %
     # of the best any margin achieves
     lg = logits_of(params, mean, istd, vec[tr], h1, h2, k)
@@ -240,6 +276,7 @@ def main():
     report = {"train": evaluate(d, params, mean, istd, mu, h1, h2, k, tr),
               "test": evaluate(d, params, mean, istd, mu, h1, h2, k, test),
               "min_margin": mu, "loss_history": hist, "variants": list(sp.VARIANTS),
+              "beta": beta, "beta_validation_slowdown": beta_scores,
               "network": [16, h1, h2, k]}
     with open(os.path.join(args.out, "selector_report.json"), "w") as f:
         json.dump(report, f, indent=1)

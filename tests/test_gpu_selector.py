@@ -72,6 +72,26 @@ def test_loss_and_gradient_against_fp64_oracle(n):
     assert torch.equal(grad, grad2)
 
 
+def test_soft_target_loss_grad_matches_oracle():
+    P = _params(64, 64, 7, seed=3)
+    g = np.random.default_rng(12)
+    n, k = 203, 7
+    z = g.standard_normal((n, 16)).astype(np.float32)
+    t = np.exp(g.standard_normal((n, k)))
+    q = (t.min(1, keepdims=True) / t) ** 8
+    q = (q / q.sum(1, keepdims=True)).astype(np.float32)
+    grad = torch.empty(_packed(P).numel(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    sp.spmv_mlp_loss_grad_soft(_packed(P), 64, 64, k, torch.from_numpy(z).cuda(),
+                               torch.from_numpy(q).cuda(), grad, loss)
+    torch.cuda.synchronize()
+    ref_loss, G = oracle.mlp_loss_grad_soft_f64({n_: P[n_].astype(np.float64) for n_ in P}, z, q)
+    ref = np.concatenate([G[n_].reshape(-1) for n_ in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    got = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
 def test_adam_bit_exact():
     g = np.random.default_rng(5)
     n = 5703

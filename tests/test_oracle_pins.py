@@ -448,6 +448,50 @@ def test_mlp_gradients_match_finite_differences():
     assert l0 == pytest.approx(math.log(5), rel=1e-15)
 
 
+def test_mlp_soft_target_gradients_match_finite_differences():
+    P = _params(16, 10, 6, 4)
+    g = np.random.default_rng(8)
+    z = g.standard_normal((7, 16))
+    q = g.random((7, 6))
+    q[:3] /= q[:3].sum(1, keepdims=True)  # distributions and unnormalised weights
+    P64 = {k: v.astype(np.float64) for k, v in P.items()}
+    loss, G = oracle.mlp_loss_grad_soft_f64(P64, z, q)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = P64[name].reshape(-1)
+        for idx in g.choice(flat.size, min(12, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = oracle.mlp_loss_grad_soft_f64(P64, z, q)
+            flat[idx] = old - h
+            lm, _ = oracle.mlp_loss_grad_soft_f64(P64, z, q)
+            flat[idx] = old
+            assert G[name].reshape(-1)[idx] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-8)
+
+
+def test_mlp_soft_targets_closed_forms():
+    """All-zero network: every logit is 0, p = 1/K, so the loss is
+    log K * mean(sum q) and dL/db3 = mean(sum(q)/K - q).  One-hot targets
+    reproduce the integer-label loss and gradient."""
+    P = _params(16, 8, 5, 6)
+    Z = {k: np.zeros_like(v, dtype=np.float64) for k, v in P.items()}
+    g = np.random.default_rng(9)
+    z = g.standard_normal((11, 16))
+    q = g.random((11, 5))
+    loss, G = oracle.mlp_loss_grad_soft_f64(Z, z, q)
+    S = q.sum(1)
+    assert loss == pytest.approx(math.log(5) * S.mean(), rel=1e-14)
+    np.testing.assert_allclose(G["b3"], (S[:, None] / 5 - q).mean(0), rtol=1e-13, atol=1e-16)
+    assert np.all(G["W1"] == 0) and np.all(G["W2"] == 0)
+    P64 = {k: v.astype(np.float64) for k, v in P.items()}
+    lab = g.integers(0, 5, 11).astype(np.int32)
+    l1, G1 = oracle.mlp_loss_grad_f64(P64, z, lab)
+    l2, G2 = oracle.mlp_loss_grad_soft_f64(P64, z, np.eye(5)[lab])
+    assert l1 == l2
+    for n_ in G1:
+        assert np.array_equal(G1[n_], G2[n_])
+
+
 # --------------------------------------------------------------- CG
 def test_cg_solves_small_spd_exactly_in_n_steps():
     g = np.random.default_rng(0)
