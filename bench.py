@@ -216,13 +216,14 @@ def run_ours(args):
     xs = [synth.uniform_vector(A.n_cols, 0).cuda() for A in mats]
     ys = [torch.empty(A.n_rows, dtype=torch.float64, device="cuda") for A in mats]
 
-    def time_spmv(P, x, y, reps=20, warm=3):
+    def time_spmv(P, x, y, reps=20, warm=3, fn=None):
+        fn = fn or (lambda: sp.spmv(P, x, y))
         for _ in range(warm):
-            sp.spmv(P, x, y)
+            fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            sp.spmv(P, x, y)
+            fn()
         e1.record()
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
@@ -270,10 +271,13 @@ def run_ours(args):
                 Pv.free()
         rec["variant_ms"] = {k: round(v, 5) for k, v in times.items()}
         rec["best_variant"] = min(times, key=times.get) if times else None
+        # the cost of this matrix's x gathers alone (spmv_gather_probe)
+        gsum = torch.empty(1, dtype=torch.float64, device="cuda")
+        rec["gather_ms"] = time_spmv(None, x, y, reps=10, fn=lambda: sp.spmv_gather_probe(dA, x, gsum))
         rec["P"], rec["P0"] = P, P0
         per.append(rec)
 
-    launches_per_step = sum(2 if r["variant"] == "merge" else 1 for r in per)
+    launches_per_step = sum(r["P"].info().launches for r in per)
     # ---------------- timed region
     for _ in range(args.warmup):
         for r, x, y in zip(per, xs, ys):
@@ -346,6 +350,9 @@ def run_ours(args):
             "features_spmvs": round(r["features_ms"] / r["plain_ms"], 2),
             "profile_spmvs": round(r["profile_select_ms"] / r["plain_ms"], 1),
             "prepare_ms": round(r["prepare_ms"], 2),
+            "gather_floor_ms": round(r["gather_ms"], 5),
+            "frac_of_gather_floor": round(r["gather_ms"] / km, 4),
+            "hbm_floor_ms": round(r["min_bytes"] / peak / 1e6, 5),
             "variant_ms": r["variant_ms"], "profile": r["profile"]})
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
@@ -369,7 +376,9 @@ def run_ours(args):
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": _traffic(per[dom]["variant"], per[dom]["matrix"]),
-                     "peak_source": f"{peak_kind} HBM copy bandwidth"},
+                     "peak_source": f"{peak_kind} HBM copy bandwidth",
+                     "gather_floor_ms": round(per[dom]["gather_ms"], 5),
+                     "frac_of_gather_floor": round(per[dom]["gather_ms"] / kern_ms[dom], 4)},
         "matrices": matrices,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk, "e2e": e2e,

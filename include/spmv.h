@@ -194,6 +194,7 @@ typedef struct {
     int32_t tile_items;    /* MERGE: merge-path items per tile as prepared      */
     int32_t bulk_copy;     /* 1 when the pipelined bulk-copy kernel is used     */
     int32_t accumulate;    /* 1 FP64, 2 FP32 (COMPRESSED with FP32 accumulation) */
+    int32_t launches;      /* kernels one spmv call launches (0 when n_rows = 0) */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */
@@ -232,6 +233,17 @@ spmv_status spmv_features(const spmv_csr_t *A, int32_t line_bytes, spmv_features
  * 8 (n_rows + 1 + nnz) bytes).  Synchronizes `stream`. */
 spmv_status spmv_profile(const spmv_csr_t *A, const double *x, int32_t reps,
                          spmv_profile_t *out, spmv_stream_t stream);
+
+/* Gather probe (a measurement aid in the spirit of the probes above, with no
+ * counterpart in the paper): *sum (device, 1 double) = sum over j of
+ * x[colind[j]] in storage order, read with as many independent gathers in
+ * flight as the GPU keeps.  Its duration is the cost of A's accesses to x
+ * alone: on matrices whose columns have no locality (random columns), the
+ * floor of any CSR kernel that reads x once per nonzero, which lies above
+ * the HBM floor there.  A's indices are not validated (they must lie in
+ * [0, n_cols)).  Allocates (stream-ordered) a small scratch.  Asynchronous. */
+spmv_status spmv_gather_probe(const spmv_csr_t *A, const double *x, double *sum,
+                              spmv_stream_t stream);
 
 /* ---- selection (Sections 3.1-3.3) ----------------------------------------- */
 spmv_thresholds_t spmv_default_thresholds(void);

@@ -70,7 +70,8 @@ class PreparedInfo(C.Structure):
                                          "items_per_warp", "value_type")] + \
         [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_blocks", "n_wide_rows",
                                   "owned_bytes", "min_bytes")] + \
-        [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32)]
+        [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32),
+         ("launches", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +86,7 @@ def declare(lib):
         "spmv_validate": (I32, [C.POINTER(CSR), P]),
         "spmv_features": (I32, [C.POINTER(CSR), I32, C.POINTER(Features), P]),
         "spmv_profile": (I32, [C.POINTER(CSR), P, I32, C.POINTER(Profile), P]),
+        "spmv_gather_probe": (I32, [C.POINTER(CSR), P, P, P]),
         "spmv_default_thresholds": (Thresholds, []),
         "spmv_classify_profile": (I32, [C.POINTER(Profile), C.POINTER(Thresholds), C.POINTER(I32)]),
         "spmv_class_variant": (I32, [I32]),

@@ -131,6 +131,18 @@ void release(spmv_prepared_t* P)
         if (p) cudaFree(p);
 }
 
+int32_t launches_of(const spmv_prepared_t* P)
+{
+    if (P->A.n_rows == 0) return 0;
+    switch (P->c.variant) {
+        case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
+        case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
+        case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
+        case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
+        default: return 1;
+    }
+}
+
 int64_t min_bytes_of(const spmv_prepared_t* P)
 {
     const spmv_csr_t& A = P->A;
@@ -544,6 +556,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.tile_items = P->tile_items;
     i.bulk_copy = P->bulk ? 1 : 0;
     i.accumulate = P->c.variant == SPMV_V6_COMPRESSED ? P->c.accumulate : 1;
+    i.launches = launches_of(P);
     *info = i;
     return SPMV_OK;
 }

@@ -109,11 +109,81 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
+// Gather probe: the sum of x over A's column indices in storage order, with
+// U independent gathers in flight per thread and nothing else per element
+// (no values, no row structure).  Its time is the cost of A's x accesses
+// alone, the floor below which no CSR kernel that reads x from memory once
+// per nonzero can go on matrices whose columns have no locality.
+constexpr int kGT = 256;
+
+template <int U>
+__global__ void __launch_bounds__(kGT)
+k_gather_probe(int64_t nnz, const int* __restrict__ ci, const double* __restrict__ x,
+               double* __restrict__ part)
+{
+    __shared__ double red[kGT / 32];
+    const int64_t stride = (int64_t)gridDim.x * kGT;
+    int64_t i = (int64_t)blockIdx.x * kGT + threadIdx.x;
+    double acc = 0.0;
+    for (; i + (U - 1) * stride < nnz; i += U * stride) {
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = __ldcs(ci + i + u * stride);
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += v[u];
+    }
+    for (; i < nnz; i += stride) acc += __ldg(x + __ldcs(ci + i));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kGT / 32; ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_parts(int n, const double* __restrict__ part, double* __restrict__ out)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+}
+
 }  // namespace
 
 }  // namespace spmvlib
 
 using namespace spmvlib;
+
+extern "C" spmv_status spmv_gather_probe(const spmv_csr_t* A, const double* x, double* sum,
+                                         spmv_stream_t stream)
+{
+    clear_error();
+    if (!A || !x || !sum) return fail(SPMV_ERR_INVALID_ARG, "spmv_gather_probe: NULL argument");
+    if (A->nnz < 0 || (A->nnz > 0 && !A->colind))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_gather_probe: bad matrix");
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = dev.sm_count * 8;
+    double* part = nullptr;
+    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(double) * grid, s));
+    k_gather_probe<4><<<grid, kGT, 0, s>>>(A->nnz, A->colind, x, part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_sum_parts<<<1, 1, 0, s>>>(grid, part, sum);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(part, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_gather_probe");
+    return SPMV_OK;
+}
 
 extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_t reps,
                                     spmv_profile_t* out, spmv_stream_t stream)

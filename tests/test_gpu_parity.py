@@ -404,6 +404,26 @@ def test_accumulate_choice_validation():
             sp.spmv_prepare(dA, bad)
 
 
+def test_gather_probe_sum_and_launch_counts():
+    A = synth.random_csr(50_000, 70_000, 9, seed=31)
+    g = np.random.default_rng(2)
+    x = torch.from_numpy(g.integers(-4, 5, A.n_cols).astype(np.float64))
+    dA = sp.DeviceCSR.from_host(A)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    sp.spmv_gather_probe(dA, x.cuda(), out)
+    # small integers: every order of summation gives the exact sum
+    assert out.item() == float(x.numpy()[A.colind.numpy()].sum())
+    expect = {"scalar": 1, "subwarp": 1, "latency": 1, "merge": 2}
+    for v, n in expect.items():
+        assert sp.spmv_prepare(dA, sp.make_choice(v)).info().launches == n
+    assert sp.spmv_prepare(dA, sp.make_choice("compressed")).info().launches == 1
+    assert sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=sp.VAL_BF16)).info().launches == 2
+    Z = synth.zipf_rows(20_000, 20_000, 1.5, 10_000, seed=1)
+    dZ = sp.DeviceCSR.from_host(Z)
+    P = sp.spmv_prepare(dZ, sp.make_choice("dynamic", block_nnz=256))
+    assert P.info().launches == 2
+
+
 # ----------------------------------------------------------------- profile + select
 def test_profile_runs_and_selection_consistent():
     A = synth.zipf_rows(200_000, 200_000, 1.5, 50_000, seed=3)
