@@ -539,7 +539,7 @@ def run_batch(args):
             sp.spmv(P, x, y)
     ms_sep = _time_ms(per_matrix, reps=5, warm=2)
     # batch lanes per row: from each matrix's selected variant's prepared shape
-    tpr = [max(1, P.info().threads_per_row) for P in preps]
+    tpr = [P.info().threads_per_row for P in preps]  # 0 (merge, stream, dynamic): from the mean
     B = sp.spmv_batch_create(dev, threads_per_row=tpr)
     sp.spmv_batch_bind(B, xs, ys)
     ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)

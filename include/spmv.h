@@ -388,9 +388,14 @@ spmv_status spmv_batch_bind(spmv_batch_t *B, const double *const *x, double *con
  * the launch is captured once into a CUDA graph (on the first such call) and
  * the graph is launched on `stream` from then on.  Asynchronous. */
 spmv_status spmv_batch_run(spmv_batch_t *B, int32_t use_graph, spmv_stream_t stream);
-/* Times every T in {1, 2, 4, ..., 32} on each matrix alone (reps launches
- * each, 0 = 3) and keeps the fastest, with rows per item 8 * 32 / T.  Needs a
- * bound batch; invalidates a captured graph.  Synchronizes `stream`. */
+/* Tunes the launch shapes for the throughput of the whole batch: matrices
+ * are grouped by the binary order of their mean row length; coordinate
+ * descent over the groups (most nonzeros first, two sweeps) tries lanes per
+ * row T in {1, 2, ..., 32}, then rows per item in {2, 4, ..., 32} passes of
+ * 32/T rows, timing the whole batch launch (median of reps, 0 = 3) and
+ * keeping a change only when it is more than 1 % faster.  Runs the batch
+ * (y is overwritten).  Needs a bound batch; invalidates a captured graph.
+ * Synchronizes `stream`. */
 spmv_status spmv_batch_autotune(spmv_batch_t *B, int32_t reps, spmv_stream_t stream);
 /* Current launch shapes (host arrays of count entries; either may be NULL). */
 spmv_status spmv_batch_config(const spmv_batch_t *B, int32_t *threads_per_row,

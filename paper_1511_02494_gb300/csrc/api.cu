@@ -207,11 +207,15 @@ spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
             return dyn_prepare(P, s);
         }
         case SPMV_V5_LATENCY: {
-            if (c.threads_per_row == 0) c.threads_per_row = auto_threads_per_row(mean / 8.0);
+            if (c.threads_per_row == 0) c.threads_per_row = auto_threads_per_row(mean / 7.0);
             DeviceInfo dev;
             if ((st = current_device(&dev)) != SPMV_OK) return st;
+            // x of up to half the L2 stays resident without help (streamed
+            // arrays are loaded evict-first); a persisting window would only
+            // take L2 away from the kernels that run next
             const int64_t xbytes = 8 * A.n_cols;
             int64_t want = xbytes < dev.max_persist_l2 ? xbytes : dev.max_persist_l2;
+            if (2 * xbytes <= (int64_t)dev.l2_bytes) want = 0;
             if (want > dev.max_window) want = dev.max_window;
             // the persisting-L2 carve-out is a limit of this process's context;
             // where it cannot be set the variant runs without the window

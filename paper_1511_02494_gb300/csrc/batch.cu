@@ -9,8 +9,14 @@
 // lanes with one DFMA per nonzero (row_partial).  A run is a single kernel
 // launch with no host work, so it can be replayed from a CUDA graph.
 //
-// Autotuning (spmv_batch_autotune) times every T in {1,...,32} on each matrix
-// alone and keeps the fastest; without it T comes from the mean row length.
+// Autotuning (spmv_batch_autotune) tunes for the throughput of the whole
+// batch: matrices are grouped by the binary order of their mean row length,
+// and coordinate descent over the groups (largest first) tries every T in
+// {1, ..., 32} and then rows per item in {2, 4, 8, 16, 32} passes of 32/T
+// rows, timing the whole persistent launch each time, keeping a change only
+// when it is more than 1 % faster.  Timing one matrix alone would measure
+// launch overhead and tail effects, not its share of a full launch.  Without
+// autotuning T comes from the mean row length.
 #include <algorithm>
 #include <vector>
 
@@ -102,14 +108,21 @@ int lg2(int t)
     return l;
 }
 
-spmv_status build_items(spmv_batch* B, cudaStream_t s)
+std::vector<BatchItem> make_items(const spmv_batch* B, const std::vector<int32_t>& tpr,
+                                  const std::vector<int32_t>& rpi)
 {
     std::vector<BatchItem> items;
     for (size_t m = 0; m < B->mats.size(); ++m) {
         const int n = (int)B->mats[m].n_rows;
-        const int r = B->rpi[m];
-        for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(B->tpr[m])});
+        const int r = rpi[m];
+        for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(tpr[m])});
     }
+    return items;
+}
+
+spmv_status build_items(spmv_batch* B, cudaStream_t s)
+{
+    std::vector<BatchItem> items = make_items(B, B->tpr, B->rpi);
     if (B->d_items) cudaFree(B->d_items);
     B->d_items = nullptr;
     B->n_items = (int64_t)items.size();
@@ -247,42 +260,90 @@ spmv_status spmv_batch_autotune(spmv_batch_t* B, int32_t reps, spmv_stream_t str
     if (!B || !B->bound) return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_autotune: bind first");
     if (reps <= 0) reps = 3;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaEvent_t e0, e1;
-    SPMV_CUDA_TRY(cudaEventCreate(&e0));
-    SPMV_CUDA_TRY(cudaEventCreate(&e1));
+    const size_t count = B->mats.size();
+    // groups: binary order of the mean row length
+    std::vector<int> group(count, 0);
+    std::vector<int64_t> group_nnz(32, 0);
+    for (size_t m = 0; m < count; ++m) {
+        const spmv_csr_t& A = B->mats[m];
+        const double mean = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
+        int g = 0;
+        while (g < 31 && (double)(2 << g) <= mean) ++g;
+        group[m] = g;
+        group_nnz[g] += A.nnz;
+    }
+    std::vector<int> order;
+    for (int g = 0; g < 32; ++g)
+        if (group_nnz[g] > 0) order.push_back(g);
+    std::sort(order.begin(), order.end(), [&](int a, int b_) { return group_nnz[a] > group_nnz[b_]; });
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     BatchItem* d_tmp = nullptr;
-    cudaError_t e = cudaSuccess;
-    for (size_t m = 0; m < B->mats.size() && e == cudaSuccess; ++m) {
-        const int n = (int)B->mats[m].n_rows;
-        if (n == 0) continue;
-        float best = 1e30f;
-        int best_t = B->tpr[m];
-        for (int T = 1; T <= 32 && e == cudaSuccess; T <<= 1) {
-            const int r = 8 * (32 / T);
-            std::vector<BatchItem> items;
-            for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(T)});
+    size_t cap = 0;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // median time of `reps` launches of the whole batch with shapes (tpr, rpi)
+    auto eval = [&](const std::vector<int32_t>& tpr, const std::vector<int32_t>& rpi, float* ms) {
+        std::vector<BatchItem> items = make_items(B, tpr, rpi);
+        if (items.size() > cap) {
             if (d_tmp) cudaFreeAsync(d_tmp, s);
-            e = cudaMallocAsync(reinterpret_cast<void**>(&d_tmp), sizeof(BatchItem) * items.size(), s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(d_tmp, items.data(), sizeof(BatchItem) * items.size(),
-                                    cudaMemcpyHostToDevice, s);
+            d_tmp = nullptr;
+            cap = items.size();
+            e = cudaMallocAsync(reinterpret_cast<void**>(&d_tmp), sizeof(BatchItem) * cap, s);
+        }
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpyAsync(d_tmp, items.data(), sizeof(BatchItem) * items.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_batch(B, B->d_mats, d_tmp, (int64_t)items.size(), s);  // warm-up
+        std::vector<float> t;
+        for (int k = 0; k < reps && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(e0, s);
             if (e == cudaSuccess) e = launch_batch(B, B->d_mats, d_tmp, (int64_t)items.size(), s);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            for (int k = 0; k < reps && e == cudaSuccess; ++k)
-                e = launch_batch(B, B->d_mats, d_tmp, (int64_t)items.size(), s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && ms < best) { best = ms; best_t = T; }
+            float v = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&v, e0, e1);
+            t.push_back(v);
         }
-        B->tpr[m] = best_t;
-        B->rpi[m] = 8 * (32 / best_t);
+        if (e != cudaSuccess || t.empty()) { *ms = 1e30f; return; }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+    };
+    std::vector<int32_t> tpr = B->tpr, rpi = B->rpi;
+    float best = 0.f;
+    eval(tpr, rpi, &best);
+    auto set_group = [&](std::vector<int32_t>& tv, std::vector<int32_t>& rv, int g, int T, int passes) {
+        for (size_t m = 0; m < count; ++m)
+            if (group[m] == g) { tv[m] = T; rv[m] = passes * (32 / T); }
+    };
+    for (int sweep = 0; sweep < 2 && e == cudaSuccess; ++sweep) {
+        for (int g : order) {
+            // lanes per row with 8 passes per item, then passes per item at that T
+            int gm = -1;
+            for (size_t m = 0; m < count; ++m) if (group[m] == g) { gm = (int)m; break; }
+            int bestT = tpr[gm], bestP = std::max(1, rpi[gm] / (32 / tpr[gm]));
+            for (int T = 1; T <= 32 && e == cudaSuccess; T <<= 1) {
+                std::vector<int32_t> tv = tpr, rv = rpi;
+                set_group(tv, rv, g, T, bestP);
+                float ms;
+                eval(tv, rv, &ms);
+                if (ms < 0.99f * best) { best = ms; bestT = T; tpr = tv; rpi = rv; }
+            }
+            for (int passes = 2; passes <= 32 && e == cudaSuccess; passes <<= 1) {
+                std::vector<int32_t> tv = tpr, rv = rpi;
+                set_group(tv, rv, g, bestT, passes);
+                float ms;
+                eval(tv, rv, &ms);
+                if (ms < 0.99f * best) { best = ms; bestP = passes; tpr = tv; rpi = rv; }
+            }
+        }
     }
     if (d_tmp) cudaFreeAsync(d_tmp, s);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "spmv_batch_autotune");
+    B->tpr = tpr;
+    B->rpi = rpi;
     return build_items(B, s);
 }
 
