@@ -87,6 +87,8 @@ def _load():
                 "orc_argmax": (i32, [i32, P, P]),
                 "orc_mlp_loss_grad_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
                 "orc_mlp_loss_grad_soft_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
+                "orc_sliced_layout": (i64, [i64, P, i32, i32, P, P, P, P]),
+                "orc_sliced_fill": (None, [i64, P, P, P, P, P, P, P, P]),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -230,6 +232,35 @@ def compress_u16(A):
     off = np.empty(A.nnz, np.uint16)
     wide = _load().orc_compress_u16(A.n_rows, _p(rp), _p(ci), _p(base), _p(off))
     return base, off, int(wide)
+
+
+def sliced_layout(A, sigma: int, cap: int):
+    """Sliced layout (32 rows per slice, column-major inside a slice): the
+    position -> row permutation, per-position row length (-1: long row or
+    past the end), slice lengths and slice starts, and the long-row count."""
+    rp, _, _ = _csr(A)
+    S = (A.n_rows + 31) // 32
+    perm = np.empty(max(A.n_rows, 1), np.int32)
+    rowlen = np.empty(max(32 * S, 1), np.int32)
+    slen = np.empty(max(S, 1), np.int32)
+    sptr = np.empty(S + 1, np.int64)
+    n_long = _load().orc_sliced_layout(A.n_rows, _p(rp), sigma, cap, _p(perm), _p(rowlen),
+                                       _p(slen), _p(sptr))
+    return perm[:A.n_rows], rowlen[:32 * S], slen[:S], sptr, int(n_long)
+
+
+def sliced_fill(A, perm, rowlen, sptr):
+    """Column-major slice contents (columns and values, zero padding)."""
+    rp, ci, va = _csr(A)
+    tot = int(sptr[-1])
+    col = np.empty(max(tot, 1), np.int32)
+    val = np.empty(max(tot, 1), np.float64)
+    perm = _np(perm, np.int32)
+    rowlen = _np(rowlen, np.int32)
+    sptr = _np(sptr, np.int64)
+    _load().orc_sliced_fill(A.n_rows, _p(rp), _p(ci), _p(va), _p(perm), _p(rowlen), _p(sptr),
+                            _p(col), _p(val))
+    return col[:tot], val[:tot]
 
 
 def mlp_forward_f32(params: dict, v) -> np.ndarray:

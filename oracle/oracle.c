@@ -11,8 +11,7 @@
  * Compiled with -O2 -ffp-contract=off: every floating-point operation below
  * is rounded as written (no fused multiply-add unless fmaf is called).
  *
- * Readings of the paper where it is silent or garbled (numbered as in the
- * design notes):
+ * Readings of the paper where it is silent or garbled (numbered O1..O20):
  *   O1  Algorithm 1 writes an assignment over an inclusive, 1-based range; the
  *       product is read as y_i = sum over the half-open 0-based range
  *       [rowptr_i, rowptr_{i+1}), with y_i = 0 for an empty row.
@@ -33,6 +32,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef unsigned __int128 u128;
@@ -375,6 +375,86 @@ int64_t orc_compress_u16(int64_t n_rows, const int32_t *rowptr, const int32_t *c
         }
     }
     return wide;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sliced layout of the SLICED variant (a GPU format for the MB and CML
+ * classes: 32 rows per slice, elements stored column-major inside a slice so
+ * that one lane per row reads coalesced).
+ *   positions: rows in order when sigma == 1; otherwise, inside each window
+ *   of sigma consecutive rows, rows sorted by key length descending, ties by
+ *   row index ascending, where a row longer than `cap` has key length 0.
+ *   rowlen[p]: length of the row at position p, -1 for a long row (> cap) or
+ *   a position past the last row (positions run to 32 * S, S = ceil(N/32)).
+ *   slice_len[s] = max(0, max rowlen over positions 32s .. 32s+31).
+ *   slice_ptr[0] = 0, slice_ptr[s+1] = slice_ptr[s] + 32 * slice_len[s].
+ * The element k of the row at position p = 32s + l lives at
+ * slice_ptr[s] + 32 k + l.  Returns the number of long rows.                 */
+static const int32_t *g_sort_rowptr;
+static int32_t g_sort_cap;
+
+static int32_t key_len(int64_t i)
+{
+    int64_t len = g_sort_rowptr[i + 1] - g_sort_rowptr[i];
+    return len > g_sort_cap ? 0 : (int32_t)len;
+}
+
+static int cmp_rows(const void *a, const void *b)
+{
+    int32_t ra = *(const int32_t *)a, rb = *(const int32_t *)b;
+    int32_t la = key_len(ra), lb = key_len(rb);
+    if (la != lb) return la > lb ? -1 : 1;
+    return ra < rb ? -1 : (ra > rb ? 1 : 0);
+}
+
+int64_t orc_sliced_layout(int64_t n_rows, const int32_t *rowptr, int32_t sigma, int32_t cap,
+                          int32_t *perm, int32_t *rowlen, int32_t *slice_len, int64_t *slice_ptr)
+{
+    int64_t n_slices = (n_rows + 31) / 32, n_long = 0;
+    for (int64_t i = 0; i < n_rows; ++i) perm[i] = (int32_t)i;
+    if (sigma > 1) {
+        g_sort_rowptr = rowptr;
+        g_sort_cap = cap;
+        for (int64_t w = 0; w < n_rows; w += sigma) {
+            int64_t cnt = n_rows - w < sigma ? n_rows - w : sigma;
+            qsort(perm + w, (size_t)cnt, sizeof(int32_t), cmp_rows);
+        }
+    }
+    for (int64_t p = 0; p < 32 * n_slices; ++p) {
+        if (p >= n_rows) { rowlen[p] = -1; continue; }
+        int64_t r = perm[p];
+        int64_t len = rowptr[r + 1] - rowptr[r];
+        if (len > cap) { rowlen[p] = -1; ++n_long; }
+        else rowlen[p] = (int32_t)len;
+    }
+    slice_ptr[0] = 0;
+    for (int64_t s = 0; s < n_slices; ++s) {
+        int32_t m = 0;
+        for (int64_t l = 0; l < 32; ++l)
+            if (rowlen[32 * s + l] > m) m = rowlen[32 * s + l];
+        slice_len[s] = m;
+        slice_ptr[s + 1] = slice_ptr[s] + 32 * (int64_t)m;
+    }
+    return n_long;
+}
+
+/* Column-major slice contents: col/val at slice_ptr[s] + 32 k + l for k <
+ * rowlen[32s + l]; every other slot is 0.                                     */
+void orc_sliced_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                     const double *val, const int32_t *perm, const int32_t *rowlen,
+                     const int64_t *slice_ptr, int32_t *col_out, double *val_out)
+{
+    int64_t n_slices = (n_rows + 31) / 32;
+    int64_t tot = slice_ptr[n_slices];
+    for (int64_t q = 0; q < tot; ++q) { col_out[q] = 0; val_out[q] = 0.0; }
+    for (int64_t p = 0; p < n_rows; ++p) {
+        if (rowlen[p] < 0) continue;
+        int64_t s = p / 32, l = p % 32, b = rowptr[perm[p]];
+        for (int64_t k = 0; k < rowlen[p]; ++k) {
+            col_out[slice_ptr[s] + 32 * k + l] = colind[b + k];
+            val_out[slice_ptr[s] + 32 * k + l] = val[b + k];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -492,6 +492,71 @@ def test_mlp_soft_targets_closed_forms():
         assert np.array_equal(G1[n_], G2[n_])
 
 
+# --------------------------------------------------------------- sliced layout
+def _csr_from_lengths(lengths, n_cols=100, seed=0):
+    g = np.random.default_rng(seed)
+    rp = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    cols = np.concatenate([np.sort(g.choice(n_cols, l, replace=False)) for l in lengths]
+                          or [np.zeros(0)]).astype(np.int32)
+    vals = g.standard_normal(int(rp[-1]))
+    return synth.HostCSR(len(lengths), n_cols, torch.from_numpy(rp), torch.from_numpy(cols),
+                         torch.from_numpy(vals), "lengths")
+
+
+def test_sliced_layout_hand_example():
+    """Five rows of lengths 1, 3, 0, 5, 2 with windows of 4 rows and long
+    rows above 4 nonzeros, worked by hand: window 0 holds rows 0-3 with key
+    lengths 1, 3, 0, 0 (row 3 is long) -> order 1, 0, 2, 3; window 1 holds row
+    4.  One slice of 32 positions; its length is 3 (row 1)."""
+    A = _csr_from_lengths([1, 3, 0, 5, 2])
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma=4, cap=4)
+    assert perm.tolist() == [1, 0, 2, 3, 4]
+    assert rowlen.tolist() == [3, 1, 0, -1, 2] + [-1] * 27
+    assert slen.tolist() == [3] and sptr.tolist() == [0, 96] and n_long == 1
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    ci = A.colind.numpy()
+    # position 0 holds row 1 (elements 1..3 of colind), position 4 row 4
+    assert [col[32 * k + 0] for k in range(3)] == ci[1:4].tolist()
+    assert [col[32 * k + 4] for k in range(2)] == ci[9:11].tolist()
+    assert col[32 * 1 + 1] == 0 and val[32 * 1 + 1] == 0.0  # padding of row 0
+    # sigma = 1: identity order
+    perm1, rowlen1, slen1, _, _ = oracle.sliced_layout(A, sigma=1, cap=4)
+    assert perm1.tolist() == [0, 1, 2, 3, 4] and rowlen1[:5].tolist() == [1, 3, 0, -1, 2]
+    assert slen1.tolist() == [3]
+
+
+@pytest.mark.parametrize("sigma,cap", [(1, 1000), (32, 1000), (256, 40), (64, 7)])
+def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap):
+    g = np.random.default_rng(sigma + cap)
+    lengths = np.minimum(g.zipf(1.6, 1000), 60)
+    lengths[g.integers(0, 1000, 30)] = 0
+    A = _csr_from_lengths(lengths.tolist(), n_cols=200, seed=3)
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma=sigma, cap=cap)
+    key = np.where(lengths > cap, 0, lengths)
+    expect = np.arange(1000)
+    if sigma > 1:
+        expect = np.concatenate([w + np.argsort(-key[w:w + sigma], kind="stable")
+                                 for w in range(0, 1000, sigma)])
+    assert np.array_equal(perm, expect)
+    assert n_long == int((lengths > cap).sum())
+    full = np.full(32 * len(slen), -1)
+    full[:1000] = np.where(lengths[perm] > cap, -1, lengths[perm])
+    assert np.array_equal(rowlen, full)
+    assert np.array_equal(slen, np.maximum(full.reshape(-1, 32).max(1), 0))
+    assert np.array_equal(sptr, np.concatenate([[0], np.cumsum(32 * slen)]))
+    # the slices hold exactly the short rows' elements
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    rp, ci, va = A.rowptr.numpy(), A.colind.numpy(), A.val.numpy()
+    for p in range(1000):
+        r, s, l = perm[p], p // 32, p % 32
+        if rowlen[p] < 0:
+            continue
+        idx = sptr[s] + 32 * np.arange(rowlen[p]) + l
+        assert np.array_equal(col[idx], ci[rp[r]:rp[r + 1]])
+        assert np.array_equal(val[idx], va[rp[r]:rp[r + 1]])
+    assert np.count_nonzero(val) == np.count_nonzero(va[np.repeat(lengths <= cap, lengths)])
+
+
 # --------------------------------------------------------------- CG
 def test_cg_solves_small_spd_exactly_in_n_steps():
     g = np.random.default_rng(0)
