@@ -232,7 +232,7 @@ def run_ours(args):
     model = sp.spmv_model_load(model_path) if os.path.exists(model_path) else None
     per = []
     candidates = [("scalar", {}), ("subwarp", {}), ("stream", {}), ("merge", {}),
-                  ("dynamic", {}), ("latency", {}), ("compressed", {})]
+                  ("dynamic", {}), ("latency", {}), ("compressed", {}), ("sliced", {})]
     for A, dA, x, y in zip(mats, dev, xs, ys):
         rec = {"matrix": A.name, "n_rows": A.n_rows, "nnz": A.nnz}
         # plain CSR

@@ -53,7 +53,11 @@ typedef enum {
 /* SpMV variants.  The class -> variant map (the GPU counterpart of Table 2,
  * Section 3.3) is CML -> LATENCY, MB -> COMPRESSED, IMB -> DYNAMIC,
  * CMP -> SUBWARP.  SCALAR is the unoptimized CSR kernel (one thread per row,
- * Algorithm 1 as written) against which speedups are reported. */
+ * Algorithm 1 as written) against which speedups are reported.  SLICED is a
+ * GPU format with no counterpart in Table 2: 32-row slices whose k-th
+ * elements are stored next to each other, one lane per row, no reduction
+ * across lanes; it serves regular matrices of the MB and CML classes (rows
+ * longer than 1024 are computed from CSR by one warp each). */
 typedef enum {
     SPMV_V0_SCALAR = 0,     /* one thread per row                                */
     SPMV_V1_SUBWARP = 1,    /* T lanes per row (T = 1..32), shuffle reduction    */
@@ -62,7 +66,8 @@ typedef enum {
     SPMV_V4_DYNAMIC = 4,    /* rows tiered by length, long rows split, dynamic queue */
     SPMV_V5_LATENCY = 5,    /* gathers of x issued ahead, x kept in L2           */
     SPMV_V6_COMPRESSED = 6, /* 16-bit column offsets, FP64/FP32/BF16 values      */
-    SPMV_NUM_VARIANTS = 7
+    SPMV_V7_SLICED = 7,     /* 32-row slices stored column-major, a lane per row */
+    SPMV_NUM_VARIANTS = 8
 } spmv_variant;
 
 /* Bottleneck classes of Section 3.1. */
@@ -154,6 +159,11 @@ typedef struct {
  *                     (32 k, k in {1, 2, 4, 6, 7, 8, 12, 16})
  *   block_nnz       : DYNAMIC nonzeros per segment of a long row (power of two,
  *                     256..2^20; default 2048)
+ *   block_nnz       : SLICED window of the length sort: 1 = rows in order, or a
+ *                     power of two in 32..4096 (rows sorted by length, longest
+ *                     first, inside windows of that many rows); 0 = rows in
+ *                     order unless that pads the slices by more than 25 %,
+ *                     then 256
  *   value_type      : COMPRESSED value storage (spmv_value_type)
  *   accumulate      : COMPRESSED arithmetic.  FP32 (the default for FP32/BF16
  *                     values) rounds x to an FP32 copy owned by the prepared
@@ -187,7 +197,8 @@ typedef struct spmv_prepared spmv_prepared_t;
 typedef struct {
     int32_t variant, threads_per_row, block_nnz, items_per_warp, value_type;
     int64_t n_rows, n_cols, nnz;
-    int64_t n_blocks;      /* STREAM windows / MERGE tiles / DYNAMIC work items */
+    int64_t n_blocks;      /* STREAM windows / MERGE tiles / DYNAMIC work items /
+                              SLICED slices */
     int64_t n_wide_rows;   /* COMPRESSED rows that kept 32-bit columns          */
     int64_t owned_bytes;   /* device bytes owned by the object                  */
     int64_t min_bytes;     /* minimum traffic of one spmv() with this format    */
@@ -204,7 +215,14 @@ typedef enum {
     SPMV_EXPORT_MERGE_NZ = 2,   /* MERGE: int32 [n_blocks + 1] start nonzero of a part  */
     SPMV_EXPORT_ROWBASE = 3,    /* COMPRESSED: int32 [n_rows] first column, -1 = wide   */
     SPMV_EXPORT_OFFSETS = 4,    /* COMPRESSED: uint16 [nnz] column - rowbase            */
-    SPMV_EXPORT_VALUES = 5      /* COMPRESSED: [nnz] values in value_type               */
+    SPMV_EXPORT_VALUES = 5,     /* COMPRESSED: [nnz] values in value_type               */
+    SPMV_EXPORT_SLICE_PERM = 6, /* SLICED, rows sorted: int32 [n_rows] position -> row  */
+    SPMV_EXPORT_SLICE_ROWLEN = 7, /* SLICED: int32 [32 S] row length per position, -1 =
+                                   long row (computed from CSR) or past the last row   */
+    SPMV_EXPORT_SLICE_LEN = 8,  /* SLICED: int32 [S] slice length (longest row in it)   */
+    SPMV_EXPORT_SLICE_PTR = 9,  /* SLICED: int64 [S + 1] first element of each slice    */
+    SPMV_EXPORT_SLICE_COL = 10, /* SLICED: int32 [slice_ptr[S]] columns, column-major   */
+    SPMV_EXPORT_SLICE_VAL = 11  /* SLICED: f64 [slice_ptr[S]] values, column-major      */
 } spmv_export;
 
 /* ---- status ---------------------------------------------------------- */

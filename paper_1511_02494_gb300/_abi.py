@@ -7,12 +7,13 @@ SPMV_OK = 0
 STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_ARG", 2: "SPMV_ERR_INVALID_CSR",
                 3: "SPMV_ERR_UNSUPPORTED", 4: "SPMV_ERR_NOMEM", 5: "SPMV_ERR_CUDA",
                 6: "SPMV_ERR_TIMEOUT", 7: "SPMV_ERR_MODEL"}
-VARIANTS = ("scalar", "subwarp", "stream", "merge", "dynamic", "latency", "compressed")
+VARIANTS = ("scalar", "subwarp", "stream", "merge", "dynamic", "latency", "compressed", "sliced")
 VARIANT_IDS = {n: i for i, n in enumerate(VARIANTS)}
 CLASSES = ("CML", "MB", "IMB", "CMP")
 VAL_F64, VAL_F32, VAL_BF16 = 0, 1, 2
 (EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
- EXPORT_VALUES) = range(6)
+ EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
+ EXPORT_SLICE_COL, EXPORT_SLICE_VAL) = range(12)
 
 
 class CSR(C.Structure):

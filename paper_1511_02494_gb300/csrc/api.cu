@@ -126,7 +126,9 @@ void release(spmv_prepared_t* P)
 {
     void* ptrs[] = {P->blocks, P->merge_nz, P->carry_row, P->carry_val, P->counter,
                     P->rowbase, P->off16, P->lowval, P->x_stage, P->y_stage, P->status,
-                    P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32};
+                    P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32,
+                    P->sl.rowlen, P->sl.slice_len, P->sl.slice_ptr, P->sl.perm, P->sl.col, P->sl.val,
+                    P->sl.long_rows, P->sl.count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -138,6 +140,7 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
+        case SPMV_V7_SLICED: return P->sl.n_long > 0 ? 2 : 1;      // + long rows
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
         default: return 1;
     }
@@ -147,6 +150,13 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
 {
     const spmv_csr_t& A = P->A;
     const int64_t vec = 8 * A.n_cols + 8 * A.n_rows + 4 * (A.n_rows + 1);
+    if (P->c.variant == SPMV_V7_SLICED) {
+        // elements once, a row length per position, slice length and start,
+        // the permutation when rows are sorted, the long rows' CSR bounds
+        const SlicedPlan& d = P->sl;
+        return 12 * A.nnz + 128 * d.n_slices + 12 * d.n_slices + (d.sigma > 1 ? 4 * A.n_rows : 0) +
+               12 * (int64_t)d.n_long + 8 * A.n_cols + 8 * A.n_rows;
+    }
     if (P->c.variant != SPMV_V6_COMPRESSED) return 12 * A.nnz + vec;
     const int vb = P->c.value_type == SPMV_VAL_F64 ? 8 : P->c.value_type == SPMV_VAL_F32 ? 4 : 2;
     // FP32 accumulation: x converted once (8 + 4 bytes per column), then read as float
@@ -273,6 +283,8 @@ spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
             if (e != cudaSuccess) return cuda_fail(e, "compress offsets/values");
             return SPMV_OK;
         }
+        case SPMV_V7_SLICED:
+            return sliced_prepare(P, s);
         default:
             return fail(SPMV_ERR_INVALID_ARG, "unknown variant");
     }
@@ -286,6 +298,9 @@ spmv_status check_choice(const spmv_choice_t* c)
         return fail(SPMV_ERR_INVALID_ARG, "threads_per_row must be a power of two in 1..32");
     if (c->variant == SPMV_V2_STREAM && c->block_nnz != 0 && !is_pow2_in(c->block_nnz, 64, 8192))
         return fail(SPMV_ERR_INVALID_ARG, "block_nnz must be a power of two in 64..8192");
+    if (c->variant == SPMV_V7_SLICED && c->block_nnz != 0 && c->block_nnz != 1 &&
+        !is_pow2_in(c->block_nnz, 32, 4096))
+        return fail(SPMV_ERR_INVALID_ARG, "SLICED sort window (block_nnz) must be 1 or a power of two in 32..4096");
     if (c->variant == SPMV_V4_DYNAMIC && c->block_nnz != 0 && !is_pow2_in(c->block_nnz, 256, 1 << 20))
         return fail(SPMV_ERR_INVALID_ARG, "DYNAMIC segment length must be a power of two in 256..2^20");
     if (c->variant == SPMV_V3_MERGE && c->block_nnz != 0 && c->block_nnz != 1024 &&
@@ -328,6 +343,7 @@ spmv_status run_impl(const spmv_prepared_t* P, const double* x, double* y, cudaS
                                  P->carry_row, P->carry_val, x, y, s);
             break;
         case SPMV_V4_DYNAMIC: e = launch_dyn(P, x, y, s); break;
+        case SPMV_V7_SLICED: e = launch_sliced(P, x, y, s); break;
         case SPMV_V5_LATENCY:
             e = launch_latency(A, c.threads_per_row, x, y, P->l2_window_bytes, s);
             break;
@@ -595,9 +611,28 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
                 else { src = P->lowval; size = (P->c.value_type == SPMV_VAL_F32 ? 4 : 2) * P->A.nnz; }
             }
             break;
+        case SPMV_EXPORT_SLICE_PERM:
+            if (v == SPMV_V7_SLICED && P->sl.sigma > 1) { src = P->sl.perm; size = 4 * P->A.n_rows; }
+            break;
+        case SPMV_EXPORT_SLICE_ROWLEN:
+            if (v == SPMV_V7_SLICED) { src = P->sl.rowlen; size = 4 * 32 * P->sl.n_slices; }
+            break;
+        case SPMV_EXPORT_SLICE_LEN:
+            if (v == SPMV_V7_SLICED) { src = P->sl.slice_len; size = 4 * P->sl.n_slices; }
+            break;
+        case SPMV_EXPORT_SLICE_PTR:
+            if (v == SPMV_V7_SLICED) { src = P->sl.slice_ptr; size = 8 * (P->sl.n_slices + 1); }
+            break;
+        case SPMV_EXPORT_SLICE_COL:
+            if (v == SPMV_V7_SLICED) { src = P->sl.col; size = 4 * P->sl.tot; }
+            break;
+        case SPMV_EXPORT_SLICE_VAL:
+            if (v == SPMV_V7_SLICED) { src = P->sl.val; size = 8 * P->sl.tot; }
+            break;
         default:
             return fail(SPMV_ERR_INVALID_ARG, "unknown export");
     }
+    if (size == 0 && src && bytes == 0) return SPMV_OK;  // an empty array
     if (!src && size == 0 && which == SPMV_EXPORT_OFFSETS && v == SPMV_V6_COMPRESSED)
         return fail(SPMV_ERR_UNSUPPORTED, "every row is wide: no 16-bit offsets were built");
     if (!src && size != 0) return fail(SPMV_ERR_UNSUPPORTED, "array not held");

@@ -54,6 +54,22 @@ struct DynPlan {
     double* partial = nullptr;  // one partial sum per segment
 };
 
+// SLICED (V7): rows longer than this are computed from CSR, one warp each
+constexpr int kSlicedCap = 1024;
+
+struct SlicedPlan {
+    int64_t n_slices = 0, tot = 0;
+    int sigma = 1, n_long = 0;
+    int* rowlen = nullptr;       // [32 n_slices] row length per position, -1: long or absent
+    int* slice_len = nullptr;    // [n_slices]
+    int64_t* slice_ptr = nullptr;  // [n_slices + 1] element offset of each slice
+    int* perm = nullptr;         // [n_rows] position -> row (sigma > 1 only)
+    int* col = nullptr;          // [tot] column-major slice contents
+    double* val = nullptr;       // [tot]
+    int* long_rows = nullptr;    // [n_long]
+    unsigned* count = nullptr;   // scratch counter
+};
+
 struct spmv_prepared {
     spmv_csr_t A{};
     spmv_choice_t c{};
@@ -78,6 +94,7 @@ struct spmv_prepared {
     unsigned* status = nullptr;    // device status word (bounded-wait timeouts)
     DynPlan dyn;
     float* x32 = nullptr;          // COMPRESSED with FP32 accumulation: FP32 copy of x
+    SlicedPlan sl;
 };
 
 namespace spmvlib {
@@ -106,6 +123,8 @@ cudaError_t launch_window(const spmv_csr_t& A, int block_nnz, const int32_t* blo
 spmv_status prepared_alloc(spmv_prepared* P, void** p, int64_t bytes);
 spmv_status dyn_prepare(spmv_prepared* P, cudaStream_t s);
 cudaError_t launch_dyn(const spmv_prepared* P, const double* x, double* y, cudaStream_t s);
+spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s);
+cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_latency(const spmv_csr_t& A, int T, const double* x, double* y,
                            int l2_window_bytes, cudaStream_t s);
 cudaError_t launch_compress(const spmv_csr_t& A, int32_t* rowbase, uint16_t* off16,

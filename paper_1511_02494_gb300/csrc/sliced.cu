@@ -1,0 +1,309 @@
+// SLICED variant (V7): sliced ELL layout, the GPU form of the paper's
+// bandwidth (MB) and latency (CML) optimizations on this machine.
+//
+// Rows are grouped in slices of 32; inside a slice the k-th elements of the
+// 32 rows are stored next to each other (column-major), so one lane per row
+// reads 32 consecutive values and 32 consecutive column indices per load and
+// issues 32 independent gathers of x per instruction.  There is no
+// reduction across lanes: each row's sum is one chain of DFMAs in row order,
+// so the FP64 pipe spends exactly one instruction slot per element of the
+// slice (the CSR kernels with T lanes per row add log2(T) shuffle-adds per
+// row, 28 % more FP64 slots on a 27-point stencil).  Lanes whose row is
+// shorter than the slice skip the padded slots (the loads and DFMAs are
+// predicated), so padding costs issue slots but no memory traffic.
+//
+// Optionally (sigma > 1) rows are sorted by length, longest first, inside
+// windows of sigma rows, so that a slice holds rows of similar length; y is
+// then written through the permutation.  Rows longer than kSlicedCap are not
+// put in slices (their slot has length -1) and are computed by one warp each
+// from the CSR arrays.  The layout is that of the oracle's orc_sliced_layout
+// and orc_sliced_fill, bit for bit.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "rowdot.cuh"
+
+namespace spmvlib {
+namespace {
+
+using namespace dev;
+constexpr int kSB = 256;       // threads per block: 8 slices
+constexpr int kSortT = 1024;   // threads of the window sort
+
+__global__ void k_sl_rowlen_identity(int64_t n_rows, const int* __restrict__ rp, int cap,
+                                     int* __restrict__ rowlen, unsigned* __restrict__ n_long)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_rows;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int len = rp[p + 1] - rp[p];
+        if (len > cap) {
+            rowlen[p] = -1;
+            atomicAdd(n_long, 1u);
+        } else {
+            rowlen[p] = len;
+        }
+    }
+}
+
+// One CTA per window of sigma rows (sigma a power of two, 32..4096): bitonic
+// sort of keys (0xFFFFFFFF - key length) << 32 | index in window, so rows come
+// out by key length descending, ties by row index ascending; slots past the
+// last row carry the largest key and end last.
+__global__ void __launch_bounds__(kSortT)
+k_sl_sort(int64_t n_rows, const int* __restrict__ rp, int sigma, int cap, int* __restrict__ perm,
+          int* __restrict__ rowlen, unsigned* __restrict__ n_long)
+{
+    extern __shared__ unsigned long long keys[];
+    const int64_t w0 = (int64_t)blockIdx.x * sigma;
+    for (int i = threadIdx.x; i < sigma; i += kSortT) {
+        const int64_t r = w0 + i;
+        unsigned long long key = ~0ull;
+        if (r < n_rows) {
+            const int len = rp[r + 1] - rp[r];
+            const unsigned klen = len > cap ? 0u : (unsigned)len;
+            key = ((unsigned long long)(0xFFFFFFFFu - klen) << 32) | (unsigned)i;
+        }
+        keys[i] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= sigma; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < sigma; i += kSortT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < sigma; i += kSortT) {
+        const int64_t p = w0 + i;
+        if (p >= n_rows) continue;
+        const int r = (int)(w0 + (int64_t)(keys[i] & 0xFFFFFFFFull));
+        perm[p] = r;
+        const int len = rp[r + 1] - rp[r];
+        if (len > cap) {
+            rowlen[p] = -1;
+            atomicAdd(n_long, 1u);
+        } else {
+            rowlen[p] = len;
+        }
+    }
+}
+
+// slice_len[s] = max(0, max over the slice's 32 positions of rowlen)
+__global__ void k_sl_slice_len(int64_t n_slices, const int* __restrict__ rowlen,
+                               int* __restrict__ slice_len)
+{
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int m = __reduce_max_sync(FULL, max(rowlen[s * 32 + lane], 0));
+    if (lane == 0) slice_len[s] = m;
+}
+
+// column-major contents of each slice (padding was zeroed beforehand)
+__global__ void k_sl_fill(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                          const double* __restrict__ v, const int* __restrict__ perm,
+                          const int* __restrict__ rowlen, const int64_t* __restrict__ slice_ptr,
+                          int* __restrict__ col, double* __restrict__ val)
+{
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int r = perm ? perm[p] : (int)p;
+    const int64_t b = rp[r];
+    const int64_t q0 = slice_ptr[s] + lane;
+    for (int k = 0; k < len; ++k) {
+        col[q0 + (int64_t)k * 32] = ci[b + k];
+        val[q0 + (int64_t)k * 32] = v[b + k];
+    }
+}
+
+// rows longer than cap, appended with one atomic per warp
+__global__ void k_sl_long_list(int64_t n_rows, const int* __restrict__ rp, int cap,
+                               int* __restrict__ list, unsigned* __restrict__ count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_iter = (n_rows + stride - 1) / stride;
+    for (int64_t it = 0; it < n_iter; ++it) {
+        const int64_t i = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool is_long = i < n_rows && rp[i + 1] - rp[i] > cap;
+        const unsigned m = __ballot_sync(FULL, is_long);
+        if (m == 0) continue;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(count, (unsigned)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (is_long) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+    }
+}
+
+// 8 blocks of 256 per SM (32 registers): measured faster than the 40-register
+// form on all three regular test matrices (random columns 0.249 against
+// 0.258 ms, stencil 0.115 against 0.136 ms, 2-nonzero rows 0.080 against
+// 0.093 ms).
+template <int U>
+__global__ void __launch_bounds__(kSB, 8)
+k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+         const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+         const int* __restrict__ col, const double* __restrict__ val,
+         const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
+    if (s >= n_slices) return;  // whole warps only
+    const int lane = threadIdx.x & 31;
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    const int L = slice_len[s];
+    const int64_t q0 = slice_ptr[s] + lane;
+    const int* __restrict__ cp = col + q0;      // element k at cp[32 k] (k < 1025)
+    const double* __restrict__ vp = val + q0;
+    double acc = 0.0;
+    for (int k = 0; k < L; k += U) {
+        int c[U];
+        double a[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = k + u < len;
+            c[u] = ok ? __ldcs(cp + (k + u) * 32) : 0;
+            a[u] = ok ? __ldcs(vp + (k + u) * 32) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < len) acc = fma(a[u], xv[u], acc);
+    }
+    if (len >= 0) y[perm ? perm[p] : p] = acc;
+}
+
+// one warp per long row, from the CSR arrays
+__global__ void __launch_bounds__(kSB)
+k_sliced_long(int n_long, const int* __restrict__ list, const int* __restrict__ rp,
+              const int* __restrict__ ci, const double* __restrict__ v,
+              const double* __restrict__ x, double* __restrict__ y)
+{
+    const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
+    if (w >= n_long) return;
+    const int lane = threadIdx.x & 31;
+    const int r = list[w];
+    const double s = group_sum(row_partial<32, 8>(rp[r], rp[r + 1], lane, ColPlain<int>{ci}, v, x), 32);
+    if (lane == 0) y[r] = s;
+}
+
+unsigned grid_of(int64_t threads, int64_t cap_blocks)
+{
+    int64_t g = (threads + kSB - 1) / kSB;
+    if (g > cap_blocks) g = cap_blocks;
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+}  // namespace
+
+spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
+{
+    const spmv_csr_t& A = P->A;
+    SlicedPlan& d = P->sl;
+    const int cap = kSlicedCap;
+    d.n_slices = (A.n_rows + 31) / 32;
+    const int64_t n_pos = 32 * d.n_slices;
+    spmv_status st;
+    if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.rowlen), 4 * std::max<int64_t>(n_pos, 1))) != SPMV_OK ||
+        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.slice_len), 4 * std::max<int64_t>(d.n_slices, 1))) != SPMV_OK ||
+        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.slice_ptr), 8 * (d.n_slices + 1))) != SPMV_OK ||
+        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.count), 4)) != SPMV_OK)
+        return st;
+    const unsigned rows_grid = grid_of(A.n_rows, (int64_t)P->sm_count * 16);
+    const unsigned slice_grid = grid_of(n_pos, INT32_MAX);
+    std::vector<int> slen((size_t)std::max<int64_t>(d.n_slices, 1));
+    std::vector<int64_t> sptr((size_t)d.n_slices + 1, 0);
+    unsigned n_long = 0;
+    // one layout pass for window length sigma (1 = rows in order)
+    auto layout = [&](int sigma) -> spmv_status {
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.rowlen, 0xFF, 4 * std::max<int64_t>(n_pos, 1), s));
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
+        if (A.n_rows > 0) {
+            if (sigma == 1) {
+                k_sl_rowlen_identity<<<rows_grid, kSB, 0, s>>>(A.n_rows, A.rowptr, cap, d.rowlen, d.count);
+            } else {
+                if (!d.perm) {
+                    spmv_status st2 = prepared_alloc(P, reinterpret_cast<void**>(&d.perm), 4 * A.n_rows);
+                    if (st2 != SPMV_OK) return st2;
+                }
+                const int64_t n_win = (A.n_rows + sigma - 1) / sigma;
+                k_sl_sort<<<(unsigned)n_win, kSortT, sizeof(unsigned long long) * sigma, s>>>(
+                    A.n_rows, A.rowptr, sigma, cap, d.perm, d.rowlen, d.count);
+            }
+            SPMV_CUDA_TRY(cudaGetLastError());
+            k_sl_slice_len<<<slice_grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len);
+            SPMV_CUDA_TRY(cudaGetLastError());
+            SPMV_CUDA_TRY(cudaMemcpyAsync(slen.data(), d.slice_len, 4 * d.n_slices, cudaMemcpyDeviceToHost, s));
+        }
+        SPMV_CUDA_TRY(cudaMemcpyAsync(&n_long, d.count, 4, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < d.n_slices; ++i) sptr[i + 1] = sptr[i] + 32 * (int64_t)slen[i];
+        return SPMV_OK;
+    };
+    int sigma = P->c.block_nnz;
+    if (sigma == 0) {
+        // rows in order unless that pads the slices by more than a quarter
+        if ((st = layout(1)) != SPMV_OK) return st;
+        sigma = sptr[d.n_slices] <= A.nnz + A.nnz / 4 ? 1 : 256;
+        if (sigma != 1 && (st = layout(sigma)) != SPMV_OK) return st;
+    } else if ((st = layout(sigma)) != SPMV_OK) {
+        return st;
+    }
+    P->c.block_nnz = sigma;
+    d.sigma = sigma;
+    d.n_long = (int)n_long;
+    d.tot = sptr[d.n_slices];
+    SPMV_CUDA_TRY(cudaMemcpyAsync(d.slice_ptr, sptr.data(), 8 * (d.n_slices + 1), cudaMemcpyHostToDevice, s));
+    if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.col), 4 * std::max<int64_t>(d.tot, 1))) != SPMV_OK ||
+        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.val), 8 * std::max<int64_t>(d.tot, 1))) != SPMV_OK)
+        return st;
+    SPMV_CUDA_TRY(cudaMemsetAsync(d.col, 0, 4 * std::max<int64_t>(d.tot, 1), s));
+    SPMV_CUDA_TRY(cudaMemsetAsync(d.val, 0, 8 * std::max<int64_t>(d.tot, 1), s));
+    if (d.n_slices > 0) {
+        k_sl_fill<<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val,
+                                             sigma > 1 ? d.perm : nullptr, d.rowlen, d.slice_ptr,
+                                             d.col, d.val);
+        SPMV_CUDA_TRY(cudaGetLastError());
+    }
+    if (d.n_long > 0) {
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.long_rows), 4 * (int64_t)d.n_long)) != SPMV_OK)
+            return st;
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
+        k_sl_long_list<<<rows_grid, kSB, 0, s>>>(A.n_rows, A.rowptr, cap, d.long_rows, d.count);
+        SPMV_CUDA_TRY(cudaGetLastError());
+    }
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
+    P->n_blocks = d.n_slices;
+    return SPMV_OK;
+}
+
+cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cudaStream_t s)
+{
+    const spmv_csr_t& A = P->A;
+    const SlicedPlan& d = P->sl;
+    if (A.n_rows == 0) return cudaSuccess;
+    k_sliced<4><<<grid_of(32 * d.n_slices, INT32_MAX), kSB, 0, s>>>(
+        d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, d.sigma > 1 ? d.perm : nullptr, d.col, d.val, x, y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || d.n_long == 0) return e;
+    k_sliced_long<<<grid_of(32 * (int64_t)d.n_long, INT32_MAX), kSB, 0, s>>>(
+        d.n_long, d.long_rows, A.rowptr, A.colind, A.val, x, y);
+    return cudaGetLastError();
+}
+
+}  // namespace spmvlib

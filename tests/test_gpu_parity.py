@@ -69,6 +69,8 @@ CHOICES = [
     ("latency", {"threads_per_row": 32}),
     ("compressed", {}), ("compressed", {"threads_per_row": 1}),
     ("compressed", {"threads_per_row": 32}),
+    ("sliced", {}), ("sliced", {"block_nnz": 1}), ("sliced", {"block_nnz": 32}),
+    ("sliced", {"block_nnz": 4096}),
 ]
 
 
@@ -273,6 +275,49 @@ def _export(P, which, n, dtype):
     t = torch.empty(n, dtype=dtype)
     sp.spmv_prepared_export(P, which, t)
     return t.numpy()
+
+
+@pytest.mark.parametrize("sigma", [1, 32, 256])
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_sliced_layout_bit_exact(sigma, name, A):
+    """The SLICED prepared arrays equal the oracle's sliced layout."""
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma))
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, 1024)
+    S = (A.n_rows + 31) // 32
+    info = P.info()
+    assert info.n_blocks == S and info.block_nnz == sigma
+    assert info.launches == (0 if A.n_rows == 0 else (2 if n_long else 1))
+    if S == 0:
+        return
+    assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWLEN, 32 * S, torch.int32), rowlen)
+    assert np.array_equal(_export(P, sp.EXPORT_SLICE_LEN, S, torch.int32), slen)
+    assert np.array_equal(_export(P, sp.EXPORT_SLICE_PTR, S + 1, torch.int64), sptr)
+    if sigma > 1:
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_PERM, A.n_rows, torch.int32), perm)
+    else:
+        with pytest.raises(sp.SpmvError):
+            _export(P, sp.EXPORT_SLICE_PERM, A.n_rows, torch.int32)
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    tot = int(sptr[-1])
+    if tot:
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_COL, tot, torch.int32), col)
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_VAL, tot, torch.float64), val)
+
+
+def test_sliced_auto_window_and_long_rows():
+    # regular rows: kept in order; Zipf rows: sorted in windows of 256, and
+    # the rows above 1024 nonzeros computed from CSR
+    L = synth.laplacian_2d_5pt(100, 100)
+    assert sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced")).info().block_nnz == 1
+    Z = synth.zipf_rows(60_000, 60_000, 1.4, 20_000, seed=9)
+    P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced"))
+    assert P.info().block_nnz == 256 and P.info().launches == 2
+    y, x = _run(Z, sp.make_choice("sliced"))
+    _assert_close(y, Z, x)
+    for bad in (2, 16, 8192):
+        with pytest.raises(sp.SpmvError):
+            sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced", block_nnz=bad))
 
 
 @pytest.mark.parametrize("name,A", MATS[:6], ids=[m[0] for m in MATS[:6]])

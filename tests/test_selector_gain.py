@@ -48,7 +48,7 @@ def _geomean(a):
 
 def test_dataset_shape(data):
     d, P, variants, k = data
-    assert d["seed"].size == 2000 and d["times"].shape == (2000, k) and k == len(sp.VARIANTS)
+    assert d["seed"].size == 2000 and d["times"].shape == (2000, k) and k <= len(sp.VARIANTS)
     assert np.array_equal(np.sort(d["seed"]), np.arange(2000))
     assert np.all(d["times"] > 0)
 
