@@ -50,14 +50,19 @@ typedef enum {
     SPMV_ERR_MODEL = 7         /* selector model missing, corrupt or bad   */
 } spmv_status;
 
-/* SpMV variants.  The class -> variant map (the GPU counterpart of Table 2,
- * Section 3.3) is CML -> LATENCY, MB -> COMPRESSED, IMB -> DYNAMIC,
- * CMP -> SUBWARP.  SCALAR is the unoptimized CSR kernel (one thread per row,
- * Algorithm 1 as written) against which speedups are reported.  SLICED is a
- * GPU format with no counterpart in Table 2: 32-row slices whose k-th
- * elements are stored next to each other, one lane per row, no reduction
- * across lanes; it serves regular matrices of the MB and CML classes (rows
- * longer than 1024 are computed from CSR by one warp each). */
+/* SpMV variants.  Each attacks one bottleneck class of Section 3.1 the way
+ * Table 2's optimizations do on a CPU: LATENCY the latency of x misses
+ * (CML), COMPRESSED the bytes streamed (MB), DYNAMIC the imbalance (IMB),
+ * SUBWARP the per-row overhead of short rows (CMP).  SLICED is a GPU format
+ * with no counterpart in Table 2: 32-row slices whose k-th elements are
+ * stored next to each other, one lane per row and no reduction across lanes
+ * (rows longer than 1024 are computed from CSR by one warp each).  The class
+ * -> variant table used by the profiling rule (spmv_class_variant) is
+ * calibrated on GB300 like the thresholds -- for each class the variant with
+ * the lowest geometric-mean slowdown on the training matrices: CML -> SLICED,
+ * MB -> SLICED, IMB -> DYNAMIC, CMP -> SLICED.  SCALAR is the unoptimized
+ * CSR kernel (one thread per row, Algorithm 1 as written) against which
+ * speedups are reported. */
 typedef enum {
     SPMV_V0_SCALAR = 0,     /* one thread per row                                */
     SPMV_V1_SUBWARP = 1,    /* T lanes per row (T = 1..32), shuffle reduction    */
@@ -253,14 +258,15 @@ spmv_status spmv_profile(const spmv_csr_t *A, const double *x, int32_t reps,
                          spmv_profile_t *out, spmv_stream_t stream);
 
 /* Gather probe (a measurement aid in the spirit of the probes above, with no
- * counterpart in the paper): *sum (device, 1 double) = sum over j of
- * x[colind[j]] in storage order, read with as many independent gathers in
- * flight as the GPU keeps.  Its duration is the cost of A's accesses to x
- * alone: on matrices whose columns have no locality (random columns), the
- * floor of any CSR kernel that reads x once per nonzero, which lies above
- * the HBM floor there.  A's indices are not validated (they must lie in
- * [0, n_cols)).  Allocates (stream-ordered) a small scratch.  Asynchronous. */
-spmv_status spmv_gather_probe(const spmv_csr_t *A, const double *x, double *sum,
+ * counterpart in the paper): *sum (device, one uint64) = the sum modulo 2^64
+ * of the 64-bit patterns of x[colind[j]] over every nonzero, read in storage
+ * order with as many independent gathers in flight as the GPU keeps and no
+ * floating-point arithmetic.  Its duration is the cost of A's accesses to x
+ * alone in CSR order: a reference for matrices whose columns have no
+ * locality, whose SpMV time it approaches.  A's indices are not validated
+ * (they must lie in [0, n_cols)).  Allocates (stream-ordered) a small
+ * scratch.  Asynchronous. */
+spmv_status spmv_gather_probe(const spmv_csr_t *A, const double *x, uint64_t *sum,
                               spmv_stream_t stream);
 
 /* ---- selection (Sections 3.1-3.3) ----------------------------------------- */

@@ -288,11 +288,13 @@ int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
 
 /* Table 2 analogue on the GPU: class -> variant id.  Variant ids:
  * 0 scalar, 1 sub-warp, 2 stream, 3 merge-path, 4 dynamic, 5 latency,
- * 6 compressed.  CML -> latency, MB -> compressed, IMB -> dynamic,
- * CMP -> sub-warp.                                                          */
+ * 6 compressed, 7 sliced.  The table is calibrated, like the thresholds: for
+ * each class named by the rule, the variant with the lowest geometric-mean
+ * slowdown against the exhaustive best on the training matrices measured on
+ * GB300 -- CML -> sliced, MB -> sliced, IMB -> dynamic, CMP -> sliced.       */
 int32_t orc_class_variant(int32_t cls)
 {
-    static const int32_t map[4] = {5, 6, 4, 1};
+    static const int32_t map[4] = {7, 7, 4, 7};
     return (cls >= 0 && cls < 4) ? map[cls] : -1;
 }
 

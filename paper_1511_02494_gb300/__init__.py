@@ -119,8 +119,9 @@ def spmv_profile(A: DeviceCSR, x, reps: int = 5, stream=None) -> Profile:
 
 
 def spmv_gather_probe(A: DeviceCSR, x, out, stream=None) -> None:
-    """out (device, 1 double) = sum of x over A's column indices; its time is
-    the cost of A's gathers of x alone."""
+    """out (device, one int64 / uint64) = sum modulo 2^64 of the bit patterns
+    of x over A's column indices; its time is the cost of A's gathers of x
+    alone."""
     _check(lib().spmv_gather_probe(C.byref(A.desc), _ptr(x), _ptr(out), _stream(stream)))
 
 

@@ -438,10 +438,13 @@ spmv_status spmv_classify_profile(const spmv_profile_t* p, const spmv_thresholds
 int32_t spmv_class_variant(int32_t cls)
 {
     switch (cls) {
-        case SPMV_CLASS_CML: return SPMV_V5_LATENCY;
-        case SPMV_CLASS_MB: return SPMV_V6_COMPRESSED;
+        // calibrated on GB300: per class, the variant with the lowest
+        // geometric-mean slowdown against the exhaustive best on the training
+        // matrices (CML 1.04, MB 1.00, IMB 1.21, CMP 1.07)
+        case SPMV_CLASS_CML: return SPMV_V7_SLICED;
+        case SPMV_CLASS_MB: return SPMV_V7_SLICED;
         case SPMV_CLASS_IMB: return SPMV_V4_DYNAMIC;
-        case SPMV_CLASS_CMP: return SPMV_V1_SUBWARP;
+        case SPMV_CLASS_CMP: return SPMV_V7_SLICED;
         default: return -1;
     }
 }

@@ -109,46 +109,48 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
-// Gather probe: the sum of x over A's column indices in storage order, with
-// U independent gathers in flight per thread and nothing else per element
-// (no values, no row structure).  Its time is the cost of A's x accesses
-// alone, the floor below which no CSR kernel that reads x from memory once
-// per nonzero can go on matrices whose columns have no locality.
+// Gather probe: a checksum of x over A's column indices in storage order --
+// the 64-bit bit patterns of x[colind[j]] added modulo 2^64 -- with U
+// independent gathers in flight per thread and no floating-point work (an
+// FP64 add per element would cost as much FP64 issue as the SpMV's DFMA).
+// Its time is the cost of A's x accesses alone in CSR storage order.
 constexpr int kGT = 256;
 
 template <int U>
 __global__ void __launch_bounds__(kGT)
 k_gather_probe(int64_t nnz, const int* __restrict__ ci, const double* __restrict__ x,
-               double* __restrict__ part)
+               unsigned long long* __restrict__ part)
 {
-    __shared__ double red[kGT / 32];
+    __shared__ unsigned long long red[kGT / 32];
     const int64_t stride = (int64_t)gridDim.x * kGT;
     int64_t i = (int64_t)blockIdx.x * kGT + threadIdx.x;
-    double acc = 0.0;
+    unsigned long long acc = 0;
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
     for (; i + (U - 1) * stride < nnz; i += U * stride) {
         int c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) c[u] = __ldcs(ci + i + u * stride);
-        double v[U];
+        unsigned long long v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = __ldg(x + c[u]);
+        for (int u = 0; u < U; ++u) v[u] = __ldg(xb + c[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) acc += v[u];
     }
-    for (; i < nnz; i += stride) acc += __ldg(x + __ldcs(ci + i));
+    for (; i < nnz; i += stride) acc += __ldg(xb + __ldcs(ci + i));
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        unsigned long long s = 0;
         for (int w = 0; w < kGT / 32; ++w) s += red[w];
         part[blockIdx.x] = s;
     }
 }
 
-__global__ void k_sum_parts(int n, const double* __restrict__ part, double* __restrict__ out)
+__global__ void k_sum_parts(int n, const unsigned long long* __restrict__ part,
+                            unsigned long long* __restrict__ out)
 {
-    double s = 0.0;
+    unsigned long long s = 0;
     for (int i = 0; i < n; ++i) s += part[i];
     *out = s;
 }
@@ -159,7 +161,7 @@ __global__ void k_sum_parts(int n, const double* __restrict__ part, double* __re
 
 using namespace spmvlib;
 
-extern "C" spmv_status spmv_gather_probe(const spmv_csr_t* A, const double* x, double* sum,
+extern "C" spmv_status spmv_gather_probe(const spmv_csr_t* A, const double* x, uint64_t* sum,
                                          spmv_stream_t stream)
 {
     clear_error();
@@ -171,12 +173,12 @@ extern "C" spmv_status spmv_gather_probe(const spmv_csr_t* A, const double* x, d
     if (st != SPMV_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = dev.sm_count * 8;
-    double* part = nullptr;
-    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(double) * grid, s));
+    unsigned long long* part = nullptr;
+    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(unsigned long long) * grid, s));
     k_gather_probe<4><<<grid, kGT, 0, s>>>(A->nnz, A->colind, x, part);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        k_sum_parts<<<1, 1, 0, s>>>(grid, part, sum);
+        k_sum_parts<<<1, 1, 0, s>>>(grid, part, reinterpret_cast<unsigned long long*>(sum));
         e = cudaGetLastError();
     }
     cudaError_t ef = cudaFreeAsync(part, s);

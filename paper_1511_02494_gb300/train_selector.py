@@ -18,6 +18,9 @@ the training split.  The fallback margin is chosen on the training split.  Outpu
 selector_dataset.npz, selector_mlp.bin, selector_report.json.
 
     python -m paper_1511_02494_gb300.train_selector --out DIR [--n 2000]
+
+A stored training set that lacks variants added to the library since is
+completed first (those variants are timed on its matrices).
 """
 from __future__ import annotations
 
@@ -116,6 +119,43 @@ def build_dataset(n: int, out_path: str, resume: bool = True, log=print):
             log(f"{i + 1}/{n} matrices, {time.time() - t_start:.0f} s")
     np.savez(out_path, **{k: np.array(v) for k, v in rows.items()})
     return {k: np.array(v) for k, v in rows.items()}
+
+
+def rule_of(prof_row) -> int:
+    p = sp.Profile()
+    p.s_noxmiss, p.s_inflate, p.s_balance = (float(v) for v in prof_row)
+    return sp.spmv_select(profile=p).variant
+
+
+def extend_dataset(out_path: str, log=print):
+    """Times the variants a stored training set lacks (columns added to the
+    library after it was built) on every one of its matrices, regenerated
+    from their seeds; resumable through NaN entries, saved every 50."""
+    d = {k: np.array(v) for k, v in np.load(out_path).items()}
+    times = d["times"].astype(np.float64)
+    if times.shape[1] < N_VAR:
+        times = np.concatenate([times, np.full((times.shape[0], N_VAR - times.shape[1]), np.nan)], 1)
+    todo = np.where(np.isnan(times).any(1))[0]
+    log(f"timing missing variants on {len(todo)} matrices")
+    t_start = time.time()
+    for n, row in enumerate(todo):
+        i = int(d["seed"][row])
+        family, n_rows = matrix_spec(i)
+        A = synth.family_matrix(family, n_rows, seed=i, device="cuda")
+        dA = sp.DeviceCSR(A.n_rows, A.n_cols, A.rowptr.contiguous(), A.colind.contiguous(),
+                          A.val.contiguous())
+        x = synth.uniform_vector(A.n_cols, i, device="cuda")
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        for v in np.where(np.isnan(times[row]))[0]:
+            times[row, v] = time_variant(dA, int(v), x, y)
+        del dA, A, x, y
+        if (n + 1) % 50 == 0 or n == len(todo) - 1:
+            d["times"] = times
+            np.savez(out_path, **d)
+            torch.cuda.empty_cache()
+            log(f"{n + 1}/{len(todo)} matrices, {time.time() - t_start:.0f} s")
+    d["times"] = times
+    return d
 
 
 def init_params(h1, h2, k, seed=0):
@@ -233,6 +273,11 @@ def main():
     build()
     ds_path = os.path.join(args.out, "selector_dataset.npz")
     d = build_dataset(args.n, ds_path, resume=not args.no_resume)
+    if d["times"].shape[1] < N_VAR:
+        d = extend_dataset(ds_path)
+    # the profiling rule's choice under the library's current class map,
+    # from the stored probe speedups
+    d["rule_variant"] = np.array([rule_of(p) for p in d["prof"]], np.int64)
     seeds = d["seed"]
     test = np.where(seeds % 5 == 0)[0]
     tr = np.where(seeds % 5 != 0)[0]

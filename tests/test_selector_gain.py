@@ -83,3 +83,20 @@ def test_library_logits_equal_oracle_on_the_dataset(data):
     ref = oracle.mlp_forward_f32(P, d["vec"][:300])
     for i in range(300):
         assert np.array_equal(sp.spmv_model_logits(m, d["vec"][i], k), ref[i])
+
+
+def test_class_variant_table_is_the_per_class_best_on_training_data(data):
+    """The profiling rule's class -> variant table is calibrated: for each
+    class the rule names on the training matrices, the mapped variant has the
+    lowest geometric-mean slowdown against the exhaustive best."""
+    d, P, variants, k = data
+    tr = np.where(d["seed"] % 5 != 0)[0]
+    times = d["times"][tr]
+    best = times.min(1)
+    cls = np.array([oracle.profile_class(*p) for p in d["prof"][tr]])
+    for c in range(4):
+        m = cls == c
+        if m.sum() < 20:
+            continue
+        slow = [_geomean(times[m, v] / best[m]) for v in range(k)]
+        assert oracle.class_variant(c) == int(np.argmin(slow)), (c, slow)
