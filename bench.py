@@ -507,7 +507,8 @@ def run_cg(args):
 
 def run_batch(args):
     """512 uneven matrices: one launch per matrix with each matrix's own
-    selected variant, against one persistent launch (plain, graph, autotuned)."""
+    selected variant, against one persistent launch that runs every matrix
+    with its selected variant (plain, graph, autotuned)."""
     import numpy as np
     import torch
     import paper_1511_02494_gb300 as sp
@@ -536,9 +537,9 @@ def run_batch(args):
         for P, x, y in zip(preps, xs, ys):
             sp.spmv(P, x, y)
     ms_sep = _time_ms(per_matrix, reps=5, warm=2)
-    # batch lanes per row: from each matrix's selected variant's prepared shape
-    tpr = [P.info().threads_per_row for P in preps]  # 0 (merge, stream, dynamic): from the mean
-    B = sp.spmv_batch_create(dev, threads_per_row=tpr)
+    # one persistent launch, each matrix with its selected variant (SLICED as
+    # slices, the others as CSR rows with their prepared lanes per row)
+    B = sp.spmv_batch_create_prepared(preps)
     sp.spmv_batch_bind(B, xs, ys)
     ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)
     ms_graph = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)

@@ -404,6 +404,13 @@ typedef struct spmv_batch spmv_batch_t;
 spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
                               const int32_t *threads_per_row, const int32_t *rows_per_item,
                               spmv_batch_t **out, spmv_stream_t stream);
+/* A batch of prepared matrices (borrowed; they must outlive the batch), each
+ * run with its own variant inside the one persistent launch: a SLICED
+ * matrix as work items of 4 slices (its long rows one item each), any other
+ * variant as CSR row items with its prepared lanes per row (from the mean
+ * row length when it has none).  Synchronizes `stream`. */
+spmv_status spmv_batch_create_prepared(const spmv_prepared_t *const *P, int32_t count,
+                                       spmv_batch_t **out, spmv_stream_t stream);
 /* Sets the vectors: x[m], y[m] are device pointers (host arrays of count
  * pointers).  Must precede spmv_batch_run; synchronizes `stream`. */
 spmv_status spmv_batch_bind(spmv_batch_t *B, const double *const *x, double *const *y,
@@ -413,7 +420,8 @@ spmv_status spmv_batch_bind(spmv_batch_t *B, const double *const *x, double *con
  * the graph is launched on `stream` from then on.  Asynchronous. */
 spmv_status spmv_batch_run(spmv_batch_t *B, int32_t use_graph, spmv_stream_t stream);
 /* Tunes the launch shapes for the throughput of the whole batch: matrices
- * are grouped by the binary order of their mean row length; coordinate
+ * are grouped by the binary order of their mean row length (SLICED matrices
+ * apart, with one lane per row and only the slices per item tuned); coordinate
  * descent over the groups (most nonzeros first, two sweeps) tries lanes per
  * row T in {1, 2, ..., 32}, then rows per item in {2, 4, ..., 32} passes of
  * 32/T rows, timing the whole batch launch (median of reps, 0 = 3) and

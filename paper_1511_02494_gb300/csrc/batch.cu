@@ -30,10 +30,21 @@ struct BatchMat {
     const double* x;
     double* y;
     int64_t n_rows;
+    // sliced layout (matrices prepared as SLICED), else null
+    const int* rowlen;
+    const int* slice_len;
+    const int64_t* slice_ptr;
+    const int* perm;
+    const int* scol;
+    const double* sval;
+    const int* long_rows;
 };
 
+// lg 0..5: rows [r0, r1) with 2^lg lanes per row; kSliceItem: slices
+// [r0, r1) of a sliced matrix; kLongItem: entries [r0, r1) of its long-row list
+constexpr int32_t kSliceItem = 8, kLongItem = 9;
 struct BatchItem {
-    int32_t m, r0, r1, lg;  // matrix, rows [r0, r1), log2 of lanes per row
+    int32_t m, r0, r1, lg;
 };
 
 struct spmv_batch {
@@ -41,6 +52,7 @@ struct spmv_batch {
     int sm_count = 0;
     std::vector<spmv_csr_t> mats;
     std::vector<int32_t> tpr, rpi;   // lanes per row, rows per item
+    std::vector<const spmv_prepared*> preps;  // SLICED matrices' prepared objects, else null
     std::vector<const double*> xs;
     std::vector<double*> ys;
     BatchMat* d_mats = nullptr;
@@ -84,6 +96,19 @@ k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, 
         const BatchItem I = items[it];
         const BatchMat M = mats[I.m];
         switch (I.lg) {
+            case kSliceItem:
+                for (int s = I.r0; s < I.r1; ++s)
+                    slice_rows<4>(s, lane, M.rowlen, M.slice_len, M.slice_ptr, M.perm, M.scol, M.sval,
+                                  M.x, M.y);
+                break;
+            case kLongItem:
+                for (int q = I.r0; q < I.r1; ++q) {
+                    const int r = M.long_rows[q];
+                    const double s = group_sum(
+                        row_partial<32, 8>(M.rp[r], M.rp[r + 1], lane, ColPlain<int>{M.ci}, M.v, M.x), 32);
+                    if (lane == 0) M.y[r] = s;
+                }
+                break;
             case 0: batch_rows<1>(M, I.r0, I.r1, lane); break;
             case 1: batch_rows<2>(M, I.r0, I.r1, lane); break;
             case 2: batch_rows<4>(M, I.r0, I.r1, lane); break;
@@ -113,6 +138,15 @@ std::vector<BatchItem> make_items(const spmv_batch* B, const std::vector<int32_t
 {
     std::vector<BatchItem> items;
     for (size_t m = 0; m < B->mats.size(); ++m) {
+        const spmv_prepared* P = B->preps[m];
+        if (P) {
+            // rows per item / 32 slices per item, then one item per long row
+            const int ns = (int)P->sl.n_slices;
+            const int k = std::max(1, rpi[m] / 32);
+            for (int s0 = 0; s0 < ns; s0 += k) items.push_back({(int32_t)m, s0, std::min(ns, s0 + k), kSliceItem});
+            for (int q = 0; q < P->sl.n_long; ++q) items.push_back({(int32_t)m, q, q + 1, kLongItem});
+            continue;
+        }
         const int n = (int)B->mats[m].n_rows;
         const int r = rpi[m];
         for (int r0 = 0; r0 < n; r0 += r) items.push_back({(int32_t)m, r0, std::min(n, r0 + r), lg2(tpr[m])});
@@ -132,6 +166,21 @@ spmv_status build_items(spmv_batch* B, cudaStream_t s)
                                   cudaMemcpyHostToDevice, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+    return SPMV_OK;
+}
+
+spmv_status finish_create(spmv_batch* B, int32_t count, cudaStream_t s, spmv_batch_t** out)
+{
+    B->xs.assign(count, nullptr);
+    B->ys.assign(count, nullptr);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&B->d_counter), 8);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, 8, s);
+    if (e == cudaSuccess && count > 0)
+        e = cudaMalloc(reinterpret_cast<void**>(&B->d_mats), sizeof(BatchMat) * count);
+    if (e != cudaSuccess) { spmv_batch_free(B); return cuda_fail(e, "spmv_batch_create"); }
+    spmv_status st = build_items(B, s);
+    if (st != SPMV_OK) { spmv_batch_free(B); return st; }
+    *out = B;
     return SPMV_OK;
 }
 
@@ -186,17 +235,44 @@ spmv_status spmv_batch_create(const spmv_csr_t* mats, int32_t count, const int32
         B->mats.push_back(mats[m]);
         B->tpr.push_back(T);
         B->rpi.push_back(r);
+        B->preps.push_back(nullptr);
     }
-    B->xs.assign(count, nullptr);
-    B->ys.assign(count, nullptr);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&B->d_counter), 8);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, 8, s);
-    if (e == cudaSuccess && count > 0)
-        e = cudaMalloc(reinterpret_cast<void**>(&B->d_mats), sizeof(BatchMat) * count);
-    if (e != cudaSuccess) { spmv_batch_free(B); return cuda_fail(e, "spmv_batch_create"); }
-    if ((st = build_items(B, s)) != SPMV_OK) { spmv_batch_free(B); return st; }
-    *out = B;
-    return SPMV_OK;
+    return finish_create(B, count, s, out);
+}
+
+spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t count,
+                                       spmv_batch_t** out, spmv_stream_t stream)
+{
+    clear_error();
+    if (!out || count < 0 || (count > 0 && !P))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_batch_create_prepared: bad argument");
+    *out = nullptr;
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spmv_batch* B = new (std::nothrow) spmv_batch();
+    if (!B) return fail(SPMV_ERR_NOMEM, "host allocation failed");
+    B->device = dev.device;
+    B->sm_count = dev.sm_count;
+    for (int m = 0; m < count; ++m) {
+        const spmv_prepared* Pm = P[m];
+        if (!Pm) { spmv_batch_free(B); return fail(SPMV_ERR_INVALID_ARG, "NULL prepared matrix"); }
+        if (Pm->device != dev.device) {
+            spmv_batch_free(B);
+            return fail(SPMV_ERR_INVALID_ARG, "prepared on another device");
+        }
+        const spmv_csr_t& A = Pm->A;
+        const bool sliced = Pm->c.variant == SPMV_V7_SLICED;
+        const double mean = A.n_rows ? (double)A.nnz / (double)A.n_rows : 1.0;
+        const int t = Pm->c.threads_per_row;
+        const int T = sliced ? 1 : (t >= 1 && t <= 32 && !(t & (t - 1)) ? t : auto_threads_per_row(mean / 7.0));
+        B->mats.push_back(A);
+        B->tpr.push_back(T);
+        B->rpi.push_back(sliced ? 4 * 32 : 8 * (32 / T));
+        B->preps.push_back(sliced ? Pm : nullptr);
+    }
+    return finish_create(B, count, s, out);
 }
 
 spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* const* y,
@@ -208,7 +284,18 @@ spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* con
     std::vector<BatchMat> h(B->mats.size());
     for (size_t m = 0; m < B->mats.size(); ++m) {
         const spmv_csr_t& A = B->mats[m];
-        h[m] = {A.rowptr, A.colind, A.val, x[m], y[m], A.n_rows};
+        h[m] = {A.rowptr, A.colind, A.val, x[m], y[m], A.n_rows,
+                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (const spmv_prepared* P = B->preps[m]) {
+            const SlicedPlan& d = P->sl;
+            h[m].rowlen = d.rowlen;
+            h[m].slice_len = d.slice_len;
+            h[m].slice_ptr = d.slice_ptr;
+            h[m].perm = d.sigma > 1 ? d.perm : nullptr;
+            h[m].scol = d.col;
+            h[m].sval = d.val;
+            h[m].long_rows = d.long_rows;
+        }
         B->xs[m] = x[m];
         B->ys[m] = y[m];
     }
@@ -263,17 +350,18 @@ spmv_status spmv_batch_autotune(spmv_batch_t* B, int32_t reps, spmv_stream_t str
     const size_t count = B->mats.size();
     // groups: binary order of the mean row length
     std::vector<int> group(count, 0);
-    std::vector<int64_t> group_nnz(32, 0);
+    std::vector<int64_t> group_nnz(64, 0);
     for (size_t m = 0; m < count; ++m) {
         const spmv_csr_t& A = B->mats[m];
         const double mean = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
         int g = 0;
         while (g < 31 && (double)(2 << g) <= mean) ++g;
+        if (B->preps[m]) g += 32;  // sliced matrices: their own groups, one lane per row
         group[m] = g;
         group_nnz[g] += A.nnz;
     }
     std::vector<int> order;
-    for (int g = 0; g < 32; ++g)
+    for (int g = 0; g < 64; ++g)
         if (group_nnz[g] > 0) order.push_back(g);
     std::sort(order.begin(), order.end(), [&](int a, int b_) { return group_nnz[a] > group_nnz[b_]; });
 
@@ -322,7 +410,7 @@ spmv_status spmv_batch_autotune(spmv_batch_t* B, int32_t reps, spmv_stream_t str
             int gm = -1;
             for (size_t m = 0; m < count; ++m) if (group[m] == g) { gm = (int)m; break; }
             int bestT = tpr[gm], bestP = std::max(1, rpi[gm] / (32 / tpr[gm]));
-            for (int T = 1; T <= 32 && e == cudaSuccess; T <<= 1) {
+            for (int T = 1; T <= (g >= 32 ? 1 : 32) && e == cudaSuccess; T <<= 1) {
                 std::vector<int32_t> tv = tpr, rv = rpi;
                 set_group(tv, rv, g, T, bestP);
                 float ms;

@@ -162,30 +162,7 @@ k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict
 {
     const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
     if (s >= n_slices) return;  // whole warps only
-    const int lane = threadIdx.x & 31;
-    const int64_t p = s * 32 + lane;
-    const int len = rowlen[p];
-    const int L = slice_len[s];
-    const int64_t q0 = slice_ptr[s] + lane;
-    const int* __restrict__ cp = col + q0;      // element k at cp[32 k] (k < 1025)
-    const double* __restrict__ vp = val + q0;
-    double acc = 0.0;
-    for (int k = 0; k < L; k += U) {
-        int c[U];
-        double a[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = k + u < len;
-            c[u] = ok ? __ldcs(cp + (k + u) * 32) : 0;
-            a[u] = ok ? __ldcs(vp + (k + u) * 32) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (k + u < len) acc = fma(a[u], xv[u], acc);
-    }
-    if (len >= 0) y[perm ? perm[p] : p] = acc;
+    slice_rows<U>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
 }
 
 // one warp per long row, from the CSR arrays

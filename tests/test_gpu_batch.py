@@ -80,3 +80,40 @@ def test_batch_explicit_shapes(batch_case):
         B.free()
     with pytest.raises(sp.SpmvError):
         sp.spmv_batch_create(dev, threads_per_row=[3] * n)
+
+
+def test_batch_of_prepared_matrices_runs_each_variant(batch_case):
+    """SLICED matrices run as slices (sorted, with long rows, and in order),
+    the others as CSR rows with their prepared lanes per row."""
+    mats, dev, xs, ys = batch_case
+    extra = [synth.zipf_rows(20_000, 20_000, 1.4, 5_000, seed=11), synth.stencil_27pt(12, seed=2)]
+    mats = list(mats) + extra
+    dev = list(dev) + [sp.DeviceCSR.from_host(A) for A in extra]
+    xs = list(xs) + [synth.uniform_vector(A.n_cols, 77 + i).cuda() for i, A in enumerate(extra)]
+    ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats]
+    kinds = ["sliced", "subwarp", "dynamic", ("sliced", 256), "latency", "compressed"]
+    preps = []
+    for i, dA in enumerate(dev):
+        k = kinds[i % len(kinds)]
+        ch = sp.make_choice(k[0], block_nnz=k[1]) if isinstance(k, tuple) else sp.make_choice(k)
+        preps.append(sp.spmv_prepare(dA, ch))
+    B = sp.spmv_batch_create_prepared(preps)
+    sp.spmv_batch_bind(B, xs, ys)
+    sp.spmv_batch_run(B)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    for y in ys:
+        y.fill_(float("nan"))
+    sp.spmv_batch_run(B, use_graph=True)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    sp.spmv_batch_autotune(B, reps=2)
+    t, r = sp.spmv_batch_config(B)
+    sl = [i for i, P in enumerate(preps) if P.info().variant == sp.VARIANT_IDS["sliced"]]
+    assert sl and all(t[i] == 1 and r[i] % 32 == 0 for i in sl)
+    for y in ys:
+        y.fill_(float("nan"))
+    sp.spmv_batch_run(B, use_graph=True)
+    torch.cuda.synchronize()
+    _check(mats, xs, ys)
+    B.free()
