@@ -406,9 +406,11 @@ spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
                               spmv_batch_t **out, spmv_stream_t stream);
 /* A batch of prepared matrices (borrowed; they must outlive the batch), each
  * run with its own variant inside the one persistent launch: a SLICED
- * matrix as work items of 4 slices (its long rows one item each), any other
- * variant as CSR row items with its prepared lanes per row (from the mean
- * row length when it has none).  Synchronizes `stream`. */
+ * matrix as work items of 4 slices (its long rows one item each); a MERGE or
+ * DYNAMIC matrix (imbalance class) as slices of rows sorted by length in
+ * windows of 256, which the batch prepares and owns (CSR rows would make a
+ * warp run as many DFMAs as its longest row); any other variant as CSR row
+ * items with its prepared lanes per row.  Synchronizes `stream`. */
 spmv_status spmv_batch_create_prepared(const spmv_prepared_t *const *P, int32_t count,
                                        spmv_batch_t **out, spmv_stream_t stream);
 /* Sets the vectors: x[m], y[m] are device pointers (host arrays of count

@@ -53,6 +53,7 @@ struct spmv_batch {
     std::vector<spmv_csr_t> mats;
     std::vector<int32_t> tpr, rpi;   // lanes per row, rows per item
     std::vector<const spmv_prepared*> preps;  // SLICED matrices' prepared objects, else null
+    std::vector<spmv_prepared*> owned;        // sliced forms the batch prepared itself
     std::vector<const double*> xs;
     std::vector<double*> ys;
     BatchMat* d_mats = nullptr;
@@ -82,7 +83,7 @@ __device__ __forceinline__ void batch_rows(const BatchMat& M, int r0, int r1, in
     }
 }
 
-__global__ void __launch_bounds__(kBT)
+__global__ void __launch_bounds__(kBT, 6)
 k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int64_t n_items,
         unsigned* __restrict__ counter)
 {
@@ -263,6 +264,19 @@ spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t 
             return fail(SPMV_ERR_INVALID_ARG, "prepared on another device");
         }
         const spmv_csr_t& A = Pm->A;
+        // imbalance variants (MERGE, DYNAMIC) run as length-sorted slices: a
+        // warp of CSR rows would run as many DFMAs as its longest row
+        if (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC) {
+            spmv_choice_t c{};
+            c.variant = SPMV_V7_SLICED;
+            c.cls = -1;
+            c.block_nnz = 256;
+            spmv_prepared* Q = nullptr;
+            st = spmv_prepare(&A, &c, 1, &Q, stream);
+            if (st != SPMV_OK) { spmv_batch_free(B); return st; }
+            B->owned.push_back(Q);
+            Pm = Q;
+        }
         const bool sliced = Pm->c.variant == SPMV_V7_SLICED;
         const double mean = A.n_rows ? (double)A.nnz / (double)A.n_rows : 1.0;
         const int t = Pm->c.threads_per_row;
@@ -454,6 +468,7 @@ void spmv_batch_free(spmv_batch_t* B)
     if (B->d_items) cudaFree(B->d_items);
     if (B->d_mats) cudaFree(B->d_mats);
     if (B->d_counter) cudaFree(B->d_counter);
+    for (spmv_prepared* Q : B->owned) spmv_prepared_free(Q);
     delete B;
 }
 
