@@ -128,7 +128,7 @@ void release(spmv_prepared_t* P)
                     P->rowbase, P->off16, P->lowval, P->x_stage, P->y_stage, P->status,
                     P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32,
                     P->sl.rowlen, P->sl.slice_len, P->sl.slice_ptr, P->sl.perm, P->sl.col, P->sl.val,
-                    P->sl.long_rows, P->sl.count};
+                    P->sl.long_rows, P->sl.count, P->sl.seg_off, P->sl.partial};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -140,7 +140,7 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
-        case SPMV_V7_SLICED: return P->sl.n_long > 0 ? 2 : 1;      // + long rows
+        case SPMV_V7_SLICED: return P->sl.n_long > 0 ? 3 : 1;      // + long-row segments, fix-up
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
         default: return 1;
     }
@@ -155,7 +155,7 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
         // the permutation when rows are sorted, the long rows' CSR bounds
         const SlicedPlan& d = P->sl;
         return 12 * A.nnz + 128 * d.n_slices + 12 * d.n_slices + (d.sigma > 1 ? 4 * A.n_rows : 0) +
-               12 * (int64_t)d.n_long + 8 * A.n_cols + 8 * A.n_rows;
+               12 * (int64_t)d.n_long + 16 * (int64_t)d.n_seg + 8 * A.n_cols + 8 * A.n_rows;
     }
     if (P->c.variant != SPMV_V6_COMPRESSED) return 12 * A.nnz + vec;
     const int vb = P->c.value_type == SPMV_VAL_F64 ? 8 : P->c.value_type == SPMV_VAL_F32 ? 4 : 2;

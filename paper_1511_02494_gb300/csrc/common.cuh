@@ -54,8 +54,10 @@ struct DynPlan {
     double* partial = nullptr;  // one partial sum per segment
 };
 
-// SLICED (V7): rows longer than this are computed from CSR, one warp each
+// SLICED (V7): rows longer than kSlicedCap are computed from CSR in segments
+// of kSlicedSeg nonzeros, one warp each
 constexpr int kSlicedCap = 1024;
+constexpr int kSlicedSeg = 2048;
 
 struct SlicedPlan {
     int64_t n_slices = 0, tot = 0;
@@ -66,7 +68,10 @@ struct SlicedPlan {
     int* perm = nullptr;         // [n_rows] position -> row (sigma > 1 only)
     int* col = nullptr;          // [tot] column-major slice contents
     double* val = nullptr;       // [tot]
-    int* long_rows = nullptr;    // [n_long]
+    int* long_rows = nullptr;    // [n_long], ascending
+    int* seg_off = nullptr;      // [n_long + 1] first segment of each long row
+    double* partial = nullptr;   // [n_seg] segment sums
+    int n_seg = 0;
     unsigned* count = nullptr;   // scratch counter
 };
 

@@ -15,8 +15,9 @@
 // Optionally (sigma > 1) rows are sorted by length, longest first, inside
 // windows of sigma rows, so that a slice holds rows of similar length; y is
 // then written through the permutation.  Rows longer than kSlicedCap are not
-// put in slices (their slot has length -1) and are computed by one warp each
-// from the CSR arrays.  The layout is that of the oracle's orc_sliced_layout
+// put in slices (their slot has length -1); they are split into segments of
+// kSlicedSeg nonzeros computed by one warp each from the CSR arrays, and a
+// fix-up adds each such row's segment sums in order.  The layout is that of the oracle's orc_sliced_layout
 // and orc_sliced_fill, bit for bit.
 #include <algorithm>
 #include <vector>
@@ -165,18 +166,46 @@ k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict
     slice_rows<U>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
 }
 
-// one warp per long row, from the CSR arrays
+__global__ void k_sl_row_lengths(int n, const int* __restrict__ list, const int* __restrict__ rp,
+                                 int* __restrict__ len)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) len[q] = rp[list[q] + 1] - rp[list[q]];
+}
+
+// Long rows are split into segments of kSlicedSeg nonzeros; one warp per
+// segment writes the segment's partial sum, and k_sliced_fixup adds each long
+// row's partials in segment order (deterministic).
 __global__ void __launch_bounds__(kSB)
-k_sliced_long(int n_long, const int* __restrict__ list, const int* __restrict__ rp,
-              const int* __restrict__ ci, const double* __restrict__ v,
-              const double* __restrict__ x, double* __restrict__ y)
+k_sliced_segments(int n_seg, int n_long, const int* __restrict__ list,
+                  const int* __restrict__ seg_off, const int* __restrict__ rp,
+                  const int* __restrict__ ci, const double* __restrict__ v,
+                  const double* __restrict__ x, double* __restrict__ partial)
 {
     const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
-    if (w >= n_long) return;
+    if (w >= n_seg) return;
     const int lane = threadIdx.x & 31;
-    const int r = list[w];
-    const double s = group_sum(row_partial<32, 8>(rp[r], rp[r + 1], lane, ColPlain<int>{ci}, v, x), 32);
-    if (lane == 0) y[r] = s;
+    int lo = 0, hi = n_long - 1;  // last long row whose first segment is <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int r = list[lo];
+    const int64_t b = (int64_t)rp[r] + (int64_t)(w - seg_off[lo]) * kSlicedSeg;
+    const int64_t e = min((int64_t)rp[r + 1], b + kSlicedSeg);
+    const double sum = group_sum(row_partial<32, 8>(b, e, lane, ColPlain<int>{ci}, v, x), 32);
+    if (lane == 0) partial[w] = sum;
+}
+
+__global__ void k_sliced_fixup(int n_long, const int* __restrict__ list,
+                               const int* __restrict__ seg_off, const double* __restrict__ partial,
+                               double* __restrict__ y)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_long) return;
+    double sum = 0.0;
+    for (int i = seg_off[q]; i < seg_off[q + 1]; ++i) sum += partial[i];
+    y[list[q]] = sum;
 }
 
 unsigned grid_of(int64_t threads, int64_t cap_blocks)
@@ -258,11 +287,31 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         SPMV_CUDA_TRY(cudaGetLastError());
     }
     if (d.n_long > 0) {
-        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.long_rows), 4 * (int64_t)d.n_long)) != SPMV_OK)
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.long_rows), 4 * (int64_t)d.n_long)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_off), 4 * ((int64_t)d.n_long + 1))) != SPMV_OK)
             return st;
         SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
         k_sl_long_list<<<rows_grid, kSB, 0, s>>>(A.n_rows, A.rowptr, cap, d.long_rows, d.count);
         SPMV_CUDA_TRY(cudaGetLastError());
+        // long rows in ascending order (host sort), their lengths (device,
+        // into seg_off as scratch), then their segment offsets (host scan)
+        std::vector<int> lr(d.n_long), len(d.n_long), off(d.n_long + 1);
+        SPMV_CUDA_TRY(cudaMemcpyAsync(lr.data(), d.long_rows, 4 * (size_t)d.n_long, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        std::sort(lr.begin(), lr.end());
+        SPMV_CUDA_TRY(cudaMemcpyAsync(d.long_rows, lr.data(), 4 * (size_t)d.n_long, cudaMemcpyHostToDevice, s));
+        k_sl_row_lengths<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, A.rowptr,
+                                                                            d.seg_off);
+        SPMV_CUDA_TRY(cudaGetLastError());
+        SPMV_CUDA_TRY(cudaMemcpyAsync(len.data(), d.seg_off, 4 * (size_t)d.n_long, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        off[0] = 0;
+        for (int q = 0; q < d.n_long; ++q) off[q + 1] = off[q] + (len[q] + kSlicedSeg - 1) / kSlicedSeg;
+        d.n_seg = off[d.n_long];
+        SPMV_CUDA_TRY(cudaMemcpyAsync(d.seg_off, off.data(), 4 * ((size_t)d.n_long + 1), cudaMemcpyHostToDevice, s));
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)d.n_seg)) != SPMV_OK)
+            return st;
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     }
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
     P->n_blocks = d.n_slices;
@@ -278,8 +327,12 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
         d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, d.sigma > 1 ? d.perm : nullptr, d.col, d.val, x, y);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || d.n_long == 0) return e;
-    k_sliced_long<<<grid_of(32 * (int64_t)d.n_long, INT32_MAX), kSB, 0, s>>>(
-        d.n_long, d.long_rows, A.rowptr, A.colind, A.val, x, y);
+    k_sliced_segments<<<grid_of(32 * (int64_t)d.n_seg, INT32_MAX), kSB, 0, s>>>(
+        d.n_seg, d.n_long, d.long_rows, d.seg_off, A.rowptr, A.colind, A.val, x, d.partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sliced_fixup<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, d.seg_off,
+                                                                      d.partial, y);
     return cudaGetLastError();
 }
 

@@ -287,7 +287,7 @@ def test_sliced_layout_bit_exact(sigma, name, A):
     S = (A.n_rows + 31) // 32
     info = P.info()
     assert info.n_blocks == S and info.block_nnz == sigma
-    assert info.launches == (0 if A.n_rows == 0 else (2 if n_long else 1))
+    assert info.launches == (0 if A.n_rows == 0 else (3 if n_long else 1))
     if S == 0:
         return
     assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWLEN, 32 * S, torch.int32), rowlen)
@@ -312,7 +312,7 @@ def test_sliced_auto_window_and_long_rows():
     assert sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced")).info().block_nnz == 1
     Z = synth.zipf_rows(60_000, 60_000, 1.4, 20_000, seed=9)
     P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced"))
-    assert P.info().block_nnz == 256 and P.info().launches == 2
+    assert P.info().block_nnz == 256 and P.info().launches == 3
     y, x = _run(Z, sp.make_choice("sliced"))
     _assert_close(y, Z, x)
     for bad in (2, 16, 8192):
