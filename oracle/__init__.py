@@ -89,6 +89,7 @@ def _load():
                 "orc_mlp_loss_grad_soft_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
                 "orc_sliced_layout": (i64, [i64, P, i32, i32, P, P, P, P]),
                 "orc_sliced_fill": (None, [i64, P, P, P, P, P, P, P, P]),
+                "orc_sliced_offsets": (i64, [i64, P, P, P, P, P, P, P]),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -261,6 +262,22 @@ def sliced_fill(A, perm, rowlen, sptr):
     _load().orc_sliced_fill(A.n_rows, _p(rp), _p(ci), _p(va), _p(perm), _p(rowlen), _p(sptr),
                             _p(col), _p(val))
     return col[:tot], val[:tot]
+
+
+def sliced_offsets(A, perm, rowlen, sptr):
+    """16-bit offsets of the sliced layout: per-position row base (first
+    column) and col - base per slot; returns (rowbase, off, largest span)."""
+    rp, ci, _ = _csr(A)
+    S = (A.n_rows + 31) // 32
+    tot = int(sptr[-1])
+    base = np.empty(max(32 * S, 1), np.int32)
+    off = np.empty(max(tot, 1), np.uint16)
+    perm = _np(perm, np.int32)
+    rowlen = _np(rowlen, np.int32)
+    sptr = _np(sptr, np.int64)
+    span = _load().orc_sliced_offsets(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr),
+                                      _p(base), _p(off))
+    return base[:32 * S], off[:tot], int(span)
 
 
 def mlp_forward_f32(params: dict, v) -> np.ndarray:

@@ -459,6 +459,32 @@ void orc_sliced_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
     }
 }
 
+/* 16-bit form of the sliced layout's columns (reading O13 on slices): the
+ * row at position p has base rowbase_pos[p] = its first column (0 for an
+ * empty row, a long row or a position past the last row), and every slot of
+ * it holds col - base; padding slots hold 0.  Returns the largest span
+ * (last - first column) over the rows in slices; offsets are meaningful only
+ * when it is below 65536.                                                     */
+int64_t orc_sliced_offsets(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                           const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
+                           int32_t *rowbase_pos, uint16_t *off_out)
+{
+    int64_t n_slices = (n_rows + 31) / 32, span = 0;
+    int64_t tot = slice_ptr[n_slices];
+    for (int64_t q = 0; q < tot; ++q) off_out[q] = 0;
+    for (int64_t p = 0; p < 32 * n_slices; ++p) {
+        rowbase_pos[p] = 0;
+        if (p >= n_rows || rowlen[p] <= 0) continue;
+        int64_t b = rowptr[perm[p]], len = rowlen[p], s = p / 32, l = p % 32;
+        int64_t first = colind[b];
+        rowbase_pos[p] = (int32_t)first;
+        if (colind[b + len - 1] - first > span) span = colind[b + len - 1] - first;
+        for (int64_t k = 0; k < len; ++k)
+            off_out[slice_ptr[s] + 32 * k + l] = (uint16_t)(colind[b + k] - first);
+    }
+    return span;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Learned selector: fully connected 16 -> H1 -> H2 -> K network with ReLU.
  * Input standardisation z_k = (v_k - mean_k) * istd_k, each product and

@@ -558,6 +558,37 @@ def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap):
     assert np.count_nonzero(val) == np.count_nonzero(va[np.repeat(lengths <= cap, lengths)])
 
 
+def test_sliced_offsets_decode_to_the_columns():
+    """base + offset gives back every column of every row in the slices,
+    padding and rows outside the slices hold 0, and the span is the largest
+    last - first column of a row in the slices."""
+    g = np.random.default_rng(17)
+    lengths = np.minimum(g.zipf(1.7, 300), 40)
+    lengths[:5] = [0, 1, 3, 41, 2]
+    A = _csr_from_lengths(lengths.tolist(), n_cols=5000, seed=4)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=64, cap=40)
+    col, _ = oracle.sliced_fill(A, perm, rowlen, sptr)
+    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr)
+    rp, ci = A.rowptr.numpy(), A.colind.numpy()
+    spans = []
+    for p in range(32 * len(slen)):
+        if p >= A.n_rows or rowlen[p] <= 0:
+            assert base[p] == 0
+            continue
+        s, l = p // 32, p % 32
+        idx = sptr[s] + 32 * np.arange(rowlen[p]) + l
+        assert np.array_equal(base[p] + off[idx].astype(np.int64), col[idx])
+        r = perm[p]
+        assert base[p] == ci[rp[r]]
+        spans.append(ci[rp[r + 1] - 1] - ci[rp[r]])
+    assert span == max(spans)
+    real = np.zeros(len(off), bool)
+    for p in range(A.n_rows):
+        if rowlen[p] > 0:
+            real[sptr[p // 32] + 32 * np.arange(rowlen[p]) + p % 32] = True
+    assert np.all(off[~real] == 0)
+
+
 # --------------------------------------------------------------- CG
 def test_cg_solves_small_spd_exactly_in_n_steps():
     g = np.random.default_rng(0)
