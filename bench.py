@@ -438,8 +438,9 @@ def _time_ms(fn, reps=10, warm=3):
 
 
 def run_cg(args):
-    """Mixed precision: compressed SpMV throughput with FP32/BF16 values (FP32
-    or FP64 accumulation), and 300 CG iterations on the SPD 7-point Laplacian 128^3 (variable
+    """Mixed precision: compressed and sliced SpMV throughput with FP32/BF16
+    values (FP32 or FP64 accumulation), and 300 CG iterations (sliced inner
+    and exact SpMV) on the SPD 7-point Laplacian 128^3 (variable
     coefficients) with an FP64, FP32 or BF16 inner SpMV and FP64 residual
     recomputation; errors are against the FP64 GPU solve."""
     import torch
@@ -455,16 +456,18 @@ def run_cg(args):
         yref = torch.empty_like(y)
         P64 = sp.spmv_prepare(dA, sp.make_choice("subwarp"))
         sp.spmv(P64, x, yref)
-        for name, vt, acc in (("f64", sp.VAL_F64, sp.ACC_F64), ("f32", sp.VAL_F32, sp.ACC_F32),
-                              ("bf16", sp.VAL_BF16, sp.ACC_F32), ("f32_acc64", sp.VAL_F32, sp.ACC_F64),
-                              ("bf16_acc64", sp.VAL_BF16, sp.ACC_F64)):
-            P = sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt, accumulate=acc))
+        for var, name, vt, acc in (
+                ("compressed", "f64", sp.VAL_F64, sp.ACC_F64), ("compressed", "f32", sp.VAL_F32, sp.ACC_F32),
+                ("compressed", "bf16", sp.VAL_BF16, sp.ACC_F32), ("compressed", "f32_acc64", sp.VAL_F32, sp.ACC_F64),
+                ("compressed", "bf16_acc64", sp.VAL_BF16, sp.ACC_F64), ("sliced", "f64", sp.VAL_F64, sp.ACC_F64),
+                ("sliced", "f32", sp.VAL_F32, sp.ACC_F32), ("sliced", "bf16", sp.VAL_BF16, sp.ACC_F32)):
+            P = sp.spmv_prepare(dA, sp.make_choice(var, value_type=vt, accumulate=acc))
             ms = _time_ms(lambda: sp.spmv(P, x, y))
             sp.spmv(P, x, y)
             scale = torch.linalg.vector_norm(yref, float("inf")).item()
             err = (torch.linalg.vector_norm(y - yref, float("inf")) / scale).item()
             mb = P.info().min_bytes
-            out["spmv"].append({"matrix": A.name, "values": name, "ms": round(ms, 5),
+            out["spmv"].append({"matrix": A.name, "variant": var, "values": name, "ms": round(ms, 5),
                                 "min_bytes": mb, "gbs": round(mb / ms / 1e6, 1),
                                 "rel_err_vs_f64": err, "wide_rows": P.info().n_wide_rows})
             P.free()
@@ -472,12 +475,12 @@ def run_cg(args):
     A = synth.variable_coeff_laplacian_3d(128, seed=0)
     dA = sp.DeviceCSR.from_host(A)
     b = synth.uniform_vector(A.n_rows, 1).cuda()
-    exact = sp.spmv_prepare(dA, sp.make_choice("subwarp"))
+    exact = sp.spmv_prepare(dA, sp.make_choice("sliced"))
     iters = 300
     xs = {}
     for name, vt, refine in (("f64", None, 0), ("f32", sp.VAL_F32, 10), ("bf16", sp.VAL_BF16, 10),
                              ("bf16_no_refine", sp.VAL_BF16, 0)):
-        inner = exact if vt is None else sp.spmv_prepare(dA, sp.make_choice("compressed", value_type=vt))
+        inner = exact if vt is None else sp.spmv_prepare(dA, sp.make_choice("sliced", value_type=vt))
         x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
         res = torch.empty(iters + 1, dtype=torch.float64, device="cuda")
         sp.spmv_cg(inner, b, x, iters, refine, A_exact=exact, resid=res, use_graph=True)

@@ -169,8 +169,11 @@ typedef struct {
  *                     first, inside windows of that many rows); 0 = rows in
  *                     order unless that pads the slices by more than 25 %,
  *                     then 256
- *   value_type      : COMPRESSED value storage (spmv_value_type)
- *   accumulate      : COMPRESSED arithmetic.  FP32 (the default for FP32/BF16
+ *   value_type      : COMPRESSED and SLICED value storage (spmv_value_type);
+ *                     SLICED with FP32/BF16 values stores 16-bit column
+ *                     offsets from each row's first column when every row in
+ *                     its slices spans fewer than 65536 columns
+ *   accumulate      : COMPRESSED and SLICED arithmetic.  FP32 (the default for FP32/BF16
  *                     values) rounds x to an FP32 copy owned by the prepared
  *                     object once per call and sums in FP32 (no FP64
  *                     instruction per nonzero; relative error ~1e-7 against
@@ -226,8 +229,13 @@ typedef enum {
                                    long row (computed from CSR) or past the last row   */
     SPMV_EXPORT_SLICE_LEN = 8,  /* SLICED: int32 [S] slice length (longest row in it)   */
     SPMV_EXPORT_SLICE_PTR = 9,  /* SLICED: int64 [S + 1] first element of each slice    */
-    SPMV_EXPORT_SLICE_COL = 10, /* SLICED: int32 [slice_ptr[S]] columns, column-major   */
-    SPMV_EXPORT_SLICE_VAL = 11  /* SLICED: f64 [slice_ptr[S]] values, column-major      */
+    SPMV_EXPORT_SLICE_COL = 10, /* SLICED: int32 [slice_ptr[S]] columns, column-major
+                                   (absent with 16-bit offsets)                        */
+    SPMV_EXPORT_SLICE_VAL = 11, /* SLICED: [slice_ptr[S]] values in value_type          */
+    SPMV_EXPORT_SLICE_OFF16 = 12, /* SLICED, 16-bit offsets: uint16 [slice_ptr[S]]
+                                   column - row base                                   */
+    SPMV_EXPORT_SLICE_ROWBASE = 13 /* SLICED, 16-bit offsets: int32 [32 S] first column
+                                   of each position's row (0 where none)               */
 } spmv_export;
 
 /* ---- status ---------------------------------------------------------- */

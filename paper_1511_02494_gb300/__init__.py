@@ -18,7 +18,7 @@ from ._abi import (  # noqa: F401  (re-exported)
     SPMV_OK, STATUS_NAMES, VARIANTS, VARIANT_IDS, CLASSES, VAL_F64, VAL_F32, VAL_BF16,
     EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
     EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
-    EXPORT_SLICE_COL, EXPORT_SLICE_VAL, declare,
+    EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE, declare,
 )
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

@@ -13,7 +13,7 @@ CLASSES = ("CML", "MB", "IMB", "CMP")
 VAL_F64, VAL_F32, VAL_BF16 = 0, 1, 2
 (EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
  EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
- EXPORT_SLICE_COL, EXPORT_SLICE_VAL) = range(12)
+ EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE) = range(14)
 
 
 class CSR(C.Structure):

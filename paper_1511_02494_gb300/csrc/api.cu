@@ -128,7 +128,8 @@ void release(spmv_prepared_t* P)
                     P->rowbase, P->off16, P->lowval, P->x_stage, P->y_stage, P->status,
                     P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32,
                     P->sl.rowlen, P->sl.slice_len, P->sl.slice_ptr, P->sl.perm, P->sl.col, P->sl.val,
-                    P->sl.long_rows, P->sl.count, P->sl.seg_off, P->sl.partial};
+                    P->sl.long_rows, P->sl.count, P->sl.seg_off, P->sl.partial, P->sl.lowval,
+                    P->sl.off, P->sl.rowbase, P->sl.x32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -140,7 +141,8 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
-        case SPMV_V7_SLICED: return P->sl.n_long > 0 ? 3 : 1;      // + long-row segments, fix-up
+        case SPMV_V7_SLICED:  // + x to FP32, + long-row segments and fix-up
+            return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0) + (P->sl.n_long > 0 ? 2 : 0);
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
         default: return 1;
     }
@@ -154,8 +156,11 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
         // elements once, a row length per position, slice length and start,
         // the permutation when rows are sorted, the long rows' CSR bounds
         const SlicedPlan& d = P->sl;
-        return 12 * A.nnz + 128 * d.n_slices + 12 * d.n_slices + (d.sigma > 1 ? 4 * A.n_rows : 0) +
-               12 * (int64_t)d.n_long + 16 * (int64_t)d.n_seg + 8 * A.n_cols + 8 * A.n_rows;
+        const int vb = d.value_type == SPMV_VAL_F64 ? 8 : d.value_type == SPMV_VAL_F32 ? 4 : 2;
+        const int cb = d.off16 ? 2 : 4;
+        return (int64_t)(vb + cb) * A.nnz + 128 * d.n_slices * (d.off16 ? 2 : 1) + 12 * d.n_slices +
+               (d.sigma > 1 ? 4 * A.n_rows : 0) + 12 * (int64_t)d.n_long + 16 * (int64_t)d.n_seg +
+               8 * A.n_cols + (d.acc32 ? 8 * A.n_cols : 0) + 8 * A.n_rows;
     }
     if (P->c.variant != SPMV_V6_COMPRESSED) return 12 * A.nnz + vec;
     const int vb = P->c.value_type == SPMV_VAL_F64 ? 8 : P->c.value_type == SPMV_VAL_F32 ? 4 : 2;
@@ -310,12 +315,13 @@ spmv_status check_choice(const spmv_choice_t* c)
         return fail(SPMV_ERR_INVALID_ARG, "items_per_warp must be 32*k, k in {1,2,4,6,7,8,12,16}");
     if (c->value_type < SPMV_VAL_F64 || c->value_type > SPMV_VAL_BF16)
         return fail(SPMV_ERR_INVALID_ARG, "value_type out of range");
-    if (c->value_type != SPMV_VAL_F64 && c->variant != SPMV_V6_COMPRESSED)
-        return fail(SPMV_ERR_UNSUPPORTED, "low-precision values only in the COMPRESSED variant");
+    const bool lowp_ok = c->variant == SPMV_V6_COMPRESSED || c->variant == SPMV_V7_SLICED;
+    if (c->value_type != SPMV_VAL_F64 && !lowp_ok)
+        return fail(SPMV_ERR_UNSUPPORTED, "low-precision values only in the COMPRESSED and SLICED variants");
     if (c->accumulate < 0 || c->accumulate > 2)
         return fail(SPMV_ERR_INVALID_ARG, "accumulate must be 0 (by value type), 1 (FP64) or 2 (FP32)");
-    if (c->accumulate == 2 && (c->variant != SPMV_V6_COMPRESSED || c->value_type == SPMV_VAL_F64))
-        return fail(SPMV_ERR_UNSUPPORTED, "FP32 accumulation needs COMPRESSED with FP32 or BF16 values");
+    if (c->accumulate == 2 && (!lowp_ok || c->value_type == SPMV_VAL_F64))
+        return fail(SPMV_ERR_UNSUPPORTED, "FP32 accumulation needs COMPRESSED or SLICED with FP32 or BF16 values");
     return SPMV_OK;
 }
 
@@ -578,7 +584,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.min_bytes = min_bytes_of(P);
     i.tile_items = P->tile_items;
     i.bulk_copy = P->bulk ? 1 : 0;
-    i.accumulate = P->c.variant == SPMV_V6_COMPRESSED ? P->c.accumulate : 1;
+    i.accumulate = P->c.variant == SPMV_V6_COMPRESSED || P->c.variant == SPMV_V7_SLICED ? P->c.accumulate : 1;
     i.launches = launches_of(P);
     *info = i;
     return SPMV_OK;
@@ -627,10 +633,20 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
             if (v == SPMV_V7_SLICED) { src = P->sl.slice_ptr; size = 8 * (P->sl.n_slices + 1); }
             break;
         case SPMV_EXPORT_SLICE_COL:
-            if (v == SPMV_V7_SLICED) { src = P->sl.col; size = 4 * P->sl.tot; }
+            if (v == SPMV_V7_SLICED && !P->sl.off16) { src = P->sl.col; size = 4 * P->sl.tot; }
             break;
         case SPMV_EXPORT_SLICE_VAL:
-            if (v == SPMV_V7_SLICED) { src = P->sl.val; size = 8 * P->sl.tot; }
+            if (v == SPMV_V7_SLICED) {
+                const int t = P->sl.value_type;
+                src = t == SPMV_VAL_F64 ? (const void*)P->sl.val : P->sl.lowval;
+                size = (t == SPMV_VAL_F64 ? 8 : t == SPMV_VAL_F32 ? 4 : 2) * P->sl.tot;
+            }
+            break;
+        case SPMV_EXPORT_SLICE_OFF16:
+            if (v == SPMV_V7_SLICED && P->sl.off16) { src = P->sl.off; size = 2 * P->sl.tot; }
+            break;
+        case SPMV_EXPORT_SLICE_ROWBASE:
+            if (v == SPMV_V7_SLICED && P->sl.off16) { src = P->sl.rowbase; size = 4 * 32 * P->sl.n_slices; }
             break;
         default:
             return fail(SPMV_ERR_INVALID_ARG, "unknown export");

@@ -72,6 +72,13 @@ struct SlicedPlan {
     int* seg_off = nullptr;      // [n_long + 1] first segment of each long row
     double* partial = nullptr;   // [n_seg] segment sums
     int n_seg = 0;
+    // low-precision values (FP32 / BF16), optionally 16-bit column offsets
+    int value_type = 0;
+    bool acc32 = false, off16 = false;
+    void* lowval = nullptr;      // [tot] values in value_type
+    uint16_t* off = nullptr;     // [tot] column - rowbase (off16)
+    int* rowbase = nullptr;      // [32 n_slices] first column of each position's row (off16)
+    float* x32 = nullptr;        // FP32 copy of x (acc32)
     unsigned* count = nullptr;   // scratch counter
 };
 

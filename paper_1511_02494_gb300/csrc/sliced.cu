@@ -19,6 +19,8 @@
 // kSlicedSeg nonzeros computed by one warp each from the CSR arrays, and a
 // fix-up adds each such row's segment sums in order.  The layout is that of the oracle's orc_sliced_layout
 // and orc_sliced_fill, bit for bit.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -208,6 +210,143 @@ __global__ void k_sliced_fixup(int n_long, const int* __restrict__ list,
     y[list[q]] = sum;
 }
 
+// ---- low-precision values (FP32 or BF16), optionally 16-bit column offsets --
+__device__ __forceinline__ float round_to(double v, float*) { return __double2float_rn(v); }
+__device__ __forceinline__ __nv_bfloat16 round_to(double v, __nv_bfloat16*) { return __double2bfloat16(v); }
+__device__ __forceinline__ float widen32(float a) { return a; }
+__device__ __forceinline__ float widen32(__nv_bfloat16 a) { return __bfloat162float(a); }
+
+__global__ void k_sl_span(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                          const int* __restrict__ perm, const int* __restrict__ rowlen,
+                          int* __restrict__ span)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 32 * n_slices) return;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int64_t b = rp[perm ? perm[p] : (int)p];
+    atomicMax(span, ci[b + len - 1] - ci[b]);
+}
+
+// column-major low-precision contents; OFF16: offsets from the row's first
+// column (rowbase per position), else 32-bit columns
+template <typename VT, bool OFF16>
+__global__ void k_sl_fill_lp(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ v, const int* __restrict__ perm,
+                             const int* __restrict__ rowlen, const int64_t* __restrict__ slice_ptr,
+                             int* __restrict__ col, uint16_t* __restrict__ off,
+                             int* __restrict__ rowbase, VT* __restrict__ val)
+{
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int64_t b = rp[perm ? perm[p] : (int)p];
+    const int64_t q0 = slice_ptr[s] + lane;
+    const int first = ci[b];
+    if (OFF16) rowbase[p] = first;
+    for (int k = 0; k < len; ++k) {
+        if (OFF16) off[q0 + (int64_t)k * 32] = (uint16_t)(ci[b + k] - first);
+        else col[q0 + (int64_t)k * 32] = ci[b + k];
+        val[q0 + (int64_t)k * 32] = round_to(v[b + k], (VT*)nullptr);
+    }
+}
+
+__global__ void k_sl_x_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ x32)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x32[i] = __double2float_rn(x[i]);
+}
+
+// One slice with low-precision values.  ACC32: FP32 copy of x, fmaf chain in
+// row order, one widening per row (bit for bit the oracle's FP32 form);
+// else each value widened to FP64 and a DFMA chain.
+template <int U, typename VT, bool OFF16, bool ACC32>
+__global__ void __launch_bounds__(kSB, 8)
+k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+            const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+            const int* __restrict__ col, const uint16_t* __restrict__ off,
+            const int* __restrict__ rowbase, const VT* __restrict__ val,
+            const double* __restrict__ x, const float* __restrict__ x32, double* __restrict__ y)
+{
+    const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    const int L = slice_len[s];
+    const int64_t q0 = slice_ptr[s] + lane;
+    const int base = OFF16 ? rowbase[p] : 0;
+    const VT* __restrict__ vp = val + q0;
+    float acc32 = 0.f;
+    double acc64 = 0.0;
+    for (int k = 0; k < L; k += U) {
+        int c[U];
+        float a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = k + u < len;
+            if (OFF16) c[u] = ok ? base + (int)__ldcs(off + q0 + (k + u) * 32) : 0;
+            else c[u] = ok ? __ldcs(col + q0 + (k + u) * 32) : 0;
+            a[u] = ok ? ldval32(vp + (k + u) * 32) : 0.f;  // exact widening of FP32 / BF16
+        }
+        if (ACC32) {
+            float xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? __ldg(x32 + c[u]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k + u < len) acc32 = fmaf(a[u], xv[u], acc32);
+        } else {
+            double xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k + u < len) acc64 = fma((double)a[u], xv[u], acc64);
+        }
+    }
+    if (len >= 0) y[perm ? perm[p] : p] = ACC32 ? (double)acc32 : acc64;
+}
+
+// long-row segments with the values rounded as the slices' (same arithmetic
+// per element; the segment's lanes are combined by a shuffle tree)
+template <typename VT, bool ACC32>
+__global__ void __launch_bounds__(kSB)
+k_sliced_segments_lp(int n_seg, int n_long, const int* __restrict__ list,
+                     const int* __restrict__ seg_off, const int* __restrict__ rp,
+                     const int* __restrict__ ci, const double* __restrict__ v,
+                     const double* __restrict__ x, const float* __restrict__ x32,
+                     double* __restrict__ partial)
+{
+    const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
+    if (w >= n_seg) return;
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n_long - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int r = list[lo];
+    const int64_t b = (int64_t)rp[r] + (int64_t)(w - seg_off[lo]) * kSlicedSeg;
+    const int64_t e = min((int64_t)rp[r + 1], b + kSlicedSeg);
+    if (ACC32) {
+        float acc = 0.f;
+        for (int64_t j = b + lane; j < e; j += 32)
+            acc = fmaf(widen32(round_to(__ldcs(v + j), (VT*)nullptr)), __ldg(x32 + __ldcs(ci + j)), acc);
+        acc = group_sum32(acc, 32);
+        if (lane == 0) partial[w] = (double)acc;
+    } else {
+        double acc = 0.0;
+        for (int64_t j = b + lane; j < e; j += 32)
+            acc = fma((double)widen32(round_to(__ldcs(v + j), (VT*)nullptr)), ldx(x + __ldcs(ci + j)), acc);
+        acc = group_sum(acc, 32);
+        if (lane == 0) partial[w] = acc;
+    }
+}
+
 unsigned grid_of(int64_t threads, int64_t cap_blocks)
 {
     int64_t g = (threads + kSB - 1) / kSB;
@@ -275,17 +414,64 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
     d.n_long = (int)n_long;
     d.tot = sptr[d.n_slices];
     SPMV_CUDA_TRY(cudaMemcpyAsync(d.slice_ptr, sptr.data(), 8 * (d.n_slices + 1), cudaMemcpyHostToDevice, s));
-    if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.col), 4 * std::max<int64_t>(d.tot, 1))) != SPMV_OK ||
-        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.val), 8 * std::max<int64_t>(d.tot, 1))) != SPMV_OK)
-        return st;
-    SPMV_CUDA_TRY(cudaMemsetAsync(d.col, 0, 4 * std::max<int64_t>(d.tot, 1), s));
-    SPMV_CUDA_TRY(cudaMemsetAsync(d.val, 0, 8 * std::max<int64_t>(d.tot, 1), s));
-    if (d.n_slices > 0) {
-        k_sl_fill<<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val,
-                                             sigma > 1 ? d.perm : nullptr, d.rowlen, d.slice_ptr,
-                                             d.col, d.val);
-        SPMV_CUDA_TRY(cudaGetLastError());
+    const int64_t tot1 = std::max<int64_t>(d.tot, 1);
+    const int* permp = sigma > 1 ? d.perm : nullptr;
+    d.value_type = P->c.value_type;
+    if (P->c.accumulate == 0) P->c.accumulate = d.value_type == SPMV_VAL_F64 ? 1 : 2;
+    d.acc32 = P->c.accumulate == 2;
+    if (d.value_type == SPMV_VAL_F64) {
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.col), 4 * tot1)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.val), 8 * tot1)) != SPMV_OK)
+            return st;
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.col, 0, 4 * tot1, s));
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.val, 0, 8 * tot1, s));
+        if (d.n_slices > 0) {
+            k_sl_fill<<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, d.rowlen,
+                                                 d.slice_ptr, d.col, d.val);
+            SPMV_CUDA_TRY(cudaGetLastError());
+        }
+    } else {
+        // 16-bit offsets when every row in the slices spans fewer than 65536 columns
+        int span = 0;
+        if (d.n_slices > 0) {
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
+            k_sl_span<<<(unsigned)((32 * d.n_slices + kSB - 1) / kSB), kSB, 0, s>>>(
+                d.n_slices, A.rowptr, A.colind, permp, d.rowlen, reinterpret_cast<int*>(d.count));
+            SPMV_CUDA_TRY(cudaGetLastError());
+            SPMV_CUDA_TRY(cudaMemcpyAsync(&span, d.count, 4, cudaMemcpyDeviceToHost, s));
+            SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        d.off16 = span < 65536;
+        const int vb = d.value_type == SPMV_VAL_F32 ? 4 : 2;
+        if ((st = prepared_alloc(P, &d.lowval, vb * tot1)) != SPMV_OK) return st;
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.lowval, 0, vb * tot1, s));
+        if (d.off16) {
+            if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.off), 2 * tot1)) != SPMV_OK ||
+                (st = prepared_alloc(P, reinterpret_cast<void**>(&d.rowbase), 4 * std::max<int64_t>(n_pos, 1))) != SPMV_OK)
+                return st;
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.off, 0, 2 * tot1, s));
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.rowbase, 0, 4 * std::max<int64_t>(n_pos, 1), s));
+        } else {
+            if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.col), 4 * tot1)) != SPMV_OK) return st;
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.col, 0, 4 * tot1, s));
+        }
+        if (d.n_slices > 0) {
+#define SPMV_SL_FILL(VT, O16)                                                                      \
+    k_sl_fill_lp<VT, O16><<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, \
+                                                     d.rowlen, d.slice_ptr, d.col, d.off,          \
+                                                     d.rowbase, static_cast<VT*>(d.lowval))
+            if (d.value_type == SPMV_VAL_F32) {
+                if (d.off16) SPMV_SL_FILL(float, true); else SPMV_SL_FILL(float, false);
+            } else {
+                if (d.off16) SPMV_SL_FILL(__nv_bfloat16, true); else SPMV_SL_FILL(__nv_bfloat16, false);
+            }
+#undef SPMV_SL_FILL
+            SPMV_CUDA_TRY(cudaGetLastError());
+        }
     }
+    if (d.acc32 &&
+        (st = prepared_alloc(P, reinterpret_cast<void**>(&d.x32), 4 * std::max<int64_t>(A.n_cols, 1))) != SPMV_OK)
+        return st;
     if (d.n_long > 0) {
         if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.long_rows), 4 * (int64_t)d.n_long)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_off), 4 * ((int64_t)d.n_long + 1))) != SPMV_OK)
@@ -323,12 +509,45 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     const spmv_csr_t& A = P->A;
     const SlicedPlan& d = P->sl;
     if (A.n_rows == 0) return cudaSuccess;
-    k_sliced<4><<<grid_of(32 * d.n_slices, INT32_MAX), kSB, 0, s>>>(
-        d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, d.sigma > 1 ? d.perm : nullptr, d.col, d.val, x, y);
-    cudaError_t e = cudaGetLastError();
+    const unsigned grid = grid_of(32 * d.n_slices, INT32_MAX);
+    const int* perm = d.sigma > 1 ? d.perm : nullptr;
+    cudaError_t e;
+    if (d.acc32 && A.n_cols > 0) {
+        k_sl_x_to_f32<<<(unsigned)((A.n_cols + kSB - 1) / kSB), kSB, 0, s>>>(A.n_cols, x, d.x32);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (d.value_type == SPMV_VAL_F64) {
+        k_sliced<4><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col,
+                                         d.val, x, y);
+    } else {
+#define SPMV_SL_LP(VT, O16, A32)                                                                   \
+    k_sliced_lp<4, VT, O16, A32><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len,          \
+                                                      d.slice_ptr, perm, d.col, d.off, d.rowbase,  \
+                                                      static_cast<const VT*>(d.lowval), x, d.x32, y)
+#define SPMV_SL_LP_VT(VT)                                                        \
+    if (d.off16) { if (d.acc32) SPMV_SL_LP(VT, true, true); else SPMV_SL_LP(VT, true, false); } \
+    else { if (d.acc32) SPMV_SL_LP(VT, false, true); else SPMV_SL_LP(VT, false, false); }
+        if (d.value_type == SPMV_VAL_F32) { SPMV_SL_LP_VT(float) } else { SPMV_SL_LP_VT(__nv_bfloat16) }
+#undef SPMV_SL_LP_VT
+#undef SPMV_SL_LP
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess || d.n_long == 0) return e;
-    k_sliced_segments<<<grid_of(32 * (int64_t)d.n_seg, INT32_MAX), kSB, 0, s>>>(
-        d.n_seg, d.n_long, d.long_rows, d.seg_off, A.rowptr, A.colind, A.val, x, d.partial);
+    const unsigned sgrid = grid_of(32 * (int64_t)d.n_seg, INT32_MAX);
+    if (d.value_type == SPMV_VAL_F64) {
+        k_sliced_segments<<<sgrid, kSB, 0, s>>>(d.n_seg, d.n_long, d.long_rows, d.seg_off, A.rowptr,
+                                                 A.colind, A.val, x, d.partial);
+    } else {
+#define SPMV_SL_SEG(VT, A32)                                                                        \
+    k_sliced_segments_lp<VT, A32><<<sgrid, kSB, 0, s>>>(d.n_seg, d.n_long, d.long_rows, d.seg_off, \
+                                                        A.rowptr, A.colind, A.val, x, d.x32, d.partial)
+        if (d.value_type == SPMV_VAL_F32) {
+            if (d.acc32) SPMV_SL_SEG(float, true); else SPMV_SL_SEG(float, false);
+        } else {
+            if (d.acc32) SPMV_SL_SEG(__nv_bfloat16, true); else SPMV_SL_SEG(__nv_bfloat16, false);
+        }
+#undef SPMV_SL_SEG
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sliced_fixup<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, d.seg_off,

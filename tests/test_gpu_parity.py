@@ -305,6 +305,59 @@ def test_sliced_layout_bit_exact(sigma, name, A):
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_VAL, tot, torch.float64), val)
 
 
+@pytest.mark.parametrize("vt", [sp.VAL_F32, sp.VAL_BF16])
+@pytest.mark.parametrize("sigma", [1, 256])
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_sliced_low_precision_layout_bit_exact(vt, sigma, name, A):
+    """Values rounded as the oracle rounds them; 16-bit offsets from each
+    row's first column when every row in the slices spans < 65536 columns."""
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, value_type=vt))
+    assert P.info().accumulate == sp.ACC_F32
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, 1024)
+    S, tot = (A.n_rows + 31) // 32, int(sptr[-1])
+    if tot == 0:
+        return
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    if vt == sp.VAL_F32:
+        got = _export(P, sp.EXPORT_SLICE_VAL, tot, torch.float32)
+        assert np.array_equal(got, oracle.round_f32(val))
+    else:
+        got = _export(P, sp.EXPORT_SLICE_VAL, tot, torch.int16).view(np.uint16)
+        assert np.array_equal(got, oracle.round_bf16(val))
+    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr)
+    if span < 65536:
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_OFF16, tot, torch.int16).view(np.uint16), off)
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWBASE, 32 * S, torch.int32), base)
+        with pytest.raises(sp.SpmvError):
+            _export(P, sp.EXPORT_SLICE_COL, tot, torch.int32)
+    else:
+        assert np.array_equal(_export(P, sp.EXPORT_SLICE_COL, tot, torch.int32), col)
+
+
+@pytest.mark.parametrize("vt,vkind", [(sp.VAL_F32, 1), (sp.VAL_BF16, 2)])
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_sliced_low_precision_parity(vt, vkind, name, A):
+    """FP32 accumulation: rows in slices are summed in row order with fmaf,
+    bit for bit the oracle's FP32 form; long rows (segments + shuffle tree)
+    within the FP32 bound.  FP64 accumulation: within the FP64 bound."""
+    lowval = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
+    x = synth.uniform_vector(A.n_cols, 5)
+    y32, _ = _run(A, sp.make_choice("sliced", value_type=vt), x)
+    ref32 = oracle.spmv_lowp32(A, x, vkind, lowval)
+    lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
+    short = lens <= 1024
+    got = y32.cpu().numpy()
+    assert np.array_equal(got[short], ref32[short])
+    if (~short).any():
+        bound = _lowp32_bound(A, x, lowval, vkind)
+        assert np.all(np.abs(got - ref32)[~short] <= bound[~short])
+    y64, _ = _run(A, sp.make_choice("sliced", value_type=vt, accumulate=sp.ACC_F64), x)
+    ref64 = oracle.spmv_lowp(A, x, vkind, lowval)
+    _, scale = oracle.spmv_ref(A, x)
+    assert np.all(np.abs(y64.cpu().numpy() - ref64) <= RTOL * scale * 1.01)
+
+
 def test_sliced_auto_window_and_long_rows():
     # regular rows: kept in order; Zipf rows: sorted in windows of 256, and
     # the rows above 1024 nonzeros computed from CSR
