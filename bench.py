@@ -59,6 +59,23 @@ def _traffic(variant: str, matrix: str):
         return None
 
 
+def _max_over_ranks(v: float, ws: int, device) -> float:
+    """The slowest rank's value (the job's time); identity on one rank."""
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_gbs(bytes_per_step_per_rank: int, steps: int, ws: int, total_ms: float) -> float:
+    """Whole-job throughput: the bytes every replica processed over the
+    slowest replica's time (weak scaling: each rank runs the full workload)."""
+    return bytes_per_step_per_rank * steps * ws / (total_ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -304,15 +321,11 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = g0.elapsed_time(g1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(g0.elapsed_time(g1), ws, "cuda")
     kern_ms = [statistics.mean(ev[k][m][0].elapsed_time(ev[k][m][1]) for k in range(args.steps))
                for m in range(len(per))]
     step_bytes = sum(r["min_bytes"] for r in per)
-    value = step_bytes * args.steps * ws / (total_ms * 1e-3) / 1e9
+    value = _job_gbs(step_bytes, args.steps, ws, total_ms)
 
     # ---------------- end to end through the public API with host buffers
     hx = [x.cpu().pin_memory() for x in xs]
