@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "rowdot.cuh"
+#include "sliced.cuh"
 
 struct BatchMat {
     const int* rp;

@@ -13,9 +13,16 @@
 // Dot products are deterministic: each block writes its partial sum, and the
 // last block to finish (an atomic ticket, no waiting) adds the partials in
 // block order and updates the scalars.
+//
+// With a SLICED inner matrix (no rows above 1024 nonzeros) q = A p and p.q
+// are one kernel, and when that matrix sums in FP32 the p update also writes
+// p's FP32 copy, so no separate conversion of p runs per iteration.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
+#include "sliced.cuh"
 
 namespace spmvlib {
 namespace {
@@ -135,14 +142,97 @@ k_axpy_x(int64_t n, double* __restrict__ x, const double* __restrict__ p, const 
         x[i] = fma(alpha, p[i], x[i]);
 }
 
-// p = r + beta p  (INIT: p = r)
+// p = r + beta p  (INIT: p = r); with p32, also its FP32 copy for a
+// low-precision inner SpMV that sums in FP32 (the same rounding its own
+// conversion of x would apply)
 template <bool INIT>
 __global__ void __launch_bounds__(kCT)
-k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ r, const CgState* st)
+k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ r, const CgState* st,
+           float* __restrict__ p32)
 {
     const double beta = INIT ? 0.0 : st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT)
-        p[i] = INIT ? r[i] : fma(beta, p[i], r[i]);
+    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT) {
+        const double v = INIT ? r[i] : fma(beta, p[i], r[i]);
+        p[i] = v;
+        if (p32) p32[i] = __double2float_rn(v);
+    }
+}
+
+// Fused q = A p and p.q for a SLICED inner matrix without long rows: each
+// lane computes its row's q_i (dev::slice_value / slice_value_lp, the same
+// arithmetic as the SLICED kernels) and adds p_i q_i to its block's partial;
+// the last block sums the partials in block order and sets pq and alpha.
+struct SlArgs {
+    int64_t n_slices;
+    const int* rowlen; const int* slice_len; const int64_t* slice_ptr; const int* perm;
+    const int* col; const double* val; const uint16_t* off; const int* rowbase; const void* lowval;
+};
+
+template <typename VT, bool OFF16, bool ACC32>
+__global__ void __launch_bounds__(kCT, 6)
+k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p32,
+             double* __restrict__ q, double* __restrict__ part, CgState* st)
+{
+    __shared__ double red[kCT / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = (int64_t)gridDim.x * (kCT / 32);
+    double contrib = 0.0;
+    // grid-stride over slices (a few blocks per SM): few partials, few tickets
+    for (int64_t s = ((int64_t)blockIdx.x * kCT + threadIdx.x) >> 5; s < a.n_slices; s += n_warps) {
+        int row;
+        double v;
+        if constexpr (sizeof(VT) == 8)
+            v = dev::slice_value<4>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm, a.col, a.val, p, &row);
+        else
+            v = dev::slice_value_lp<4, VT, OFF16, ACC32>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
+                                                         a.col, a.off, a.rowbase,
+                                                         static_cast<const VT*>(a.lowval), p, p32, &row);
+        if (row >= 0) {
+            q[row] = v;
+            contrib = fma(p[row], v, contrib);
+        }
+    }
+    contrib = block_reduce(contrib, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = contrib;
+    if (!last_block(&st->ticket)) return;
+    const double sum = sum_partials(part, red);
+    if (threadIdx.x == 0) {
+        st->pq = sum;
+        st->alpha = st->rs / sum;
+        st->ticket = 0;
+    }
+}
+
+bool fusable(const spmv_prepared* P)
+{
+    return P->c.variant == SPMV_V7_SLICED && P->sl.n_long == 0 && P->A.n_rows > 0;
+}
+
+unsigned sliced_dot_grid(const spmv_prepared* P)
+{
+    const int64_t need = (32 * P->sl.n_slices + kCT - 1) / kCT;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)P->sm_count * 6));
+}
+
+cudaError_t launch_sliced_dot(const spmv_prepared* P, const double* p, double* q, double* part,
+                              CgState* st, cudaStream_t s)
+{
+    const SlicedPlan& d = P->sl;
+    SlArgs a{d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, d.sigma > 1 ? d.perm : nullptr,
+             d.col, d.val, d.off, d.rowbase, d.lowval};
+    const unsigned grid = sliced_dot_grid(P);
+    if (d.value_type == SPMV_VAL_F64) {
+        k_sliced_dot<double, false, false><<<grid, kCT, 0, s>>>(a, p, nullptr, q, part, st);
+    } else {
+#define SPMV_CG_SL(VT, O16, A32) k_sliced_dot<VT, O16, A32><<<grid, kCT, 0, s>>>(a, p, d.x32, q, part, st)
+#define SPMV_CG_SL_VT(VT)                                                                  \
+    if (d.off16) { if (d.acc32) SPMV_CG_SL(VT, true, true); else SPMV_CG_SL(VT, true, false); } \
+    else { if (d.acc32) SPMV_CG_SL(VT, false, true); else SPMV_CG_SL(VT, false, false); }
+        if (d.value_type == SPMV_VAL_F32) { SPMV_CG_SL_VT(float) } else { SPMV_CG_SL_VT(__nv_bfloat16) }
+#undef SPMV_CG_SL_VT
+#undef SPMV_CG_SL
+    }
+    return cudaGetLastError();
 }
 
 struct CgBufs {
@@ -156,13 +246,21 @@ spmv_status enqueue_cg(const spmv_prepared* Pi, const spmv_prepared* Pe, const d
 {
     const int64_t n = Pi->A.n_rows;
     spmv_status st;
+    // a SLICED inner matrix takes the fused q = A p, p.q kernel; when it sums
+    // in FP32, p's FP32 copy is written by the p update
+    const bool fused = fusable(Pi);
+    float* p32 = fused && Pi->sl.acc32 ? Pi->sl.x32 : nullptr;
     // r0 = b - A x0 (exact), p0 = r0
     if ((st = spmv(Pe, x, w.q, reinterpret_cast<spmv_stream_t>(s))) != SPMV_OK) return st;
     k_update<false, true, kInit><<<grid, kCT, 0, s>>>(n, x, w.p, w.r, w.q, b, w.part, w.st, resid, 0);
-    k_update_p<true><<<grid, kCT, 0, s>>>(n, w.p, w.r, w.st);
+    k_update_p<true><<<grid, kCT, 0, s>>>(n, w.p, w.r, w.st, p32);
     for (int t = 1; t <= iters; ++t) {
-        if ((st = spmv(Pi, w.p, w.q, reinterpret_cast<spmv_stream_t>(s))) != SPMV_OK) return st;
-        k_dot_pq<kAlpha><<<grid, kCT, 0, s>>>(n, w.p, w.q, w.part, w.st);
+        if (fused) {
+            SPMV_CUDA_TRY(launch_sliced_dot(Pi, w.p, w.q, w.part, w.st, s));
+        } else {
+            if ((st = spmv(Pi, w.p, w.q, reinterpret_cast<spmv_stream_t>(s))) != SPMV_OK) return st;
+            k_dot_pq<kAlpha><<<grid, kCT, 0, s>>>(n, w.p, w.q, w.part, w.st);
+        }
         if (refine > 0 && t % refine == 0) {
             k_axpy_x<<<grid, kCT, 0, s>>>(n, x, w.p, w.st);
             if ((st = spmv(Pe, x, w.q, reinterpret_cast<spmv_stream_t>(s))) != SPMV_OK) return st;
@@ -172,7 +270,7 @@ spmv_status enqueue_cg(const spmv_prepared* Pi, const spmv_prepared* Pe, const d
             k_update<true, false, kBeta><<<grid, kCT, 0, s>>>(n, x, w.p, w.r, w.q, b, w.part,
                                                               w.st, resid, t);
         }
-        k_update_p<false><<<grid, kCT, 0, s>>>(n, w.p, w.r, w.st);
+        k_update_p<false><<<grid, kCT, 0, s>>>(n, w.p, w.r, w.st, p32);
     }
     SPMV_CUDA_TRY(cudaGetLastError());
     return SPMV_OK;
@@ -207,7 +305,8 @@ extern "C" spmv_status spmv_cg(const spmv_prepared_t* A_inner, const spmv_prepar
     SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.r), 8 * n, s));
     SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.p), 8 * n, s));
     SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.q), 8 * n, s));
-    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.part), 8 * (size_t)grid, s));
+    const size_t n_part = std::max<size_t>(grid, fusable(Pi) ? sliced_dot_grid(Pi) : 0);
+    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.part), 8 * n_part, s));
     SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w.st), sizeof(CgState), s));
     SPMV_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(CgState), s));
     if (use_graph) {

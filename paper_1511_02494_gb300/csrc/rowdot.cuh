@@ -94,45 +94,6 @@ __device__ __forceinline__ double row_partial(int64_t b, int64_t e, int lane, co
     return acc;
 }
 
-// One 32-row slice of the sliced layout: lane l sums the row at position
-// p = 32 s + l, element k of which sits at col/val[slice_ptr[s] + 32 k + l],
-// as one DFMA chain in row order; loads and DFMAs past the row's length are
-// predicated off.  rowlen[p] < 0 marks a position without a row (a long row
-// computed elsewhere, or past the last row): nothing is written for it.
-template <int U>
-__device__ __forceinline__ void slice_rows(int64_t s, int lane, const int* __restrict__ rowlen,
-                                           const int* __restrict__ slice_len,
-                                           const int64_t* __restrict__ slice_ptr,
-                                           const int* __restrict__ perm,
-                                           const int* __restrict__ col,
-                                           const double* __restrict__ val,
-                                           const double* __restrict__ x, double* __restrict__ y)
-{
-    const int64_t p = s * 32 + lane;
-    const int len = rowlen[p];
-    const int L = slice_len[s];
-    const int64_t q0 = slice_ptr[s] + lane;
-    const int* __restrict__ cp = col + q0;      // element k at cp[32 k] (k < 1025)
-    const double* __restrict__ vp = val + q0;
-    double acc = 0.0;
-    for (int k = 0; k < L; k += U) {
-        int c[U];
-        double a[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = k + u < len;
-            c[u] = ok ? __ldcs(cp + (k + u) * 32) : 0;
-            a[u] = ok ? __ldcs(vp + (k + u) * 32) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (k + u < len) acc = fma(a[u], xv[u], acc);
-    }
-    if (len >= 0) y[perm ? perm[p] : p] = acc;
-}
-
 // FP32 form for low-precision values: x comes from an FP32 copy, products
 // and sums are FP32 FMAs (the FP32 pipe is ~60x wider than FP64's on this
 // GPU), so the row costs no FP64 instruction at all.

@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 #include "rowdot.cuh"
+#include "sliced.cuh"
 
 namespace spmvlib {
 namespace {
@@ -260,9 +261,7 @@ __global__ void k_sl_x_to_f32(int64_t n, const double* __restrict__ x, float* __
     if (i < n) x32[i] = __double2float_rn(x[i]);
 }
 
-// One slice with low-precision values.  ACC32: FP32 copy of x, fmaf chain in
-// row order, one widening per row (bit for bit the oracle's FP32 form);
-// else each value widened to FP64 and a DFMA chain.
+// One slice with low-precision values (slice_value_lp).
 template <int U, typename VT, bool OFF16, bool ACC32>
 __global__ void __launch_bounds__(kSB, 8)
 k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
@@ -273,42 +272,10 @@ k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restr
 {
     const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
     if (s >= n_slices) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t p = s * 32 + lane;
-    const int len = rowlen[p];
-    const int L = slice_len[s];
-    const int64_t q0 = slice_ptr[s] + lane;
-    const int base = OFF16 ? rowbase[p] : 0;
-    const VT* __restrict__ vp = val + q0;
-    float acc32 = 0.f;
-    double acc64 = 0.0;
-    for (int k = 0; k < L; k += U) {
-        int c[U];
-        float a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = k + u < len;
-            if (OFF16) c[u] = ok ? base + (int)__ldcs(off + q0 + (k + u) * 32) : 0;
-            else c[u] = ok ? __ldcs(col + q0 + (k + u) * 32) : 0;
-            a[u] = ok ? ldval32(vp + (k + u) * 32) : 0.f;  // exact widening of FP32 / BF16
-        }
-        if (ACC32) {
-            float xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? __ldg(x32 + c[u]) : 0.f;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (k + u < len) acc32 = fmaf(a[u], xv[u], acc32);
-        } else {
-            double xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (k + u < len) acc64 = fma((double)a[u], xv[u], acc64);
-        }
-    }
-    if (len >= 0) y[perm ? perm[p] : p] = ACC32 ? (double)acc32 : acc64;
+    int row;
+    const double v = slice_value_lp<U, VT, OFF16, ACC32>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr,
+                                                         perm, col, off, rowbase, val, x, x32, &row);
+    if (row >= 0) y[row] = v;
 }
 
 // long-row segments with the values rounded as the slices' (same arithmetic

@@ -38,7 +38,7 @@ def _close(x, r, xo, ro):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-@pytest.mark.parametrize("variant", ["subwarp", "compressed", "dynamic", "stream"])
+@pytest.mark.parametrize("variant", ["subwarp", "compressed", "dynamic", "stream", "sliced"])
 def test_cg_fp64_matches_oracle(variant, graph):
     A = synth.variable_coeff_laplacian_3d(14, seed=1)
     b = synth.uniform_vector(A.n_rows, 3)
@@ -54,10 +54,11 @@ def test_cg_low_precision_inner_matches_oracle(vt, vkind, refine):
     A = synth.variable_coeff_laplacian_3d(12, seed=2)
     b = synth.uniform_vector(A.n_rows, 4)
     low = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
-    x, r = _run(A, b, 50, sp.make_choice("compressed", value_type=vt, accumulate=sp.ACC_F64),
-                refine=refine)
-    xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 50, vkind=vkind, lowval=low, refine=refine)
-    _close(x, r, xo, ro)
+    for variant in ("compressed", "sliced"):
+        x, r = _run(A, b, 50, sp.make_choice(variant, value_type=vt, accumulate=sp.ACC_F64),
+                    refine=refine)
+        xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 50, vkind=vkind, lowval=low, refine=refine)
+        _close(x, r, xo, ro)
 
 
 def test_cg_refinement_recovers_fp64_accuracy():
@@ -88,7 +89,52 @@ def test_cg_fp32_accumulation_with_refinement_reaches_fp64_accuracy(vt, graph):
     b = synth.uniform_vector(A.n_rows, 5)
     x, _ = _run(A, b, 150, sp.make_choice("compressed", value_type=vt), refine=10, graph=graph)
     xn, _ = _run(A, b, 150, sp.make_choice("compressed", value_type=vt), refine=0)
+    # the fused SLICED path (p's FP32 copy written by the p update)
+    xs, _ = _run(A, b, 150, sp.make_choice("sliced", value_type=vt), refine=10, graph=graph,
+                 exact="sliced")
+    res_s = np.linalg.norm(b.numpy() - oracle.spmv(A, xs)) / np.linalg.norm(b.numpy())
+    assert res_s < 1e-8
     res = np.linalg.norm(b.numpy() - oracle.spmv(A, x)) / np.linalg.norm(b.numpy())
     res_n = np.linalg.norm(b.numpy() - oracle.spmv(A, xn)) / np.linalg.norm(b.numpy())
     assert res < 1e-8
     assert res_n > 10 * res
+
+
+def _laplacian_with_full_row(m=40, eps=1e-3):
+    """SPD: the 2-D Laplacian on an m x m grid plus a weak coupling of row
+    and column 0 to every other unknown (a row above 1024 nonzeros), with the
+    diagonal raised to keep it dominant; conditioned like the Laplacian."""
+    L = synth.laplacian_2d_5pt(m, m)
+    n = L.n_rows
+    rp, ci, v = L.rowptr.numpy(), L.colind.numpy(), L.val.numpy()
+    entries = {}
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            entries[(i, int(ci[k]))] = float(v[k])
+    for j in range(1, n):
+        entries[(0, j)] = entries.get((0, j), 0.0) - eps
+        entries[(j, 0)] = entries.get((j, 0), 0.0) - eps
+        entries[(j, j)] += eps
+    entries[(0, 0)] += eps * (n - 1)
+    keys = sorted(entries)
+    r = np.array([k[0] for k in keys]); c = np.array([k[1] for k in keys])
+    vals = np.array([entries[k] for k in keys])
+    rpn = np.zeros(n + 1, np.int64)
+    np.add.at(rpn, r + 1, 1)
+    return synth.HostCSR(n, n, torch.from_numpy(np.cumsum(rpn).astype(np.int32)),
+                         torch.from_numpy(c.astype(np.int32)), torch.from_numpy(vals), "lap_full_row")
+
+
+@pytest.mark.parametrize("vt", [None, sp.VAL_BF16])
+def test_cg_sliced_with_a_long_row_takes_the_unfused_path(vt):
+    A = _laplacian_with_full_row()
+    b = synth.uniform_vector(A.n_rows, 9)
+    ch = sp.make_choice("sliced") if vt is None else sp.make_choice("sliced", value_type=vt,
+                                                                     accumulate=sp.ACC_F64)
+    dA = sp.DeviceCSR.from_host(A)
+    assert sp.spmv_prepare(dA, ch).info().launches >= 3  # long-row segments present
+    x, r = _run(A, b, 40, ch, refine=10 if vt else 0)
+    low = None if vt is None else oracle.round_bf16(A.val)
+    xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 40, vkind=0 if vt is None else 2, lowval=low,
+                       refine=10 if vt else 0)
+    _close(x, r, xo, ro)
