@@ -387,6 +387,16 @@ spmv_status spmv(const spmv_prepared_t *P, const double *x, double *y, spmv_stre
 spmv_status spmv_host(spmv_prepared_t *P, const double *x_host, double *y_host,
                       spmv_stream_t stream);
 
+/* spmv_host without the final synchronisation: the copy of x, the SpMV and
+ * the copy of y are enqueued on `stream`, and y_host is valid once the
+ * stream has been synchronised.  With page-locked x_host and y_host the
+ * copies are asynchronous, so calls on different prepared objects issued on
+ * different streams overlap: one matrix's upload, another's SpMV and a
+ * third's download run at once.  Calls on one prepared object must not
+ * overlap (they share its staging buffers). */
+spmv_status spmv_host_async(spmv_prepared_t *P, const double *x_host, double *y_host,
+                            spmv_stream_t stream);
+
 spmv_status spmv_prepared_info(const spmv_prepared_t *P, spmv_prepared_info_t *info);
 
 /* Copies one owned array of P (see spmv_export) into host memory dst of

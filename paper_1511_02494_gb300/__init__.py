@@ -201,6 +201,12 @@ def spmv_host(P: Prepared, x_host, y_host, stream=None) -> None:
     _check(lib().spmv_host(P.handle, _ptr(x_host), _ptr(y_host), _stream(stream)))
 
 
+def spmv_host_async(P: Prepared, x_host, y_host, stream=None) -> None:
+    """As spmv_host, enqueued on `stream` without waiting: y_host is valid
+    after the stream is synchronised (pinned tensors for overlap)."""
+    _check(lib().spmv_host_async(P.handle, _ptr(x_host), _ptr(y_host), _stream(stream)))
+
+
 def spmv_prepared_info(P: Prepared) -> PreparedInfo:
     out = PreparedInfo()
     _check(lib().spmv_prepared_info(P.handle, C.byref(out)))

@@ -96,6 +96,7 @@ def declare(lib):
         "spmv_prepare": (I32, [C.POINTER(CSR), C.POINTER(Choice), I32, C.POINTER(P), P]),
         "spmv": (I32, [P, P, P, P]),
         "spmv_host": (I32, [P, P, P, P]),
+        "spmv_host_async": (I32, [P, P, P, P]),
         "spmv_prepared_info": (I32, [P, C.POINTER(PreparedInfo)]),
         "spmv_prepared_export": (I32, [P, I32, P, I64, P]),
         "spmv_prepared_status": (I32, [P, P]),

@@ -546,6 +546,15 @@ spmv_status spmv(const spmv_prepared_t* P, const double* x, double* y, spmv_stre
 spmv_status spmv_host(spmv_prepared_t* P, const double* x_host, double* y_host,
                       spmv_stream_t stream)
 {
+    spmv_status st = spmv_host_async(P, x_host, y_host, stream);
+    if (st != SPMV_OK) return st;
+    SPMV_CUDA_TRY(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    return SPMV_OK;
+}
+
+spmv_status spmv_host_async(spmv_prepared_t* P, const double* x_host, double* y_host,
+                            spmv_stream_t stream)
+{
     clear_error();
     if (!P || (!x_host && P->A.n_cols > 0) || (!y_host && P->A.n_rows > 0))
         return fail(SPMV_ERR_INVALID_ARG, "spmv_host: NULL argument");
@@ -561,7 +570,6 @@ spmv_status spmv_host(spmv_prepared_t* P, const double* x_host, double* y_host,
     if (st != SPMV_OK) return st;
     if (P->A.n_rows > 0)
         SPMV_CUDA_TRY(cudaMemcpyAsync(y_host, P->y_stage, 8 * P->A.n_rows, cudaMemcpyDeviceToHost, s));
-    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     return SPMV_OK;
 }
 

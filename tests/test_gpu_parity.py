@@ -556,6 +556,25 @@ def test_spmv_host_end_to_end():
         _assert_close(y, A, x)
 
 
+def test_spmv_host_async_on_several_streams():
+    """Matrices issued with spmv_host_async on separate streams, each y
+    valid after its stream is synchronised."""
+    mats = [synth.stencil_27pt(14, seed=3), synth.random_csr(20_000, 15_000, 12, seed=4),
+            synth.short_rows(30_000, 8, seed=5)]
+    variants = ["sliced", "subwarp", "compressed"]
+    preps = [sp.spmv_prepare(sp.DeviceCSR.from_host(A), sp.make_choice(v)) for A, v in zip(mats, variants)]
+    xs = [synth.uniform_vector(A.n_cols, 20 + i).pin_memory() for i, A in enumerate(mats)]
+    ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64).pin_memory() for A in mats]
+    streams = [torch.cuda.Stream() for _ in mats]
+    for _ in range(2):
+        for P, x, y, s in zip(preps, xs, ys, streams):
+            sp.spmv_host_async(P, x, y, stream=s)
+        for s in streams:
+            s.synchronize()
+        for A, x, y in zip(mats, xs, ys):
+            _assert_close(y, A, x)
+
+
 # ----------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def four_class():
