@@ -529,6 +529,43 @@ def run_cg(args):
     return 0
 
 
+def run_features(args):
+    """Feature extraction (Table 1) on the four-class matrices: wall time of
+    spmv_features (kernel, readback, host derivation) against the selected
+    SpMV, and its bytes: rowptr and colind once."""
+    import numpy as np
+    import torch
+    import paper_1511_02494_gb300 as sp
+    import synth
+    from paper_1511_02494_gb300.build import build
+    build()
+    out = {"mode": "features", "matrices": []}
+    for A in synth.four_class_set():
+        dA = sp.DeviceCSR.from_host(A)
+        for _ in range(3):
+            sp.spmv_features(dA)
+        ts = []
+        for _ in range(7):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sp.spmv_features(dA)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = float(np.median(ts))
+        nbytes = 4 * (A.n_rows + 1) + 4 * A.nnz
+        P = sp.spmv_prepare(dA, sp.make_choice("sliced"))
+        x = synth.uniform_vector(A.n_cols, 0).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        spmv_ms = _time_ms(lambda: sp.spmv(P, x, y))
+        out["matrices"].append({"matrix": A.name, "features_ms": round(ms, 4), "bytes": nbytes,
+                                "gbs": round(nbytes / ms / 1e6, 1), "sliced_spmv_ms": round(spmv_ms, 4),
+                                "features_in_spmvs": round(ms / spmv_ms, 2)})
+        P.free()
+        del dA
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_batch(args):
     """512 uneven matrices: one launch per matrix with each matrix's own
     selected variant, against one persistent launch that runs every matrix
@@ -606,6 +643,7 @@ def main():
     ap.add_argument("--matrix", default="stencil", choices=["stencil", "random", "zipf", "short"])
     ap.add_argument("--cg", action="store_true", help="mixed-precision SpMV and CG report")
     ap.add_argument("--batch", action="store_true", help="batched persistent SpMV report")
+    ap.add_argument("--features", action="store_true", help="feature extraction report")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -613,6 +651,8 @@ def main():
         return run_single(args)
     if args.cg:
         return run_cg(args)
+    if args.features:
+        return run_features(args)
     if args.batch:
         return run_batch(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -12,6 +12,8 @@
 // The doubles of Table 1 are derived on the host from these integers.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace spmvlib {
@@ -28,6 +30,8 @@ struct FeatAcc {
     u64 disp_sum, disp_sq_lo, disp_sq_hi, clust_sum;
     u64 ngroups_sum, misses_sum;
     u64 err;
+    u64 n_long;  // rows of kShortCap < nnz <= kChunk (front of the list)
+    u64 n_huge;  // rows of nnz > kChunk (back of the list, chunked)
 };
 
 __device__ __forceinline__ u64 shfl_u64(u64 v, int o) {
@@ -65,136 +69,108 @@ __device__ __forceinline__ u64 warp_max_u64(u64 v) {
 
 constexpr int kFields = 16;  // FeatAcc words reduced per block (err excluded)
 
-// Sub-warp of T lanes per row; a grid-stride loop over row groups.  Each lane
-// examines elements j = b + lane + k T, four per pass, comparing each column
-// with its predecessor in the row.
-template <int T, bool FEATURES>
-__global__ void __launch_bounds__(256)
-k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restrict__ rp,
-               const int* __restrict__ ci, int64_t line_bytes, FeatAcc* __restrict__ acc)
+// floor(a 2^32 / b) for 0 <= a <= b < 2^31, exactly, without a 64-bit
+// integer division: an FP32 estimate of the quotient, then the integer
+// remainder a 2^32 - q b corrected into [0, b).  The estimate is within about
+// 800 of the quotient and the remainder's own FP32 correction within one, so
+// the final steps run at most once (capped at four).  Arguments outside that
+// range come only from rows the pass flags as invalid (columns not strictly
+// increasing or out of range), whose results are discarded: they give 0.
+__device__ __forceinline__ u64 fixq32(u64 a, u64 b)
 {
-    constexpr int U = 4;
-    __shared__ u64 s_red[8][kFields];
-    __shared__ u64 s_err;
-    const int lane = threadIdx.x & (T - 1);
-    const int64_t groups_total = (int64_t)gridDim.x * (blockDim.x / T);
+    if (a == 0 || b == 0 || b >= (1ull << 31) || a > b) return 0;
+    if (a == b) return 1ull << 32;
+    const float rb = __frcp_rn((float)b);
+    const u64 num = a << 32;
+    u64 q = (u64)__fmul_rn(__fmul_rn((float)a, rb), 4294967296.0f);
+    int64_t rem = (int64_t)(num - q * b);
+    const int64_t c = (int64_t)floorf(__fmul_rn((float)rem, rb));
+    q += (u64)c;
+    rem -= c * (int64_t)b;
+    for (int i = 0; i < 4 && rem < 0; ++i) { --q; rem += (int64_t)b; }
+    for (int i = 0; i < 4 && rem >= (int64_t)b; ++i) { ++q; rem -= (int64_t)b; }
+    return q;
+}
+
+// Per-thread partial aggregates of the rows a thread finalizes.
+struct RowAgg {
     u64 nnz_min_c = 0, nnz_max = 0, nnz_sum = 0, nnz_sq = 0;
     u64 bw_min_c = 0, bw_max = 0, bw_sum = 0, disp_sum = 0, clust_sum = 0, ng_sum = 0, ms_sum = 0;
     u128 bw_sq = 0, disp_sq = 0;
-    u64 err = 0;
-    if (threadIdx.x == 0) s_err = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (rp[0] != 0) err |= 1;
-        if ((int64_t)rp[n_rows] != nnz) err |= 2;
+
+    // one row: nz nonzeros, columns first..last, ng / ms counted over its
+    // elements after the first (the first element adds one to each)
+    __device__ __forceinline__ void add(u64 nz, int64_t first, int64_t last, u64 ng, u64 ms) {
+        u64 bw = 0, dq = 0, cq = 0;
+        if (nz > 0) {
+            bw = (u64)(last - first);
+            ng += 1;
+            ms += 1;
+            dq = fixq32(nz, bw + 1);
+            cq = fixq32(ng, nz);
+        }
+        nnz_min_c = max(nnz_min_c, ~nz);
+        nnz_max = max(nnz_max, nz);
+        nnz_sum += nz;
+        nnz_sq += nz * nz;
+        bw_min_c = max(bw_min_c, ~bw);
+        bw_max = max(bw_max, bw);
+        bw_sum += bw;
+        bw_sq += (u128)bw * bw;
+        disp_sum += dq;
+        disp_sq += (u128)dq * dq;
+        clust_sum += cq;
+        ng_sum += ng;
+        ms_sum += ms;
     }
-    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
-    const int64_t n_iter = (n_rows + groups_total - 1) / groups_total;
-    for (int64_t it = 0; it < n_iter; ++it) {
-        const int64_t row = g0 + it * groups_total;
-        int64_t b = 0, e = 0;
-        bool ok = row < n_rows;
-        if (ok) {
-            b = rp[row];
-            e = rp[row + 1];
-            if (b < 0 || e < b || e > nnz) { err |= 4; ok = false; b = e = 0; }
-        }
-        u64 ng = 0, ms = 0, bad = 0;
-        for (int64_t j0 = b + lane; j0 < e; j0 += (int64_t)U * T) {
-            int64_t c[U], cp[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t j = j0 + u * T;
-                c[u] = j < e ? (int64_t)ci[j] : 0;
-                cp[u] = (j < e && j > b) ? (int64_t)ci[j - 1] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t j = j0 + u * T;
-                if (j < e) {
-                    if (c[u] < 0 || c[u] >= n_cols) bad |= 8;
-                    if (j > b) {
-                        const int64_t d = c[u] - cp[u];
-                        if (d <= 0) bad |= 16;
-                        ng += (d != 1);
-                        ms += (8 * d > line_bytes);
-                    }
-                }
-            }
-        }
-        for (int o = T >> 1; o > 0; o >>= 1) {
-            ng += __shfl_xor_sync(FULL_MASK, ng, o);
-            ms += __shfl_xor_sync(FULL_MASK, ms, o);
-            bad |= __shfl_xor_sync(FULL_MASK, bad, o);
-        }
-        err |= bad;
-        if (FEATURES && ok && lane == 0) {
-            const u64 nz = (u64)(e - b);
-            u64 bw = 0, dq = 0, cq = 0;
-            if (nz > 0) {
-                bw = (u64)((int64_t)ci[e - 1] - (int64_t)ci[b]);
-                ng += 1;
-                ms += 1;
-                dq = (nz << 32) / (bw + 1);
-                cq = (ng << 32) / nz;
-            }
-            nnz_min_c = max(nnz_min_c, ~nz);
-            nnz_max = max(nnz_max, nz);
-            nnz_sum += nz;
-            nnz_sq += nz * nz;
-            bw_min_c = max(bw_min_c, ~bw);
-            bw_max = max(bw_max, bw);
-            bw_sum += bw;
-            bw_sq += (u128)bw * bw;
-            disp_sum += dq;
-            disp_sq += (u128)dq * dq;
-            clust_sum += cq;
-            ng_sum += ng;
-            ms_sum += ms;
-        }
-    }
-    // warp reduction, then block reduction, then one set of atomics per block
+};
+
+// Warp reduction, then block reduction, then one set of atomics per block.
+template <bool FEATURES>
+__device__ void flush_block(RowAgg& r, u64 err, u64 (*s_red)[kFields], u64* s_err, FeatAcc* acc)
+{
     for (int o = 16; o > 0; o >>= 1) err |= shfl_u64(err, o);
     const int w = threadIdx.x >> 5;
     if (FEATURES) {
-        nnz_min_c = warp_max_u64(nnz_min_c);
-        nnz_max = warp_max_u64(nnz_max);
-        nnz_sum = warp_sum_u64(nnz_sum);
-        nnz_sq = warp_sum_u64(nnz_sq);
-        bw_min_c = warp_max_u64(bw_min_c);
-        bw_max = warp_max_u64(bw_max);
-        bw_sum = warp_sum_u64(bw_sum);
-        bw_sq = warp_sum_u128(bw_sq);
-        disp_sum = warp_sum_u64(disp_sum);
-        disp_sq = warp_sum_u128(disp_sq);
-        clust_sum = warp_sum_u64(clust_sum);
-        ng_sum = warp_sum_u64(ng_sum);
-        ms_sum = warp_sum_u64(ms_sum);
+        r.nnz_min_c = warp_max_u64(r.nnz_min_c);
+        r.nnz_max = warp_max_u64(r.nnz_max);
+        r.nnz_sum = warp_sum_u64(r.nnz_sum);
+        r.nnz_sq = warp_sum_u64(r.nnz_sq);
+        r.bw_min_c = warp_max_u64(r.bw_min_c);
+        r.bw_max = warp_max_u64(r.bw_max);
+        r.bw_sum = warp_sum_u64(r.bw_sum);
+        r.bw_sq = warp_sum_u128(r.bw_sq);
+        r.disp_sum = warp_sum_u64(r.disp_sum);
+        r.disp_sq = warp_sum_u128(r.disp_sq);
+        r.clust_sum = warp_sum_u64(r.clust_sum);
+        r.ng_sum = warp_sum_u64(r.ng_sum);
+        r.ms_sum = warp_sum_u64(r.ms_sum);
     }
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-        if (err) atomicOr(&s_err, err);
-        u64* r = s_red[w];
-        r[0] = nnz_min_c; r[1] = nnz_max; r[2] = nnz_sum; r[3] = nnz_sq;
-        r[4] = bw_min_c; r[5] = bw_max; r[6] = bw_sum;
-        r[7] = (u64)bw_sq; r[8] = (u64)(bw_sq >> 64);
-        r[9] = disp_sum; r[10] = (u64)disp_sq; r[11] = (u64)(disp_sq >> 64);
-        r[12] = clust_sum; r[13] = ng_sum; r[14] = ms_sum; r[15] = 0;
+        if (err) atomicOr(s_err, err);
+        u64* t = s_red[w];
+        t[0] = r.nnz_min_c; t[1] = r.nnz_max; t[2] = r.nnz_sum; t[3] = r.nnz_sq;
+        t[4] = r.bw_min_c; t[5] = r.bw_max; t[6] = r.bw_sum;
+        t[7] = (u64)r.bw_sq; t[8] = (u64)(r.bw_sq >> 64);
+        t[9] = r.disp_sum; t[10] = (u64)r.disp_sq; t[11] = (u64)(r.disp_sq >> 64);
+        t[12] = r.clust_sum; t[13] = r.ng_sum; t[14] = r.ms_sum; t[15] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nw = blockDim.x >> 5;
-        if (s_err) atomicOr(&acc->err, s_err);
+        if (*s_err) atomicOr(&acc->err, *s_err);
         if (FEATURES) {
             u64 t[kFields] = {0};
             u128 bsq = 0, dsq = 0;
             for (int k = 0; k < nw; ++k) {
-                const u64* r = s_red[k];
-                t[0] = max(t[0], r[0]); t[1] = max(t[1], r[1]); t[2] += r[2]; t[3] += r[3];
-                t[4] = max(t[4], r[4]); t[5] = max(t[5], r[5]); t[6] += r[6];
-                bsq += ((u128)r[8] << 64) | r[7];
-                t[9] += r[9];
-                dsq += ((u128)r[11] << 64) | r[10];
-                t[12] += r[12]; t[13] += r[13]; t[14] += r[14];
+                const u64* q = s_red[k];
+                t[0] = max(t[0], q[0]); t[1] = max(t[1], q[1]); t[2] += q[2]; t[3] += q[3];
+                t[4] = max(t[4], q[4]); t[5] = max(t[5], q[5]); t[6] += q[6];
+                bsq += ((u128)q[8] << 64) | q[7];
+                t[9] += q[9];
+                dsq += ((u128)q[11] << 64) | q[10];
+                t[12] += q[12]; t[13] += q[13]; t[14] += q[14];
             }
             if (t[0]) atomicMax(&acc->nnz_min_c, t[0]);
             if (t[1]) atomicMax(&acc->nnz_max, t[1]);
@@ -213,22 +189,240 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
     }
 }
 
-template <bool F>
-cudaError_t launch_pass(int T, unsigned grid, cudaStream_t s, const spmv_csr_t* A,
-                        int64_t line_bytes, FeatAcc* acc)
+// Elements [j0, e) of a row starting at b, every `step`-th one, U at a time:
+// ng counts columns that do not follow their predecessor by one, ms those
+// more than a line away from it; bad collects CSR violations.
+template <int U>
+__device__ __forceinline__ void count_elements(int64_t b, int64_t j0, int64_t e, int step,
+                                               const int* __restrict__ ci, int64_t n_cols,
+                                               int64_t line_bytes, u64& ng, u64& ms, u64& bad)
 {
-    switch (T) {
-#define SPMV_FP_CASE(TT)                                                                 \
-    case TT:                                                                             \
-        k_feature_pass<TT, F><<<grid, 256, 0, s>>>(A->n_rows, A->n_cols, A->nnz, A->rowptr, \
-                                                   A->colind, line_bytes, acc);          \
-        break;
-        SPMV_FP_CASE(1) SPMV_FP_CASE(2) SPMV_FP_CASE(4) SPMV_FP_CASE(8) SPMV_FP_CASE(16)
-        SPMV_FP_CASE(32)
-#undef SPMV_FP_CASE
-        default: return cudaErrorInvalidValue;
+    for (; j0 < e; j0 += (int64_t)U * step) {
+        int64_t c[U], cp[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u * step;
+            c[u] = j < e ? (int64_t)ci[j] : 0;
+            cp[u] = (j < e && j > b) ? (int64_t)ci[j - 1] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u * step;
+            if (j < e) {
+                if (c[u] < 0 || c[u] >= n_cols) bad |= 8;
+                if (j > b) {
+                    const int64_t d = c[u] - cp[u];
+                    if (d <= 0) bad |= 16;
+                    ng += (d != 1);
+                    ms += (8 * d > line_bytes);
+                }
+            }
+        }
     }
-    return cudaGetLastError();
+}
+
+// Rows of at most kShortCap nonzeros: a lane per row, warps taking tiles of
+// 32 consecutive rows.  Each lane walks its row in order, four loads in
+// flight, keeping the previous column in a register, so every element is
+// loaded once and the per-row arithmetic (two 64-bit divisions, 128-bit
+// squares) runs on all 32 lanes.  Longer rows are listed for the chunked
+// kernels below.
+constexpr int64_t kShortCap = 64;
+constexpr int64_t kChunk = 4096;
+
+template <bool FEATURES>
+__global__ void __launch_bounds__(256)
+k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restrict__ rp,
+               const int* __restrict__ ci, int64_t line_bytes, int* __restrict__ long_rows,
+               int64_t max_long, FeatAcc* __restrict__ acc)
+{
+    constexpr int U = 4;
+    __shared__ u64 s_red[8][kFields];
+    __shared__ u64 s_err;
+    const int lane = threadIdx.x & 31;
+    RowAgg r;
+    u64 err = 0;
+    if (threadIdx.x == 0) s_err = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rp[0] != 0) err |= 1;
+        if ((int64_t)rp[n_rows] != nnz) err |= 2;
+    }
+    const int64_t n_tiles = (n_rows + 31) / 32;
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; tile < n_tiles;
+         tile += n_warps) {
+        const int64_t row = tile * 32 + lane;
+        int64_t b = 0, nz = 0;
+        bool is_long = false, row_ok = false;
+        if (row < n_rows) {
+            b = rp[row];
+            const int64_t e = rp[row + 1];
+            if (b < 0 || e < b || e > nnz) { err |= 4; b = 0; }
+            else if (e - b > kShortCap) is_long = true;
+            else { nz = e - b; row_ok = true; }
+        }
+        u64 ng = 0, ms = 0;
+        int64_t first = 0, prev = 0;
+        if (nz > 0) {
+            first = prev = ci[b];
+            if (first < 0 || first >= n_cols) err |= 8;
+        }
+        for (int64_t k = 1; k < nz; k += U) {
+            int64_t c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) c[u] = k + u < nz ? (int64_t)ci[b + k + u] : 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (k + u < nz) {
+                    if (c[u] < 0 || c[u] >= n_cols) err |= 8;
+                    const int64_t d = c[u] - prev;
+                    if (d <= 0) err |= 16;
+                    ng += (d != 1);
+                    ms += (8 * d > line_bytes);
+                    prev = c[u];
+                }
+            }
+        }
+        if (FEATURES && row_ok) r.add((u64)nz, first, prev, ng, ms);
+        // long rows: up to kChunk nonzeros to the front of the list (a warp
+        // each), longer ones to the back (chunked)
+        const bool huge = is_long && rp[row + 1] - rp[row] > kChunk;
+        const unsigned mm = __ballot_sync(FULL_MASK, is_long && !huge);
+        const unsigned mh = __ballot_sync(FULL_MASK, huge);
+        if (mm | mh) {
+            u64 bm = 0, bh = 0;
+            if (lane == 0) {
+                if (mm) bm = atomicAdd(&acc->n_long, (u64)__popc(mm));
+                if (mh) bh = atomicAdd(&acc->n_huge, (u64)__popc(mh));
+            }
+            bm = __shfl_sync(FULL_MASK, bm, 0);
+            bh = __shfl_sync(FULL_MASK, bh, 0);
+            const unsigned lt = (1u << lane) - 1u;
+            // overlapping rows (a rowptr that is not monotone) can list more
+            // rows than the buffer holds; the error flag is set for them
+            if (is_long && !huge) {
+                const u64 pos = bm + __popc(mm & lt);
+                if (pos < (u64)max_long) long_rows[pos] = (int)row;
+                else err |= 4;
+            }
+            if (huge) {
+                const u64 pos = bh + __popc(mh & lt);
+                if (pos < (u64)max_long) long_rows[max_long - 1 - pos] = (int)row;
+                else err |= 4;
+            }
+        }
+    }
+    flush_block<FEATURES>(r, err, s_red, &s_err, acc);
+}
+
+// Exclusive scan of the huge rows' chunk counts (one block, a contiguous
+// segment per thread): chunk_off[q] is the first chunk of huge row q (list
+// entry max_long - 1 - q), chunk_off[n_huge] their total.  Also zeroes the
+// per-row totals, the tickets and the work counter of the chunk kernel.
+__global__ void __launch_bounds__(1024)
+k_chunk_offsets(const int* __restrict__ long_rows, int64_t max_long, const int* __restrict__ rp,
+                int* __restrict__ chunk_off, u64* __restrict__ ng, u64* __restrict__ ms,
+                unsigned* __restrict__ done, unsigned* __restrict__ next,
+                const FeatAcc* __restrict__ acc)
+{
+    __shared__ int part[1024];
+    const int64_t nh = min((int64_t)acc->n_huge, max_long);
+    const int n = (int)nh;
+    for (int q = threadIdx.x; q < n; q += 1024) { ng[q] = 0; ms[q] = 0; done[q] = 0; }
+    if (threadIdx.x == 0) *next = 0;
+    const int per = (n + 1023) / 1024;
+    const int q0 = min(n, (int)threadIdx.x * per), q1 = min(n, q0 + per);
+    int local = 0;
+    for (int q = q0; q < q1; ++q) {
+        const int row = long_rows[max_long - 1 - q];
+        local += (int)((rp[row + 1] - rp[row] + kChunk - 1) / kChunk);
+    }
+    part[threadIdx.x] = local;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - local;
+    for (int q = q0; q < q1; ++q) {
+        chunk_off[q] = run;
+        const int row = long_rows[max_long - 1 - q];
+        run += (int)((rp[row + 1] - rp[row] + kChunk - 1) / kChunk);
+    }
+    if (threadIdx.x == 1023) chunk_off[n] = part[1023];
+}
+
+// Chunks of kChunk nonzeros of the long rows: persistent warps take chunks
+// from an atomic counter, add the chunk's counts to the row's totals, and the
+// warp that completes a row's last chunk (a ticket per row) adds the row to
+// its aggregates.  Integer sums: the result does not depend on the order.
+struct LongScratch {
+    u64* ng;          // [max_long]
+    u64* ms;          // [max_long]
+    unsigned* done;   // [max_long] chunks finished
+    unsigned* next;   // work counter
+};
+
+template <bool FEATURES>
+__global__ void __launch_bounds__(256)
+k_feature_chunks(const int* __restrict__ long_rows, int64_t max_long, const int* __restrict__ chunk_off,
+                 int64_t n_cols, const int* __restrict__ rp, const int* __restrict__ ci,
+                 int64_t line_bytes, LongScratch w, FeatAcc* __restrict__ acc)
+{
+    __shared__ u64 s_red[8][kFields];
+    __shared__ u64 s_err;
+    if (threadIdx.x == 0) s_err = 0;
+    const int lane = threadIdx.x & 31;
+    const int n_mid = (int)min((int64_t)acc->n_long, max_long);
+    const int n_huge = (int)min((int64_t)acc->n_huge, max_long);
+    const int total = n_mid + (n_huge > 0 ? chunk_off[n_huge] : 0);
+    RowAgg r;
+    u64 bad = 0;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(w.next, 1u);
+        it = __shfl_sync(FULL_MASK, it, 0);
+        if (it >= total) break;
+        if (it < n_mid) {
+            // a row of at most kChunk nonzeros: the whole row by this warp
+            const int row = long_rows[it];
+            const int64_t b = rp[row], e = rp[row + 1];
+            u64 ng = 0, ms = 0;
+            count_elements<4>(b, b + lane, e, 32, ci, n_cols, line_bytes, ng, ms, bad);
+            ng = warp_sum_u64(ng);
+            ms = warp_sum_u64(ms);
+            if (FEATURES && lane == 0) r.add((u64)(e - b), (int64_t)ci[b], (int64_t)ci[e - 1], ng, ms);
+            continue;
+        }
+        const int ic = it - n_mid;
+        int lo = 0, hi = n_huge - 1;  // the huge row whose chunks include ic
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (chunk_off[mid] <= ic) lo = mid; else hi = mid - 1;
+        }
+        const int row = long_rows[max_long - 1 - lo];
+        const int64_t b = rp[row], e = rp[row + 1];
+        const int64_t c0 = b + (int64_t)(ic - chunk_off[lo]) * kChunk;
+        const int64_t c1 = min(e, c0 + kChunk);
+        u64 ng = 0, ms = 0;
+        count_elements<4>(b, c0 + lane, c1, 32, ci, n_cols, line_bytes, ng, ms, bad);
+        ng = warp_sum_u64(ng);
+        ms = warp_sum_u64(ms);
+        if (lane == 0) {
+            atomicAdd(&w.ng[lo], ng);
+            atomicAdd(&w.ms[lo], ms);
+            __threadfence();
+            const unsigned n_chunks = (unsigned)(chunk_off[lo + 1] - chunk_off[lo]);
+            if (atomicAdd(&w.done[lo], 1u) == n_chunks - 1) {
+                __threadfence();
+                const u64 tng = atomicAdd(&w.ng[lo], 0ull), tms = atomicAdd(&w.ms[lo], 0ull);
+                if (FEATURES) r.add((u64)(e - b), (int64_t)ci[b], (int64_t)ci[e - 1], tng, tms);
+            }
+        }
+    }
+    flush_block<FEATURES>(r, bad, s_red, &s_err, acc);
 }
 
 double sd_from_sums(u64 n, u64 s1, u128 s2)
@@ -243,6 +437,10 @@ float lg1p(double v) { return (float)log2(1.0 + v); }
 thread_local FeatAcc* t_host_acc = nullptr;
 thread_local FeatAcc* t_dev_acc = nullptr;
 thread_local int t_dev_acc_device = -1;
+// device scratch of the long-row kernels, per host thread; grows, never shrinks
+thread_local void* t_scratch = nullptr;
+thread_local size_t t_scratch_bytes = 0;
+thread_local int t_scratch_device = -1;
 
 }  // namespace
 
@@ -279,13 +477,53 @@ spmv_status run_feature_pass(const spmv_csr_t* A, int32_t line_bytes, spmv_featu
     FeatAcc* acc = t_dev_acc;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(FeatAcc), s);
     if (e == cudaSuccess && A->n_rows > 0) {
-        const int T = auto_threads_per_row((double)A->nnz / (double)A->n_rows / 4.0);
-        int64_t blocks = (A->n_rows * T + 255) / 256;
-        const int64_t cap = (int64_t)dev.sm_count * 16;
-        if (blocks > cap) blocks = cap;
+        // scratch: per-long-row totals and tickets, the work counter, the
+        // long-row list and the chunk offsets
+        const int64_t max_long = std::min<int64_t>(A->n_rows, A->nnz / (kShortCap + 1) + 1);
+        const size_t bytes = sizeof(u64) * 2 * (size_t)max_long + sizeof(unsigned) * (size_t)(max_long + 1) +
+                             sizeof(int) * (size_t)(2 * max_long + 1) + 64;
+        if (t_scratch_device != dev.device || t_scratch_bytes < bytes) {
+            if (t_scratch) cudaFree(t_scratch);
+            t_scratch = nullptr;
+            t_scratch_bytes = 0;
+            e = cudaMalloc(&t_scratch, bytes);
+            if (e == cudaSuccess) { t_scratch_bytes = bytes; t_scratch_device = dev.device; }
+        }
+        u64* ng = static_cast<u64*>(t_scratch);
+        u64* ms = ng + max_long;
+        unsigned* done = reinterpret_cast<unsigned*>(ms + max_long);
+        unsigned* next = done + max_long;
+        int* long_rows = reinterpret_cast<int*>(next + 1);
+        int* chunk_off = long_rows + max_long;
+        int64_t blocks = ((A->n_rows + 31) / 32 * 32 + 255) / 256;
+        const int64_t lim = (int64_t)dev.sm_count * 16;
+        if (blocks > lim) blocks = lim;
         if (blocks < 1) blocks = 1;
-        e = out ? launch_pass<true>(T, (unsigned)blocks, s, A, line_bytes, acc)
-                : launch_pass<false>(T, (unsigned)blocks, s, A, line_bytes, acc);
+        const unsigned cgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_long, (int64_t)dev.sm_count * 2));
+        LongScratch w{ng, ms, done, next};
+        if (e == cudaSuccess) {
+            if (out)
+                k_feature_pass<true><<<(unsigned)blocks, 256, 0, s>>>(A->n_rows, A->n_cols, A->nnz, A->rowptr,
+                                                                      A->colind, line_bytes, long_rows, max_long, acc);
+            else
+                k_feature_pass<false><<<(unsigned)blocks, 256, 0, s>>>(A->n_rows, A->n_cols, A->nnz, A->rowptr,
+                                                                       A->colind, line_bytes, long_rows, max_long, acc);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            k_chunk_offsets<<<1, 1024, 0, s>>>(long_rows, max_long, A->rowptr, chunk_off, ng, ms, done,
+                                               next, acc);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            if (out)
+                k_feature_chunks<true><<<cgrid, 256, 0, s>>>(long_rows, max_long, chunk_off, A->n_cols, A->rowptr,
+                                                             A->colind, line_bytes, w, acc);
+            else
+                k_feature_chunks<false><<<cgrid, 256, 0, s>>>(long_rows, max_long, chunk_off, A->n_cols, A->rowptr,
+                                                              A->colind, line_bytes, w, acc);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(t_host_acc, acc, sizeof(FeatAcc),
                                               cudaMemcpyDeviceToHost, s);
