@@ -87,9 +87,9 @@ def _load():
                 "orc_argmax": (i32, [i32, P, P]),
                 "orc_mlp_loss_grad_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
                 "orc_mlp_loss_grad_soft_f64": (C.c_double, [i32, i32, i32, i32] + [P] * 14),
-                "orc_sliced_layout": (i64, [i64, P, i32, i32, P, P, P, P]),
-                "orc_sliced_fill": (None, [i64, P, P, P, P, P, P, P, P]),
-                "orc_sliced_offsets": (i64, [i64, P, P, P, P, P, P, P]),
+                "orc_sliced_layout": (i64, [i64, P, i32, i32, i32, P, P, P, P]),
+                "orc_sliced_fill": (None, [i64, P, P, P, P, P, P, i32, P, P]),
+                "orc_sliced_offsets": (i64, [i64, P, P, P, P, P, i32, P, P]),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -235,7 +235,7 @@ def compress_u16(A):
     return base, off, int(wide)
 
 
-def sliced_layout(A, sigma: int, cap: int):
+def sliced_layout(A, sigma: int, cap: int, vec: int = 1):
     """Sliced layout (32 rows per slice, column-major inside a slice): the
     position -> row permutation, per-position row length (-1: long row or
     past the end), slice lengths and slice starts, and the long-row count."""
@@ -245,12 +245,12 @@ def sliced_layout(A, sigma: int, cap: int):
     rowlen = np.empty(max(32 * S, 1), np.int32)
     slen = np.empty(max(S, 1), np.int32)
     sptr = np.empty(S + 1, np.int64)
-    n_long = _load().orc_sliced_layout(A.n_rows, _p(rp), sigma, cap, _p(perm), _p(rowlen),
+    n_long = _load().orc_sliced_layout(A.n_rows, _p(rp), sigma, cap, vec, _p(perm), _p(rowlen),
                                        _p(slen), _p(sptr))
     return perm[:A.n_rows], rowlen[:32 * S], slen[:S], sptr, int(n_long)
 
 
-def sliced_fill(A, perm, rowlen, sptr):
+def sliced_fill(A, perm, rowlen, sptr, vec: int = 1):
     """Column-major slice contents (columns and values, zero padding)."""
     rp, ci, va = _csr(A)
     tot = int(sptr[-1])
@@ -260,11 +260,11 @@ def sliced_fill(A, perm, rowlen, sptr):
     rowlen = _np(rowlen, np.int32)
     sptr = _np(sptr, np.int64)
     _load().orc_sliced_fill(A.n_rows, _p(rp), _p(ci), _p(va), _p(perm), _p(rowlen), _p(sptr),
-                            _p(col), _p(val))
+                            vec, _p(col), _p(val))
     return col[:tot], val[:tot]
 
 
-def sliced_offsets(A, perm, rowlen, sptr):
+def sliced_offsets(A, perm, rowlen, sptr, vec: int = 1):
     """16-bit offsets of the sliced layout: per-position row base (first
     column) and col - base per slot; returns (rowbase, off, largest span)."""
     rp, ci, _ = _csr(A)
@@ -276,7 +276,7 @@ def sliced_offsets(A, perm, rowlen, sptr):
     rowlen = _np(rowlen, np.int32)
     sptr = _np(sptr, np.int64)
     span = _load().orc_sliced_offsets(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr),
-                                      _p(base), _p(off))
+                                      vec, _p(base), _p(off))
     return base[:32 * S], off[:tot], int(span)
 
 

@@ -389,9 +389,12 @@ int64_t orc_compress_u16(int64_t n_rows, const int32_t *rowptr, const int32_t *c
  *   rowlen[p]: length of the row at position p, -1 for a long row (> cap) or
  *   a position past the last row (positions run to 32 * S, S = ceil(N/32)).
  *   slice_len[s] = max(0, max rowlen over positions 32s .. 32s+31).
- *   slice_ptr[0] = 0, slice_ptr[s+1] = slice_ptr[s] + 32 * slice_len[s].
- * The element k of the row at position p = 32s + l lives at
- * slice_ptr[s] + 32 k + l.  Returns the number of long rows.                 */
+ *   slice_ptr[0] = 0, slice_ptr[s+1] = slice_ptr[s] + 32 * slice_len[s]
+ *   rounded up to a multiple of vec.
+ * With vec elements of a row side by side (vec = 1, 2 or 4), the element k
+ * of the row at position p = 32s + l lives at
+ * slice_ptr[s] + 32 vec floor(k / vec) + vec l + (k mod vec)
+ * (for vec = 1: slice_ptr[s] + 32 k + l).  Returns the number of long rows.  */
 static const int32_t *g_sort_rowptr;
 static int32_t g_sort_cap;
 
@@ -410,7 +413,8 @@ static int cmp_rows(const void *a, const void *b)
 }
 
 int64_t orc_sliced_layout(int64_t n_rows, const int32_t *rowptr, int32_t sigma, int32_t cap,
-                          int32_t *perm, int32_t *rowlen, int32_t *slice_len, int64_t *slice_ptr)
+                          int32_t vec, int32_t *perm, int32_t *rowlen, int32_t *slice_len,
+                          int64_t *slice_ptr)
 {
     int64_t n_slices = (n_rows + 31) / 32, n_long = 0;
     for (int64_t i = 0; i < n_rows; ++i) perm[i] = (int32_t)i;
@@ -435,26 +439,31 @@ int64_t orc_sliced_layout(int64_t n_rows, const int32_t *rowptr, int32_t sigma, 
         for (int64_t l = 0; l < 32; ++l)
             if (rowlen[32 * s + l] > m) m = rowlen[32 * s + l];
         slice_len[s] = m;
-        slice_ptr[s + 1] = slice_ptr[s] + 32 * (int64_t)m;
+        slice_ptr[s + 1] = slice_ptr[s] + 32 * (int64_t)((m + vec - 1) / vec * vec);
     }
     return n_long;
 }
 
 /* Column-major slice contents: col/val at slice_ptr[s] + 32 k + l for k <
  * rowlen[32s + l]; every other slot is 0.                                     */
+static int64_t slot_of(const int64_t *slice_ptr, int64_t p, int64_t k, int32_t vec)
+{
+    return slice_ptr[p / 32] + 32 * vec * (k / vec) + vec * (p % 32) + k % vec;
+}
+
 void orc_sliced_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
                      const double *val, const int32_t *perm, const int32_t *rowlen,
-                     const int64_t *slice_ptr, int32_t *col_out, double *val_out)
+                     const int64_t *slice_ptr, int32_t vec, int32_t *col_out, double *val_out)
 {
     int64_t n_slices = (n_rows + 31) / 32;
     int64_t tot = slice_ptr[n_slices];
     for (int64_t q = 0; q < tot; ++q) { col_out[q] = 0; val_out[q] = 0.0; }
     for (int64_t p = 0; p < n_rows; ++p) {
         if (rowlen[p] < 0) continue;
-        int64_t s = p / 32, l = p % 32, b = rowptr[perm[p]];
+        int64_t b = rowptr[perm[p]];
         for (int64_t k = 0; k < rowlen[p]; ++k) {
-            col_out[slice_ptr[s] + 32 * k + l] = colind[b + k];
-            val_out[slice_ptr[s] + 32 * k + l] = val[b + k];
+            col_out[slot_of(slice_ptr, p, k, vec)] = colind[b + k];
+            val_out[slot_of(slice_ptr, p, k, vec)] = val[b + k];
         }
     }
 }
@@ -467,7 +476,7 @@ void orc_sliced_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
  * when it is below 65536.                                                     */
 int64_t orc_sliced_offsets(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
                            const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
-                           int32_t *rowbase_pos, uint16_t *off_out)
+                           int32_t vec, int32_t *rowbase_pos, uint16_t *off_out)
 {
     int64_t n_slices = (n_rows + 31) / 32, span = 0;
     int64_t tot = slice_ptr[n_slices];
@@ -475,12 +484,12 @@ int64_t orc_sliced_offsets(int64_t n_rows, const int32_t *rowptr, const int32_t 
     for (int64_t p = 0; p < 32 * n_slices; ++p) {
         rowbase_pos[p] = 0;
         if (p >= n_rows || rowlen[p] <= 0) continue;
-        int64_t b = rowptr[perm[p]], len = rowlen[p], s = p / 32, l = p % 32;
+        int64_t b = rowptr[perm[p]], len = rowlen[p];
         int64_t first = colind[b];
         rowbase_pos[p] = (int32_t)first;
         if (colind[b + len - 1] - first > span) span = colind[b + len - 1] - first;
         for (int64_t k = 0; k < len; ++k)
-            off_out[slice_ptr[s] + 32 * k + l] = (uint16_t)(colind[b + k] - first);
+            off_out[slot_of(slice_ptr, p, k, vec)] = (uint16_t)(colind[b + k] - first);
     }
     return span;
 }

@@ -520,19 +520,27 @@ def test_sliced_layout_hand_example():
     assert [col[32 * k + 0] for k in range(3)] == ci[1:4].tolist()
     assert [col[32 * k + 4] for k in range(2)] == ci[9:11].tolist()
     assert col[32 * 1 + 1] == 0 and val[32 * 1 + 1] == 0.0  # padding of row 0
+    # four elements of a row side by side: the slice holds 32 x 4 slots;
+    # element k of position p at 128 (k // 4) + 4 p + k % 4
+    _, _, slen4, sptr4, _ = oracle.sliced_layout(A, sigma=4, cap=4, vec=4)
+    assert slen4.tolist() == [3] and sptr4.tolist() == [0, 128]
+    col4, _ = oracle.sliced_fill(A, perm, rowlen, sptr4, vec=4)
+    assert col4[0:3].tolist() == ci[1:4].tolist() and col4[3] == 0
+    assert col4[16:18].tolist() == ci[9:11].tolist()
     # sigma = 1: identity order
     perm1, rowlen1, slen1, _, _ = oracle.sliced_layout(A, sigma=1, cap=4)
     assert perm1.tolist() == [0, 1, 2, 3, 4] and rowlen1[:5].tolist() == [1, 3, 0, -1, 2]
     assert slen1.tolist() == [3]
 
 
+@pytest.mark.parametrize("vec", [1, 2, 4])
 @pytest.mark.parametrize("sigma,cap", [(1, 1000), (32, 1000), (256, 40), (64, 7)])
-def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap):
+def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap, vec):
     g = np.random.default_rng(sigma + cap)
     lengths = np.minimum(g.zipf(1.6, 1000), 60)
     lengths[g.integers(0, 1000, 30)] = 0
     A = _csr_from_lengths(lengths.tolist(), n_cols=200, seed=3)
-    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma=sigma, cap=cap)
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma=sigma, cap=cap, vec=vec)
     key = np.where(lengths > cap, 0, lengths)
     expect = np.arange(1000)
     if sigma > 1:
@@ -544,21 +552,24 @@ def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap):
     full[:1000] = np.where(lengths[perm] > cap, -1, lengths[perm])
     assert np.array_equal(rowlen, full)
     assert np.array_equal(slen, np.maximum(full.reshape(-1, 32).max(1), 0))
-    assert np.array_equal(sptr, np.concatenate([[0], np.cumsum(32 * slen)]))
+    padded = (slen + vec - 1) // vec * vec
+    assert np.array_equal(sptr, np.concatenate([[0], np.cumsum(32 * padded)]))
     # the slices hold exactly the short rows' elements
-    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr, vec=vec)
     rp, ci, va = A.rowptr.numpy(), A.colind.numpy(), A.val.numpy()
     for p in range(1000):
         r, s, l = perm[p], p // 32, p % 32
         if rowlen[p] < 0:
             continue
-        idx = sptr[s] + 32 * np.arange(rowlen[p]) + l
+        k = np.arange(rowlen[p])
+        idx = sptr[s] + 32 * vec * (k // vec) + vec * l + k % vec
         assert np.array_equal(col[idx], ci[rp[r]:rp[r + 1]])
         assert np.array_equal(val[idx], va[rp[r]:rp[r + 1]])
     assert np.count_nonzero(val) == np.count_nonzero(va[np.repeat(lengths <= cap, lengths)])
 
 
-def test_sliced_offsets_decode_to_the_columns():
+@pytest.mark.parametrize("vec", [1, 4])
+def test_sliced_offsets_decode_to_the_columns(vec):
     """base + offset gives back every column of every row in the slices,
     padding and rows outside the slices hold 0, and the span is the largest
     last - first column of a row in the slices."""
@@ -566,9 +577,9 @@ def test_sliced_offsets_decode_to_the_columns():
     lengths = np.minimum(g.zipf(1.7, 300), 40)
     lengths[:5] = [0, 1, 3, 41, 2]
     A = _csr_from_lengths(lengths.tolist(), n_cols=5000, seed=4)
-    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=64, cap=40)
-    col, _ = oracle.sliced_fill(A, perm, rowlen, sptr)
-    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=64, cap=40, vec=vec)
+    col, _ = oracle.sliced_fill(A, perm, rowlen, sptr, vec=vec)
+    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr, vec=vec)
     rp, ci = A.rowptr.numpy(), A.colind.numpy()
     spans = []
     for p in range(32 * len(slen)):
@@ -576,7 +587,8 @@ def test_sliced_offsets_decode_to_the_columns():
             assert base[p] == 0
             continue
         s, l = p // 32, p % 32
-        idx = sptr[s] + 32 * np.arange(rowlen[p]) + l
+        k = np.arange(rowlen[p])
+        idx = sptr[s] + 32 * vec * (k // vec) + vec * l + k % vec
         assert np.array_equal(base[p] + off[idx].astype(np.int64), col[idx])
         r = perm[p]
         assert base[p] == ci[rp[r]]
@@ -585,7 +597,8 @@ def test_sliced_offsets_decode_to_the_columns():
     real = np.zeros(len(off), bool)
     for p in range(A.n_rows):
         if rowlen[p] > 0:
-            real[sptr[p // 32] + 32 * np.arange(rowlen[p]) + p % 32] = True
+            k = np.arange(rowlen[p])
+            real[sptr[p // 32] + 32 * vec * (k // vec) + vec * (p % 32) + k % vec] = True
     assert np.all(off[~real] == 0)
 
 
