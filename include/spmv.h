@@ -228,7 +228,11 @@ typedef enum {
     SPMV_EXPORT_SLICE_ROWLEN = 7, /* SLICED: int32 [32 S] row length per position, -1 =
                                    long row (computed from CSR) or past the last row   */
     SPMV_EXPORT_SLICE_LEN = 8,  /* SLICED: int32 [S] slice length (longest row in it)   */
-    SPMV_EXPORT_SLICE_PTR = 9,  /* SLICED: int64 [S + 1] first element of each slice    */
+    SPMV_EXPORT_SLICE_PTR = 9,  /* SLICED: int64 [S + 1] first slot of each slice; with
+                                   FP64 values element k of position 32 s + l is at
+                                   slot ptr[s] + 32 k + l, with FP32/BF16 values at
+                                   ptr[s] + 128 (k / 4) + 4 l + k % 4 (slices padded
+                                   to a multiple of 4 elements per row)                */
     SPMV_EXPORT_SLICE_COL = 10, /* SLICED: int32 [slice_ptr[S]] columns, column-major
                                    (absent with 16-bit offsets)                        */
     SPMV_EXPORT_SLICE_VAL = 11, /* SLICED: [slice_ptr[S]] values in value_type          */

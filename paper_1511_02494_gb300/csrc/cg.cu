@@ -184,7 +184,7 @@ k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p
         if constexpr (sizeof(VT) == 8)
             v = dev::slice_value<4>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm, a.col, a.val, p, &row);
         else
-            v = dev::slice_value_lp<4, VT, OFF16, ACC32>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
+            v = dev::slice_value_lp<OFF16 ? 2 : 1, VT, OFF16, ACC32>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
                                                          a.col, a.off, a.rowbase,
                                                          static_cast<const VT*>(a.lowval), p, p32, &row);
         if (row >= 0) {

@@ -74,6 +74,7 @@ struct SlicedPlan {
     int n_seg = 0;
     // low-precision values (FP32 / BF16), optionally 16-bit column offsets
     int value_type = 0;
+    int vec = 1;                 // elements of a row side by side: 1 (FP64) or 4 (FP32/BF16)
     bool acc32 = false, off16 = false;
     void* lowval = nullptr;      // [tot] values in value_type
     uint16_t* off = nullptr;     // [tot] column - rowbase (off16)

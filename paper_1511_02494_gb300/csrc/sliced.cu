@@ -229,8 +229,9 @@ __global__ void k_sl_span(int64_t n_slices, const int* __restrict__ rp, const in
     atomicMax(span, ci[b + len - 1] - ci[b]);
 }
 
-// column-major low-precision contents; OFF16: offsets from the row's first
-// column (rowbase per position), else 32-bit columns
+// low-precision contents, four elements of a row side by side (element k
+// at slice_ptr[s] + 128 (k / 4) + 4 l + k % 4); OFF16: offsets from the
+// row's first column (rowbase per position), else 32-bit columns
 template <typename VT, bool OFF16>
 __global__ void k_sl_fill_lp(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
                              const double* __restrict__ v, const int* __restrict__ perm,
@@ -245,13 +246,14 @@ __global__ void k_sl_fill_lp(int64_t n_slices, const int* __restrict__ rp, const
     const int len = rowlen[p];
     if (len <= 0) return;
     const int64_t b = rp[perm ? perm[p] : (int)p];
-    const int64_t q0 = slice_ptr[s] + lane;
+    const int64_t q0 = slice_ptr[s] + 4 * lane;
     const int first = ci[b];
     if (OFF16) rowbase[p] = first;
     for (int k = 0; k < len; ++k) {
-        if (OFF16) off[q0 + (int64_t)k * 32] = (uint16_t)(ci[b + k] - first);
-        else col[q0 + (int64_t)k * 32] = ci[b + k];
-        val[q0 + (int64_t)k * 32] = round_to(v[b + k], (VT*)nullptr);
+        const int64_t q = q0 + (int64_t)(k >> 2) * 128 + (k & 3);
+        if (OFF16) off[q] = (uint16_t)(ci[b + k] - first);
+        else col[q] = ci[b + k];
+        val[q] = round_to(v[b + k], (VT*)nullptr);
     }
 }
 
@@ -273,7 +275,9 @@ k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restr
     const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
     if (s >= n_slices) return;
     int row;
-    const double v = slice_value_lp<U, VT, OFF16, ACC32>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr,
+    // two groups of four in flight with 16-bit offsets; one with 32-bit
+    // columns (gather-bound rows, where registers are worth more as warps)
+    const double v = slice_value_lp<OFF16 ? 2 : 1, VT, OFF16, ACC32>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr,
                                                          perm, col, off, rowbase, val, x, x32, &row);
     if (row >= 0) y[row] = v;
 }
@@ -364,9 +368,12 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         }
         SPMV_CUDA_TRY(cudaMemcpyAsync(&n_long, d.count, 4, cudaMemcpyDeviceToHost, s));
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < d.n_slices; ++i) sptr[i + 1] = sptr[i] + 32 * (int64_t)slen[i];
+        for (int64_t i = 0; i < d.n_slices; ++i)
+            sptr[i + 1] = sptr[i] + 32 * (int64_t)((slen[i] + d.vec - 1) / d.vec * d.vec);
         return SPMV_OK;
     };
+    // FP64 values: one element per slot row; FP32/BF16: four side by side
+    d.vec = P->c.value_type == SPMV_VAL_F64 ? 1 : 4;
     int sigma = P->c.block_nnz;
     if (sigma == 0) {
         // rows in order unless that pads the slices by more than a quarter

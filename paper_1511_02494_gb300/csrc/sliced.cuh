@@ -65,10 +65,27 @@ __device__ __forceinline__ void slice_rows(int64_t s, int lane, const int* __res
     if (row >= 0) y[row] = v;
 }
 
-// FP32 or BF16 values, 32-bit columns or 16-bit offsets from rowbase[p].
-// ACC32: x32 is the FP32 copy of x; fmaf chain, one widening per row.
-// Otherwise each value is widened to FP64 and summed with DFMAs.
-template <int U, typename VT, bool OFF16, bool ACC32>
+// FP32 or BF16 values, 32-bit columns or 16-bit offsets from rowbase[p],
+// with four elements of a row side by side: element k of the row at
+// position p = 32 s + l sits at slot slice_ptr[s] + 128 (k / 4) + 4 l + k % 4,
+// so one lane loads four offsets (8 bytes) and four values (8 or 16 bytes)
+// per instruction.  ACC32: x32 is the FP32 copy of x; fmaf chain in row
+// order, one widening per row.  Otherwise each value is widened to FP64 and
+// summed with DFMAs.  Padded slots are loaded with their group but never
+// multiplied.
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float* a) {
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+    a[0] = __uint_as_float(v.x << 16);
+    a[1] = __uint_as_float(v.x & 0xffff0000u);
+    a[2] = __uint_as_float(v.y << 16);
+    a[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+__device__ __forceinline__ void load4(const float* p, float* a) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
+
+template <int G, typename VT, bool OFF16, bool ACC32>
 __device__ __forceinline__ double slice_value_lp(int64_t s, int lane, const int* __restrict__ rowlen,
                                                  const int* __restrict__ slice_len,
                                                  const int64_t* __restrict__ slice_ptr,
@@ -83,35 +100,56 @@ __device__ __forceinline__ double slice_value_lp(int64_t s, int lane, const int*
     const int64_t p = s * 32 + lane;
     const int len = rowlen[p];
     const int L = slice_len[s];
-    const int64_t q0 = slice_ptr[s] + lane;
+    const int64_t q0 = slice_ptr[s] + 4 * lane;   // group g of the row at q0 + 128 g
     const int base = OFF16 ? rowbase[p] : 0;
-    const VT* __restrict__ vp = val + q0;
     float acc32 = 0.f;
     double acc64 = 0.0;
-    for (int k = 0; k < L; k += U) {
-        int c[U];
-        float a[U];
+    for (int k = 0; k < L; k += 4 * G) {
+        int c[G][4];
+        float a[G][4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = k + u < len;
-            if (OFF16) c[u] = ok ? base + (int)__ldcs(off + q0 + (k + u) * 32) : 0;
-            else c[u] = ok ? __ldcs(col + q0 + (k + u) * 32) : 0;
-            a[u] = ok ? ldval32(vp + (k + u) * 32) : 0.f;  // exact widening of FP32 / BF16
+        for (int g = 0; g < G; ++g) {
+            const int kg = k + 4 * g;
+            const int64_t q = q0 + (int64_t)(kg >> 2) * 128;
+            if (kg < len) {
+                if (OFF16) {
+                    const uint2 o = __ldcs(reinterpret_cast<const uint2*>(off + q));
+                    c[g][0] = base + (int)(o.x & 0xffffu);
+                    c[g][1] = base + (int)(o.x >> 16);
+                    c[g][2] = base + (int)(o.y & 0xffffu);
+                    c[g][3] = base + (int)(o.y >> 16);
+                } else {
+                    const int4 o = __ldcs(reinterpret_cast<const int4*>(col + q));
+                    c[g][0] = o.x; c[g][1] = o.y; c[g][2] = o.z; c[g][3] = o.w;
+                }
+                load4(val + q, a[g]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { c[g][u] = 0; a[g][u] = 0.f; }
+            }
         }
         if (ACC32) {
-            float xv[U];
+            float xv[G][4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? __ldg(x32 + c[u]) : 0.f;
+            for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (k + u < len) acc32 = fmaf(a[u], xv[u], acc32);
+                for (int u = 0; u < 4; ++u) xv[g][u] = k + 4 * g + u < len ? __ldg(x32 + c[g][u]) : 0.f;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + 4 * g + u < len) acc32 = fmaf(a[g][u], xv[g][u], acc32);
         } else {
-            double xv[U];
+            double xv[G][4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + c[u]) : 0.0;
+            for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (k + u < len) acc64 = fma((double)a[u], xv[u], acc64);
+                for (int u = 0; u < 4; ++u) xv[g][u] = k + 4 * g + u < len ? ldx(x + c[g][u]) : 0.0;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + 4 * g + u < len) acc64 = fma((double)a[g][u], xv[g][u], acc64);
         }
     }
     *row = len >= 0 ? (perm ? perm[p] : (int)p) : -1;

@@ -314,18 +314,20 @@ def test_sliced_low_precision_layout_bit_exact(vt, sigma, name, A):
     dA = sp.DeviceCSR.from_host(A)
     P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, value_type=vt))
     assert P.info().accumulate == sp.ACC_F32
-    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, 1024)
+    # low-precision slices keep four elements of a row side by side
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, 1024, vec=4)
     S, tot = (A.n_rows + 31) // 32, int(sptr[-1])
     if tot == 0:
         return
-    col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
+    assert np.array_equal(_export(P, sp.EXPORT_SLICE_PTR, S + 1, torch.int64), sptr)
+    col, val = oracle.sliced_fill(A, perm, rowlen, sptr, vec=4)
     if vt == sp.VAL_F32:
         got = _export(P, sp.EXPORT_SLICE_VAL, tot, torch.float32)
         assert np.array_equal(got, oracle.round_f32(val))
     else:
         got = _export(P, sp.EXPORT_SLICE_VAL, tot, torch.int16).view(np.uint16)
         assert np.array_equal(got, oracle.round_bf16(val))
-    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr)
+    base, off, span = oracle.sliced_offsets(A, perm, rowlen, sptr, vec=4)
     if span < 65536:
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_OFF16, tot, torch.int16).view(np.uint16), off)
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWBASE, 32 * S, torch.int32), base)
