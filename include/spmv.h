@@ -162,6 +162,11 @@ typedef struct {
  *   items_per_warp  : MERGE items per warp of the warp-level kernel used instead
  *                     when rowptr, colind or val is not 16-byte aligned
  *                     (32 k, k in {1, 2, 4, 6, 7, 8, 12, 16})
+ *   items_per_warp  : SLICED row-length cap, 1..65536 (0 = 1024): rows with
+ *                     more nonzeros are left out of the slices and computed
+ *                     from CSR in segments of 2048 nonzeros, one warp each.
+ *                     A lane's chain of FMAs is at most this long, so a low
+ *                     cap with a wide sort window suits power-law row lengths
  *   block_nnz       : DYNAMIC nonzeros per segment of a long row (power of two,
  *                     256..2^20; default 2048)
  *   block_nnz       : SLICED window of the length sort: 1 = rows in order, or a

@@ -311,8 +311,12 @@ spmv_status check_choice(const spmv_choice_t* c)
     if (c->variant == SPMV_V3_MERGE && c->block_nnz != 0 && c->block_nnz != 1024 &&
         c->block_nnz != 1536 && c->block_nnz != 2048)
         return fail(SPMV_ERR_INVALID_ARG, "MERGE tile items (block_nnz) must be 1024, 1536 or 2048");
-    if (c->items_per_warp != 0 && !merge_items_ok(c->items_per_warp))
+    if (c->variant == SPMV_V7_SLICED) {
+        if (c->items_per_warp < 0 || c->items_per_warp > kSlicedCapMax)
+            return fail(SPMV_ERR_INVALID_ARG, "SLICED row-length cap (items_per_warp) must be in 0..65536");
+    } else if (c->items_per_warp != 0 && !merge_items_ok(c->items_per_warp)) {
         return fail(SPMV_ERR_INVALID_ARG, "items_per_warp must be 32*k, k in {1,2,4,6,7,8,12,16}");
+    }
     if (c->value_type < SPMV_VAL_F64 || c->value_type > SPMV_VAL_BF16)
         return fail(SPMV_ERR_INVALID_ARG, "value_type out of range");
     const bool lowp_ok = c->variant == SPMV_V6_COMPRESSED || c->variant == SPMV_V7_SLICED;

@@ -28,6 +28,13 @@ namespace spmvlib {
 namespace {
 
 constexpr int kCT = 256;
+// The vector kernels give each thread kUnr elements kCT apart per pass of
+// the grid-stride loop and load all of them before any arithmetic, so a
+// thread keeps several independent loads of every vector in flight.
+constexpr int kUnr = 4;
+
+__device__ __forceinline__ int64_t first_index() { return (int64_t)blockIdx.x * kCT * kUnr + threadIdx.x; }
+__device__ __forceinline__ int64_t grid_step() { return (int64_t)gridDim.x * kCT * kUnr; }
 
 struct CgState {
     double rs, rs_new, pq, alpha, beta;
@@ -80,8 +87,17 @@ k_dot_pq(int64_t n, const double* __restrict__ p, const double* __restrict__ q,
 {
     __shared__ double red[kCT / 32];
     double v = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT)
-        v = fma(p[i], q[i], v);
+    for (int64_t i0 = first_index(); i0 < n; i0 += grid_step()) {
+        double pv[kUnr], qv[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            pv[u] = i < n ? p[i] : 0.0;
+            qv[u] = i < n ? q[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) v = fma(pv[u], qv[u], v);
+    }
     v = block_reduce(v, red);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
     if (!last_block(&st->ticket)) return;
@@ -106,13 +122,29 @@ k_update(int64_t n, double* __restrict__ x, const double* __restrict__ p, double
     __shared__ double red[kCT / 32];
     const double alpha = st->alpha;
     double v = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT) {
-        if (UPDATE_X) x[i] = fma(alpha, p[i], x[i]);
-        double ri;
-        if (RECOMPUTE) ri = b[i] - q[i];
-        else ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        v = fma(ri, ri, v);
+    for (int64_t i0 = first_index(); i0 < n; i0 += grid_step()) {
+        double xv[kUnr], pv[kUnr], rv[kUnr], qv[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            const bool ok = i < n;
+            if (UPDATE_X) {
+                xv[u] = ok ? x[i] : 0.0;
+                pv[u] = ok ? p[i] : 0.0;
+            }
+            rv[u] = ok ? (RECOMPUTE ? b[i] : r[i]) : 0.0;
+            qv[u] = ok ? q[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            if (i < n) {
+                if (UPDATE_X) x[i] = fma(alpha, pv[u], xv[u]);
+                const double ri = RECOMPUTE ? rv[u] - qv[u] : fma(-alpha, qv[u], rv[u]);
+                r[i] = ri;
+                v = fma(ri, ri, v);
+            }
+        }
     }
     v = block_reduce(v, red);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
@@ -138,8 +170,18 @@ __global__ void __launch_bounds__(kCT)
 k_axpy_x(int64_t n, double* __restrict__ x, const double* __restrict__ p, const CgState* st)
 {
     const double alpha = st->alpha;
-    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT)
-        x[i] = fma(alpha, p[i], x[i]);
+    for (int64_t i0 = first_index(); i0 < n; i0 += grid_step()) {
+        double xv[kUnr], pv[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            xv[u] = i < n ? x[i] : 0.0;
+            pv[u] = i < n ? p[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u)
+            if (i0 + u * kCT < n) x[i0 + u * kCT] = fma(alpha, pv[u], xv[u]);
+    }
 }
 
 // p = r + beta p  (INIT: p = r); with p32, also its FP32 copy for a
@@ -151,10 +193,23 @@ k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ r, cons
            float* __restrict__ p32)
 {
     const double beta = INIT ? 0.0 : st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kCT) {
-        const double v = INIT ? r[i] : fma(beta, p[i], r[i]);
-        p[i] = v;
-        if (p32) p32[i] = __double2float_rn(v);
+    for (int64_t i0 = first_index(); i0 < n; i0 += grid_step()) {
+        double pv[kUnr], rv[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            rv[u] = i < n ? r[i] : 0.0;
+            pv[u] = !INIT && i < n ? p[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+            const int64_t i = i0 + u * kCT;
+            if (i < n) {
+                const double v = INIT ? rv[u] : fma(beta, pv[u], rv[u]);
+                p[i] = v;
+                if (p32) p32[i] = __double2float_rn(v);
+            }
+        }
     }
 }
 
@@ -162,6 +217,13 @@ k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ r, cons
 // lane computes its row's q_i (dev::slice_value / slice_value_lp, the same
 // arithmetic as the SLICED kernels) and adds p_i q_i to its block's partial;
 // the last block sums the partials in block order and sets pq and alpha.
+// Resident blocks per SM of the fused kernel: FP64 values fit 8 (32
+// registers, two elements in flight per lane); the low-precision bodies need
+// 40 registers, so 6.
+template <typename VT>
+constexpr int dot_blocks() { return sizeof(VT) == 8 ? 8 : 6; }
+constexpr int kDotU = 2;
+
 struct SlArgs {
     int64_t n_slices;
     const int* rowlen; const int* slice_len; const int64_t* slice_ptr; const int* perm;
@@ -169,7 +231,7 @@ struct SlArgs {
 };
 
 template <typename VT, bool OFF16, bool ACC32>
-__global__ void __launch_bounds__(kCT, 6)
+__global__ void __launch_bounds__(kCT, dot_blocks<VT>())
 k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p32,
              double* __restrict__ q, double* __restrict__ part, CgState* st)
 {
@@ -182,7 +244,7 @@ k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p
         int row;
         double v;
         if constexpr (sizeof(VT) == 8)
-            v = dev::slice_value<4>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm, a.col, a.val, p, &row);
+            v = dev::slice_value<kDotU>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm, a.col, a.val, p, &row);
         else
             v = dev::slice_value_lp<OFF16 ? 2 : 1, VT, OFF16, ACC32>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
                                                          a.col, a.off, a.rowbase,
@@ -211,7 +273,8 @@ bool fusable(const spmv_prepared* P)
 unsigned sliced_dot_grid(const spmv_prepared* P)
 {
     const int64_t need = (32 * P->sl.n_slices + kCT - 1) / kCT;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)P->sm_count * 6));
+    const int per_sm = P->sl.value_type == SPMV_VAL_F64 ? dot_blocks<double>() : dot_blocks<float>();
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)P->sm_count * per_sm));
 }
 
 cudaError_t launch_sliced_dot(const spmv_prepared* P, const double* p, double* q, double* part,
@@ -298,7 +361,7 @@ extern "C" spmv_status spmv_cg(const spmv_prepared_t* A_inner, const spmv_prepar
     spmv_status st = current_device(&dev);
     if (st != SPMV_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int64_t g = (n + kCT - 1) / kCT;
+    int64_t g = (n + kCT * kUnr - 1) / (kCT * kUnr);
     if (g > (int64_t)dev.sm_count * 4) g = (int64_t)dev.sm_count * 4;
     const unsigned grid = (unsigned)g;
     CgBufs w;

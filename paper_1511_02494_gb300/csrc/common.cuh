@@ -54,14 +54,16 @@ struct DynPlan {
     double* partial = nullptr;  // one partial sum per segment
 };
 
-// SLICED (V7): rows longer than kSlicedCap are computed from CSR in segments
-// of kSlicedSeg nonzeros, one warp each
+// SLICED (V7): rows longer than the plan's cap (kSlicedCap unless chosen)
+// are computed from CSR in segments of kSlicedSeg nonzeros, one warp each
 constexpr int kSlicedCap = 1024;
+constexpr int kSlicedCapMax = 1 << 16;
 constexpr int kSlicedSeg = 2048;
 
 struct SlicedPlan {
     int64_t n_slices = 0, tot = 0;
     int sigma = 1, n_long = 0;
+    int cap = 0;                 // longest row kept in the slices; longer rows go to segments
     int* rowlen = nullptr;       // [32 n_slices] row length per position, -1: long or absent
     int* slice_len = nullptr;    // [n_slices]
     int64_t* slice_ptr = nullptr;  // [n_slices + 1] element offset of each slice

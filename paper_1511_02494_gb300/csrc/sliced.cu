@@ -14,7 +14,7 @@
 //
 // Optionally (sigma > 1) rows are sorted by length, longest first, inside
 // windows of sigma rows, so that a slice holds rows of similar length; y is
-// then written through the permutation.  Rows longer than kSlicedCap are not
+// then written through the permutation.  Rows longer than a cap are not
 // put in slices (their slot has length -1); they are split into segments of
 // kSlicedSeg nonzeros computed by one warp each from the CSR arrays, and a
 // fix-up adds each such row's segment sums in order.  The layout is that of the oracle's orc_sliced_layout
@@ -331,7 +331,8 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
 {
     const spmv_csr_t& A = P->A;
     SlicedPlan& d = P->sl;
-    const int cap = kSlicedCap;
+    const int cap = P->c.items_per_warp > 0 ? P->c.items_per_warp : kSlicedCap;
+    d.cap = cap;
     d.n_slices = (A.n_rows + 31) / 32;
     const int64_t n_pos = 32 * d.n_slices;
     spmv_status st;
@@ -384,6 +385,7 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         return st;
     }
     P->c.block_nnz = sigma;
+    P->c.items_per_warp = cap;
     d.sigma = sigma;
     d.n_long = (int)n_long;
     d.tot = sptr[d.n_slices];

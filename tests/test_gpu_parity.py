@@ -70,7 +70,8 @@ CHOICES = [
     ("compressed", {}), ("compressed", {"threads_per_row": 1}),
     ("compressed", {"threads_per_row": 32}),
     ("sliced", {}), ("sliced", {"block_nnz": 1}), ("sliced", {"block_nnz": 32}),
-    ("sliced", {"block_nnz": 4096}),
+    ("sliced", {"block_nnz": 4096}), ("sliced", {"block_nnz": 4096, "items_per_warp": 32}),
+    ("sliced", {"items_per_warp": 1}),
 ]
 
 
@@ -277,16 +278,18 @@ def _export(P, which, n, dtype):
     return t.numpy()
 
 
-@pytest.mark.parametrize("sigma", [1, 32, 256])
+@pytest.mark.parametrize("sigma,cap", [(1, 1024), (32, 1024), (256, 1024), (1, 8), (4096, 32)])
 @pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
-def test_sliced_layout_bit_exact(sigma, name, A):
-    """The SLICED prepared arrays equal the oracle's sliced layout."""
+def test_sliced_layout_bit_exact(sigma, cap, name, A):
+    """The SLICED prepared arrays equal the oracle's sliced layout, for the
+    default row-length cap (1024) and chosen ones."""
     dA = sp.DeviceCSR.from_host(A)
-    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma))
-    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, 1024)
+    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma,
+                                           items_per_warp=0 if cap == 1024 else cap))
+    perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, cap)
     S = (A.n_rows + 31) // 32
     info = P.info()
-    assert info.n_blocks == S and info.block_nnz == sigma
+    assert info.n_blocks == S and info.block_nnz == sigma and info.items_per_warp == cap
     assert info.launches == (0 if A.n_rows == 0 else (3 if n_long else 1))
     if S == 0:
         return
@@ -337,24 +340,27 @@ def test_sliced_low_precision_layout_bit_exact(vt, sigma, name, A):
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_COL, tot, torch.int32), col)
 
 
+@pytest.mark.parametrize("cap", [1024, 16])
 @pytest.mark.parametrize("vt,vkind", [(sp.VAL_F32, 1), (sp.VAL_BF16, 2)])
 @pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
-def test_sliced_low_precision_parity(vt, vkind, name, A):
+def test_sliced_low_precision_parity(vt, vkind, cap, name, A):
     """FP32 accumulation: rows in slices are summed in row order with fmaf,
     bit for bit the oracle's FP32 form; long rows (segments + shuffle tree)
     within the FP32 bound.  FP64 accumulation: within the FP64 bound."""
     lowval = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
     x = synth.uniform_vector(A.n_cols, 5)
-    y32, _ = _run(A, sp.make_choice("sliced", value_type=vt), x)
+    ipw = 0 if cap == 1024 else cap
+    y32, _ = _run(A, sp.make_choice("sliced", value_type=vt, items_per_warp=ipw), x)
     ref32 = oracle.spmv_lowp32(A, x, vkind, lowval)
     lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
-    short = lens <= 1024
+    short = lens <= cap
     got = y32.cpu().numpy()
     assert np.array_equal(got[short], ref32[short])
     if (~short).any():
         bound = _lowp32_bound(A, x, lowval, vkind)
         assert np.all(np.abs(got - ref32)[~short] <= bound[~short])
-    y64, _ = _run(A, sp.make_choice("sliced", value_type=vt, accumulate=sp.ACC_F64), x)
+    y64, _ = _run(A, sp.make_choice("sliced", value_type=vt, accumulate=sp.ACC_F64,
+                                    items_per_warp=ipw), x)
     ref64 = oracle.spmv_lowp(A, x, vkind, lowval)
     _, scale = oracle.spmv_ref(A, x)
     assert np.all(np.abs(y64.cpu().numpy() - ref64) <= RTOL * scale * 1.01)
@@ -373,6 +379,15 @@ def test_sliced_auto_window_and_long_rows():
     for bad in (2, 16, 8192):
         with pytest.raises(sp.SpmvError):
             sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced", block_nnz=bad))
+    for bad in (-1, 65537):
+        with pytest.raises(sp.SpmvError):
+            sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced", items_per_warp=bad))
+    # a cap of 32 sends every Zipf row above 32 nonzeros to the segments
+    P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced", block_nnz=4096,
+                                                                   items_per_warp=32))
+    assert P.info().items_per_warp == 32 and P.info().launches == 3
+    y, x = _run(Z, sp.make_choice("sliced", block_nnz=4096, items_per_warp=32))
+    _assert_close(y, Z, x)
 
 
 @pytest.mark.parametrize("name,A", MATS[:6], ids=[m[0] for m in MATS[:6]])
