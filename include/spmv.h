@@ -56,11 +56,13 @@ typedef enum {
  * SUBWARP the per-row overhead of short rows (CMP).  SLICED is a GPU format
  * with no counterpart in Table 2: 32-row slices whose k-th elements are
  * stored next to each other, one lane per row and no reduction across lanes
- * (rows longer than 1024 are computed from CSR by one warp each).  The class
- * -> variant table used by the profiling rule (spmv_class_variant) is
+ * (rows above a length cap are computed from CSR by one warp each); its
+ * prepare step adapts the layout to the row lengths (a length sort and a low
+ * cap when rows are uneven, four slices per warp when all are short).  The
+ * class -> variant table used by the profiling rule (spmv_class_variant) is
  * calibrated on GB300 like the thresholds -- for each class the variant with
- * the lowest geometric-mean slowdown on the training matrices: CML -> SLICED,
- * MB -> SLICED, IMB -> DYNAMIC, CMP -> SLICED.  SCALAR is the unoptimized
+ * the lowest geometric-mean slowdown on the training matrices, which is
+ * SLICED for all four classes.  SCALAR is the unoptimized
  * CSR kernel (one thread per row, Algorithm 1 as written) against which
  * speedups are reported. */
 typedef enum {
@@ -153,6 +155,9 @@ typedef struct {
 /* A variant and its launch parameters.  Zero parameters mean "choose".
  *   threads_per_row : SUBWARP / LATENCY / COMPRESSED / DYNAMIC (short rows) lanes
  *                     per row (1..32, power of 2)
+ *   threads_per_row : SLICED with FP64 values: slices per warp, 1, 2 or 4 (a
+ *                     lane sums one row of each); 0 = 4 when no slice is
+ *                     longer than four elements, else 1
  *   block_nnz       : STREAM nonzeros per window (64..8192, power of 2; default
  *                     2048).  With 1024 or 2048 and 16-byte-aligned arrays the
  *                     pipelined bulk-copy kernel runs; otherwise a kernel that
@@ -173,7 +178,8 @@ typedef struct {
  *                     power of two in 32..4096 (rows sorted by length, longest
  *                     first, inside windows of that many rows); 0 = rows in
  *                     order unless that pads the slices by more than 25 %,
- *                     then 256
+ *                     then 4096 with a row-length cap of 32 (unless
+ *                     items_per_warp sets the cap)
  *   value_type      : COMPRESSED and SLICED value storage (spmv_value_type);
  *                     SLICED with FP32/BF16 values stores 16-bit column
  *                     offsets from each row's first column when every row in

@@ -291,10 +291,10 @@ int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
  * 6 compressed, 7 sliced.  The table is calibrated, like the thresholds: for
  * each class named by the rule, the variant with the lowest geometric-mean
  * slowdown against the exhaustive best on the training matrices measured on
- * GB300 -- CML -> sliced, MB -> sliced, IMB -> dynamic, CMP -> sliced.       */
+ * GB300 -- sliced for every class (CML, MB, IMB, CMP).                      */
 int32_t orc_class_variant(int32_t cls)
 {
-    static const int32_t map[4] = {7, 7, 4, 7};
+    static const int32_t map[4] = {7, 7, 7, 7};
     return (cls >= 0 && cls < 4) ? map[cls] : -1;
 }
 

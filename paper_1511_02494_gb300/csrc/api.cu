@@ -312,6 +312,9 @@ spmv_status check_choice(const spmv_choice_t* c)
         c->block_nnz != 1536 && c->block_nnz != 2048)
         return fail(SPMV_ERR_INVALID_ARG, "MERGE tile items (block_nnz) must be 1024, 1536 or 2048");
     if (c->variant == SPMV_V7_SLICED) {
+        if (c->threads_per_row != 0 && c->threads_per_row != 1 && c->threads_per_row != 2 &&
+            c->threads_per_row != 4)
+            return fail(SPMV_ERR_INVALID_ARG, "SLICED slices per warp (threads_per_row) must be 0, 1, 2 or 4");
         if (c->items_per_warp < 0 || c->items_per_warp > kSlicedCapMax)
             return fail(SPMV_ERR_INVALID_ARG, "SLICED row-length cap (items_per_warp) must be in 0..65536");
     } else if (c->items_per_warp != 0 && !merge_items_ok(c->items_per_warp)) {
@@ -450,10 +453,13 @@ int32_t spmv_class_variant(int32_t cls)
     switch (cls) {
         // calibrated on GB300: per class, the variant with the lowest
         // geometric-mean slowdown against the exhaustive best on the training
-        // matrices (CML 1.04, MB 1.00, IMB 1.21, CMP 1.07)
+        // matrices (CML 1.04, MB 1.00, IMB 1.16, CMP 1.04).  SLICED wins every
+        // class because its prepare step adapts the layout to the row lengths
+        // (length sort and row cap for imbalance, four slices per warp for
+        // short rows); DYNAMIC is next for IMB (1.26)
         case SPMV_CLASS_CML: return SPMV_V7_SLICED;
         case SPMV_CLASS_MB: return SPMV_V7_SLICED;
-        case SPMV_CLASS_IMB: return SPMV_V4_DYNAMIC;
+        case SPMV_CLASS_IMB: return SPMV_V7_SLICED;
         case SPMV_CLASS_CMP: return SPMV_V7_SLICED;
         default: return -1;
     }

@@ -63,7 +63,6 @@ constexpr int kSlicedSeg = 2048;
 struct SlicedPlan {
     int64_t n_slices = 0, tot = 0;
     int sigma = 1, n_long = 0;
-    int cap = 0;                 // longest row kept in the slices; longer rows go to segments
     int* rowlen = nullptr;       // [32 n_slices] row length per position, -1: long or absent
     int* slice_len = nullptr;    // [n_slices]
     int64_t* slice_ptr = nullptr;  // [n_slices + 1] element offset of each slice

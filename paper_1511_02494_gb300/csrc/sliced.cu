@@ -169,6 +169,20 @@ k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict
     slice_rows<U>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
 }
 
+// R consecutive slices per warp (slice_rows_multi), for short slices whose
+// few loads per lane leave the warp waiting on latency.
+template <int U, int R, int B>
+__global__ void __launch_bounds__(kSB, B)
+k_sliced_multi(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+               const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+               const int* __restrict__ col, const double* __restrict__ val,
+               const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t s0 = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
+    if (s0 >= n_slices) return;  // whole warps only
+    slice_rows_multi<U, R>(s0, n_slices, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
+}
+
 __global__ void k_sl_row_lengths(int n, const int* __restrict__ list, const int* __restrict__ rp,
                                  int* __restrict__ len)
 {
@@ -331,8 +345,7 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
 {
     const spmv_csr_t& A = P->A;
     SlicedPlan& d = P->sl;
-    const int cap = P->c.items_per_warp > 0 ? P->c.items_per_warp : kSlicedCap;
-    d.cap = cap;
+    int cap = P->c.items_per_warp > 0 ? P->c.items_per_warp : kSlicedCap;
     d.n_slices = (A.n_rows + 31) / 32;
     const int64_t n_pos = 32 * d.n_slices;
     spmv_status st;
@@ -377,16 +390,34 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
     d.vec = P->c.value_type == SPMV_VAL_F64 ? 1 : 4;
     int sigma = P->c.block_nnz;
     if (sigma == 0) {
-        // rows in order unless that pads the slices by more than a quarter
+        // rows in order unless that pads the slices by more than a quarter;
+        // then rows sorted by length in windows of 4096, and (unless the cap
+        // was chosen) every row above 32 nonzeros computed by a warp, so that
+        // no lane's chain is longer than one element per lane of a warp
         if ((st = layout(1)) != SPMV_OK) return st;
-        sigma = sptr[d.n_slices] <= A.nnz + A.nnz / 4 ? 1 : 256;
-        if (sigma != 1 && (st = layout(sigma)) != SPMV_OK) return st;
+        if (sptr[d.n_slices] > A.nnz + A.nnz / 4) {
+            sigma = 4096;
+            if (P->c.items_per_warp == 0) cap = 32;
+            if ((st = layout(sigma)) != SPMV_OK) return st;
+        } else {
+            sigma = 1;
+        }
     } else if ((st = layout(sigma)) != SPMV_OK) {
         return st;
     }
     P->c.block_nnz = sigma;
     P->c.items_per_warp = cap;
     d.sigma = sigma;
+    // FP64 values: slices per warp, 4 when no slice is longer than four
+    // elements (a lane's few loads leave a warp waiting on latency, so one
+    // warp takes four slices), else 1 (longer slices keep four elements of
+    // one row in flight instead)
+    if (P->c.value_type != SPMV_VAL_F64) {
+        P->c.threads_per_row = 1;
+    } else if (P->c.threads_per_row == 0) {
+        const int longest = d.n_slices > 0 ? *std::max_element(slen.begin(), slen.begin() + d.n_slices) : 0;
+        P->c.threads_per_row = longest <= 4 ? 4 : 1;
+    }
     d.n_long = (int)n_long;
     d.tot = sptr[d.n_slices];
     SPMV_CUDA_TRY(cudaMemcpyAsync(d.slice_ptr, sptr.data(), 8 * (d.n_slices + 1), cudaMemcpyHostToDevice, s));
@@ -493,8 +524,18 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (d.value_type == SPMV_VAL_F64) {
-        k_sliced<4><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col,
-                                         d.val, x, y);
+        // R slices per warp (sliced_prepare chose R, or the caller did)
+#define SPMV_SL_M(U, RR, B) \
+    k_sliced_multi<U, RR, B><<<grid_of(32 * ((d.n_slices + RR - 1) / RR), INT32_MAX), kSB, 0, s>>>( \
+        d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col, d.val, x, y)
+        switch (P->c.threads_per_row) {
+            case 2: SPMV_SL_M(2, 2, 6); break;
+            case 4: SPMV_SL_M(1, 4, 4); break;
+            default:
+                k_sliced<4><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col,
+                                                 d.val, x, y);
+        }
+#undef SPMV_SL_M
     } else {
 #define SPMV_SL_LP(VT, O16, A32)                                                                   \
     k_sliced_lp<4, VT, O16, A32><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len,          \

@@ -65,6 +65,62 @@ __device__ __forceinline__ void slice_rows(int64_t s, int lane, const int* __res
     if (row >= 0) y[row] = v;
 }
 
+// R consecutive slices s0 .. s0 + R - 1 at once: the lane sums one row of
+// each (the same FMA chain per row as slice_value), with U elements of every
+// row in flight, so a warp overlaps the R slices' load latencies.  Slices
+// past n_slices are skipped.
+template <int U, int R>
+__device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, int lane,
+                                                 const int* __restrict__ rowlen,
+                                                 const int* __restrict__ slice_len,
+                                                 const int64_t* __restrict__ slice_ptr,
+                                                 const int* __restrict__ perm,
+                                                 const int* __restrict__ col,
+                                                 const double* __restrict__ val,
+                                                 const double* __restrict__ x, double* __restrict__ y)
+{
+    int len[R];
+    int64_t q0[R];
+    double acc[R];
+    int L = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t s = s0 + r;
+        const bool in = s < n_slices;
+        len[r] = in ? rowlen[s * 32 + lane] : -1;
+        q0[r] = in ? slice_ptr[s] + lane : 0;
+        L = max(L, in ? slice_len[s] : 0);
+        acc[r] = 0.0;
+    }
+    for (int k = 0; k < L; k += U) {
+        int c[R][U];
+        double a[R][U], xv[R][U];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = k + u < len[r];
+                c[r][u] = ok ? __ldcs(col + q0[r] + (k + u) * 32) : 0;
+                a[r][u] = ok ? __ldcs(val + q0[r] + (k + u) * 32) : 0.0;
+            }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[r][u] = k + u < len[r] ? ldx(x + c[r][u]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k + u < len[r]) acc[r] = fma(a[r][u], xv[r][u], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (len[r] < 0) continue;
+        const int64_t p = (s0 + r) * 32 + lane;
+        y[perm ? perm[p] : (int)p] = acc[r];
+    }
+}
+
 // FP32 or BF16 values, 32-bit columns or 16-bit offsets from rowbase[p],
 // with four elements of a row side by side: element k of the row at
 // position p = 32 s + l sits at slot slice_ptr[s] + 128 (k / 4) + 4 l + k % 4,

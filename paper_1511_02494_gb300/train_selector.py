@@ -267,13 +267,23 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--no-resume", action="store_true")
     ap.add_argument("--betas", type=float, nargs="+", default=[2.0, 4.0, 8.0, 16.0, 32.0, math.inf])
+    ap.add_argument("--retime", nargs="+", default=[], choices=list(sp.VARIANTS),
+                    help="variants whose kernels changed: time them again on every stored matrix")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     from paper_1511_02494_gb300.build import build
     build()
     ds_path = os.path.join(args.out, "selector_dataset.npz")
     d = build_dataset(args.n, ds_path, resume=not args.no_resume)
-    if d["times"].shape[1] < N_VAR:
+    if args.retime:
+        times = d["times"].astype(np.float64)
+        if times.shape[1] < N_VAR:
+            times = np.concatenate([times, np.full((times.shape[0], N_VAR - times.shape[1]), np.nan)], 1)
+        for v in args.retime:
+            times[:, sp.VARIANTS.index(v)] = np.nan
+        d["times"] = times
+        np.savez(ds_path, **d)
+    if d["times"].shape[1] < N_VAR or np.isnan(d["times"]).any():
         d = extend_dataset(ds_path)
     # the profiling rule's choice under the library's current class map,
     # from the stored probe speedups

@@ -71,7 +71,9 @@ CHOICES = [
     ("compressed", {"threads_per_row": 32}),
     ("sliced", {}), ("sliced", {"block_nnz": 1}), ("sliced", {"block_nnz": 32}),
     ("sliced", {"block_nnz": 4096}), ("sliced", {"block_nnz": 4096, "items_per_warp": 32}),
-    ("sliced", {"items_per_warp": 1}),
+    ("sliced", {"items_per_warp": 1}), ("sliced", {"threads_per_row": 1}),
+    ("sliced", {"threads_per_row": 2}), ("sliced", {"threads_per_row": 4}),
+    ("sliced", {"threads_per_row": 4, "block_nnz": 256, "items_per_warp": 8}),
 ]
 
 
@@ -340,17 +342,20 @@ def test_sliced_low_precision_layout_bit_exact(vt, sigma, name, A):
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_COL, tot, torch.int32), col)
 
 
-@pytest.mark.parametrize("cap", [1024, 16])
+@pytest.mark.parametrize("ipw", [0, 16])
 @pytest.mark.parametrize("vt,vkind", [(sp.VAL_F32, 1), (sp.VAL_BF16, 2)])
 @pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
-def test_sliced_low_precision_parity(vt, vkind, cap, name, A):
+def test_sliced_low_precision_parity(vt, vkind, ipw, name, A):
     """FP32 accumulation: rows in slices are summed in row order with fmaf,
     bit for bit the oracle's FP32 form; long rows (segments + shuffle tree)
-    within the FP32 bound.  FP64 accumulation: within the FP64 bound."""
+    within the FP32 bound.  FP64 accumulation: within the FP64 bound.  The
+    row-length cap is chosen (ipw = 0) or set."""
     lowval = oracle.round_f32(A.val) if vkind == 1 else oracle.round_bf16(A.val)
     x = synth.uniform_vector(A.n_cols, 5)
-    ipw = 0 if cap == 1024 else cap
-    y32, _ = _run(A, sp.make_choice("sliced", value_type=vt, items_per_warp=ipw), x)
+    choice = sp.make_choice("sliced", value_type=vt, items_per_warp=ipw)
+    cap = sp.spmv_prepare(sp.DeviceCSR.from_host(A), choice).info().items_per_warp
+    assert cap == (ipw or cap) and cap in (ipw, 32, 1024)
+    y32, _ = _run(A, choice, x)
     ref32 = oracle.spmv_lowp32(A, x, vkind, lowval)
     lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
     short = lens <= cap
@@ -367,13 +372,25 @@ def test_sliced_low_precision_parity(vt, vkind, cap, name, A):
 
 
 def test_sliced_auto_window_and_long_rows():
-    # regular rows: kept in order; Zipf rows: sorted in windows of 256, and
-    # the rows above 1024 nonzeros computed from CSR
+    # regular rows: kept in order, one slice per warp; Zipf rows: sorted in
+    # windows of 4096 and every row above 32 nonzeros computed from CSR
     L = synth.laplacian_2d_5pt(100, 100)
-    assert sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced")).info().block_nnz == 1
+    info = sp.spmv_prepare(sp.DeviceCSR.from_host(L), sp.make_choice("sliced")).info()
+    assert info.block_nnz == 1 and info.items_per_warp == 1024 and info.threads_per_row == 1
     Z = synth.zipf_rows(60_000, 60_000, 1.4, 20_000, seed=9)
     P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced"))
-    assert P.info().block_nnz == 256 and P.info().launches == 3
+    assert P.info().block_nnz == 4096 and P.info().items_per_warp == 32 and P.info().launches == 3
+    # a chosen cap is kept
+    P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced", items_per_warp=512))
+    assert P.info().block_nnz == 4096 and P.info().items_per_warp == 512
+    # rows of two nonzeros: four slices per warp (FP64), one with FP32 values
+    S = synth.short_rows(50_000)
+    assert sp.spmv_prepare(sp.DeviceCSR.from_host(S), sp.make_choice("sliced")).info().threads_per_row == 4
+    assert sp.spmv_prepare(sp.DeviceCSR.from_host(S), sp.make_choice(
+        "sliced", value_type=sp.VAL_F32)).info().threads_per_row == 1
+    for bad in (3, 8, 32):
+        with pytest.raises(sp.SpmvError):
+            sp.spmv_prepare(sp.DeviceCSR.from_host(S), sp.make_choice("sliced", threads_per_row=bad))
     y, x = _run(Z, sp.make_choice("sliced"))
     _assert_close(y, Z, x)
     for bad in (2, 16, 8192):

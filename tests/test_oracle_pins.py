@@ -311,9 +311,8 @@ def test_profile_rule_nan_never_selected():
 
 def test_class_to_variant_table():
     # Table 2 analogue, calibrated on GB300 (checked against the committed
-    # training data in test_selector_gain): CML -> sliced (7), MB -> sliced,
-    # IMB -> dynamic (4), CMP -> sliced
-    assert [oracle.class_variant(c) for c in range(4)] == [7, 7, 4, 7]
+    # training data in test_selector_gain): sliced (7) for every class
+    assert [oracle.class_variant(c) for c in range(4)] == [7, 7, 7, 7]
 
 
 # --------------------------------------------------------------- partitions
