@@ -141,8 +141,9 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
-        case SPMV_V7_SLICED:  // + x to FP32, + long-row segments and fix-up
-            return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0) + (P->sl.n_long > 0 ? 2 : 0);
+        case SPMV_V7_SLICED:  // + x to FP32, + long-row segments, + fix-up of rows with several
+            return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0) + (P->sl.n_long > 0 ? 1 : 0) +
+                   (P->sl.n_fix > 0 ? 1 : 0);
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
         default: return 1;
     }
@@ -154,12 +155,13 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
     const int64_t vec = 8 * A.n_cols + 8 * A.n_rows + 4 * (A.n_rows + 1);
     if (P->c.variant == SPMV_V7_SLICED) {
         // elements once, a row length per position, slice length and start,
-        // the permutation when rows are sorted, the long rows' CSR bounds
+        // the permutation when rows are sorted, the long rows' list and
+        // segment offsets, per segment its bounds and row and a partial
         const SlicedPlan& d = P->sl;
         const int vb = d.value_type == SPMV_VAL_F64 ? 8 : d.value_type == SPMV_VAL_F32 ? 4 : 2;
         const int cb = d.off16 ? 2 : 4;
         return (int64_t)(vb + cb) * A.nnz + 128 * d.n_slices * (d.off16 ? 2 : 1) + 12 * d.n_slices +
-               (d.sigma > 1 ? 4 * A.n_rows : 0) + 12 * (int64_t)d.n_long + 16 * (int64_t)d.n_seg +
+               (d.sigma > 1 ? 4 * A.n_rows : 0) + 12 * (int64_t)d.n_long + 36 * (int64_t)d.n_seg +
                8 * A.n_cols + (d.acc32 ? 8 * A.n_cols : 0) + 8 * A.n_rows;
     }
     if (P->c.variant != SPMV_V6_COMPRESSED) return 12 * A.nnz + vec;

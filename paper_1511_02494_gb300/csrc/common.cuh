@@ -72,6 +72,10 @@ struct SlicedPlan {
     int* long_rows = nullptr;    // [n_long], ascending
     int* seg_off = nullptr;      // [n_long + 1] first segment of each long row
     double* partial = nullptr;   // [n_seg] segment sums
+    int64_t* seg_be = nullptr;   // [2 n_seg] CSR begin and end of each segment
+    int* seg_row = nullptr;      // [n_seg] row of a segment that is its row's only one, else -1
+    int* fix = nullptr;          // [n_fix] long rows (list indices) with several segments
+    int n_fix = 0;
     int n_seg = 0;
     // low-precision values (FP32 / BF16), optionally 16-bit column offsets
     int value_type = 0;

@@ -190,36 +190,59 @@ __global__ void k_sl_row_lengths(int n, const int* __restrict__ list, const int*
     if (q < n) len[q] = rp[list[q] + 1] - rp[list[q]];
 }
 
-// Long rows are split into segments of kSlicedSeg nonzeros; one warp per
-// segment writes the segment's partial sum, and k_sliced_fixup adds each long
-// row's partials in segment order (deterministic).
+// Long rows are split into segments of kSlicedSeg nonzeros; seg_be holds
+// each segment's CSR begin and end, seg_row the row of a segment that is its
+// row's only one (that segment writes y itself) and -1 otherwise.
+__global__ void k_sl_seg_table(int n_long, const int* __restrict__ list, const int* __restrict__ seg_off,
+                               const int* __restrict__ rp, int64_t* __restrict__ seg_be,
+                               int* __restrict__ seg_row)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_long) return;
+    const int r = list[q];
+    const int64_t b0 = rp[r], e0 = rp[r + 1];
+    const bool single = seg_off[q + 1] - seg_off[q] == 1;
+    for (int j = seg_off[q]; j < seg_off[q + 1]; ++j) {
+        const int64_t b = b0 + (int64_t)(j - seg_off[q]) * kSlicedSeg;
+        seg_be[2 * (int64_t)j] = b;
+        seg_be[2 * (int64_t)j + 1] = min(e0, b + kSlicedSeg);
+        seg_row[j] = single ? r : -1;
+    }
+}
+
+__device__ __forceinline__ longlong2 segment_bounds(const int64_t* seg_be, int w)
+{
+    return __ldg(reinterpret_cast<const longlong2*>(seg_be) + w);
+}
+
+// One warp per segment writes the segment's sum: to y when it is its row's
+// only segment, else to partial, and k_sliced_fixup adds the partials of
+// each row with several segments in segment order (deterministic).
 __global__ void __launch_bounds__(kSB)
-k_sliced_segments(int n_seg, int n_long, const int* __restrict__ list,
-                  const int* __restrict__ seg_off, const int* __restrict__ rp,
+k_sliced_segments(int n_seg, const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
                   const int* __restrict__ ci, const double* __restrict__ v,
-                  const double* __restrict__ x, double* __restrict__ partial)
+                  const double* __restrict__ x, double* __restrict__ partial, double* __restrict__ y)
 {
     const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
     if (w >= n_seg) return;
     const int lane = threadIdx.x & 31;
-    int lo = 0, hi = n_long - 1;  // last long row whose first segment is <= w
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    const int r = list[lo];
-    const int64_t b = (int64_t)rp[r] + (int64_t)(w - seg_off[lo]) * kSlicedSeg;
-    const int64_t e = min((int64_t)rp[r + 1], b + kSlicedSeg);
+    const longlong2 be = segment_bounds(seg_be, w);
+    const int64_t b = be.x, e = be.y;
     const double sum = group_sum(row_partial<32, 8>(b, e, lane, ColPlain<int>{ci}, v, x), 32);
-    if (lane == 0) partial[w] = sum;
+    if (lane == 0) {
+        const int r1 = seg_row[w];
+        if (r1 >= 0) y[r1] = sum; else partial[w] = sum;
+    }
 }
 
-__global__ void k_sliced_fixup(int n_long, const int* __restrict__ list,
+// fix[t]: index in the long-row list of the t-th row with several segments
+__global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int* __restrict__ list,
                                const int* __restrict__ seg_off, const double* __restrict__ partial,
                                double* __restrict__ y)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_long) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_fix) return;
+    const int q = fix[t];
     double sum = 0.0;
     for (int i = seg_off[q]; i < seg_off[q + 1]; ++i) sum += partial[i];
     y[list[q]] = sum;
@@ -300,35 +323,34 @@ k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restr
 // per element; the segment's lanes are combined by a shuffle tree)
 template <typename VT, bool ACC32>
 __global__ void __launch_bounds__(kSB)
-k_sliced_segments_lp(int n_seg, int n_long, const int* __restrict__ list,
-                     const int* __restrict__ seg_off, const int* __restrict__ rp,
+k_sliced_segments_lp(int n_seg, const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
                      const int* __restrict__ ci, const double* __restrict__ v,
                      const double* __restrict__ x, const float* __restrict__ x32,
-                     double* __restrict__ partial)
+                     double* __restrict__ partial, double* __restrict__ y)
 {
     const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
     if (w >= n_seg) return;
     const int lane = threadIdx.x & 31;
-    int lo = 0, hi = n_long - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    const int r = list[lo];
-    const int64_t b = (int64_t)rp[r] + (int64_t)(w - seg_off[lo]) * kSlicedSeg;
-    const int64_t e = min((int64_t)rp[r + 1], b + kSlicedSeg);
+    const longlong2 be = segment_bounds(seg_be, w);
+    const int64_t b = be.x, e = be.y;
     if (ACC32) {
         float acc = 0.f;
         for (int64_t j = b + lane; j < e; j += 32)
             acc = fmaf(widen32(round_to(__ldcs(v + j), (VT*)nullptr)), __ldg(x32 + __ldcs(ci + j)), acc);
         acc = group_sum32(acc, 32);
-        if (lane == 0) partial[w] = (double)acc;
+        if (lane == 0) {
+            const int r1 = seg_row[w];
+            if (r1 >= 0) y[r1] = (double)acc; else partial[w] = (double)acc;
+        }
     } else {
         double acc = 0.0;
         for (int64_t j = b + lane; j < e; j += 32)
             acc = fma((double)widen32(round_to(__ldcs(v + j), (VT*)nullptr)), ldx(x + __ldcs(ci + j)), acc);
         acc = group_sum(acc, 32);
-        if (lane == 0) partial[w] = acc;
+        if (lane == 0) {
+            const int r1 = seg_row[w];
+            if (r1 >= 0) y[r1] = acc; else partial[w] = acc;
+        }
     }
 }
 
@@ -502,8 +524,21 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         for (int q = 0; q < d.n_long; ++q) off[q + 1] = off[q] + (len[q] + kSlicedSeg - 1) / kSlicedSeg;
         d.n_seg = off[d.n_long];
         SPMV_CUDA_TRY(cudaMemcpyAsync(d.seg_off, off.data(), 4 * ((size_t)d.n_long + 1), cudaMemcpyHostToDevice, s));
-        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)d.n_seg)) != SPMV_OK)
+        // the rows with several segments, summed by the fix-up
+        std::vector<int> fix;
+        for (int q = 0; q < d.n_long; ++q)
+            if (off[q + 1] - off[q] > 1) fix.push_back(q);
+        d.n_fix = (int)fix.size();
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)d.n_seg)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_be), 16 * (int64_t)d.n_seg)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_row), 4 * (int64_t)d.n_seg)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.fix), 4 * std::max<int64_t>(d.n_fix, 1))) != SPMV_OK)
             return st;
+        if (d.n_fix > 0)
+            SPMV_CUDA_TRY(cudaMemcpyAsync(d.fix, fix.data(), 4 * (size_t)d.n_fix, cudaMemcpyHostToDevice, s));
+        k_sl_seg_table<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, d.seg_off,
+                                                                          A.rowptr, d.seg_be, d.seg_row);
+        SPMV_CUDA_TRY(cudaGetLastError());
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     }
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
@@ -552,12 +587,11 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     if (e != cudaSuccess || d.n_long == 0) return e;
     const unsigned sgrid = grid_of(32 * (int64_t)d.n_seg, INT32_MAX);
     if (d.value_type == SPMV_VAL_F64) {
-        k_sliced_segments<<<sgrid, kSB, 0, s>>>(d.n_seg, d.n_long, d.long_rows, d.seg_off, A.rowptr,
-                                                 A.colind, A.val, x, d.partial);
+        k_sliced_segments<<<sgrid, kSB, 0, s>>>(d.n_seg, d.seg_be, d.seg_row, A.colind, A.val, x, d.partial, y);
     } else {
 #define SPMV_SL_SEG(VT, A32)                                                                        \
-    k_sliced_segments_lp<VT, A32><<<sgrid, kSB, 0, s>>>(d.n_seg, d.n_long, d.long_rows, d.seg_off, \
-                                                        A.rowptr, A.colind, A.val, x, d.x32, d.partial)
+    k_sliced_segments_lp<VT, A32><<<sgrid, kSB, 0, s>>>(d.n_seg, d.seg_be, d.seg_row, A.colind, A.val, x, \
+                                                        d.x32, d.partial, y)
         if (d.value_type == SPMV_VAL_F32) {
             if (d.acc32) SPMV_SL_SEG(float, true); else SPMV_SL_SEG(float, false);
         } else {
@@ -566,9 +600,9 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
 #undef SPMV_SL_SEG
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_sliced_fixup<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, d.seg_off,
-                                                                      d.partial, y);
+    if (e != cudaSuccess || d.n_fix == 0) return e;
+    k_sliced_fixup<<<(unsigned)((d.n_fix + 255) / 256), 256, 0, s>>>(d.n_fix, d.fix, d.long_rows, d.seg_off,
+                                                                     d.partial, y);
     return cudaGetLastError();
 }
 

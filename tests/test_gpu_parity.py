@@ -292,7 +292,9 @@ def test_sliced_layout_bit_exact(sigma, cap, name, A):
     S = (A.n_rows + 31) // 32
     info = P.info()
     assert info.n_blocks == S and info.block_nnz == sigma and info.items_per_warp == cap
-    assert info.launches == (0 if A.n_rows == 0 else (3 if n_long else 1))
+    lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
+    several = bool((lens > max(cap, 2048)).any())  # long rows of several segments: the fix-up
+    assert info.launches == (0 if A.n_rows == 0 else 1 + (n_long > 0) + several)
     if S == 0:
         return
     assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWLEN, 32 * S, torch.int32), rowlen)
