@@ -455,10 +455,10 @@ int32_t spmv_class_variant(int32_t cls)
     switch (cls) {
         // calibrated on GB300: per class, the variant with the lowest
         // geometric-mean slowdown against the exhaustive best on the training
-        // matrices (CML 1.04, MB 1.00, IMB 1.16, CMP 1.04).  SLICED wins every
+        // matrices (CML 1.04, MB 1.00, IMB 1.13, CMP 1.05).  SLICED wins every
         // class because its prepare step adapts the layout to the row lengths
         // (length sort and row cap for imbalance, four slices per warp for
-        // short rows); DYNAMIC is next for IMB (1.26)
+        // short rows); DYNAMIC is next for IMB (1.28)
         case SPMV_CLASS_CML: return SPMV_V7_SLICED;
         case SPMV_CLASS_MB: return SPMV_V7_SLICED;
         case SPMV_CLASS_IMB: return SPMV_V7_SLICED;
