@@ -90,6 +90,8 @@ def _load():
                 "orc_sliced_layout": (i64, [i64, P, i32, i32, i32, P, P, P, P]),
                 "orc_sliced_fill": (None, [i64, P, P, P, P, P, P, i32, P, P]),
                 "orc_sliced_offsets": (i64, [i64, P, P, P, P, P, i32, P, P]),
+                "orc_sliced_diag": (i64, [i64, P, P, P, P, P, P]),
+                "orc_sliced_index_bytes": (i32, [i64]),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -278,6 +280,24 @@ def sliced_offsets(A, perm, rowlen, sptr, vec: int = 1):
     span = _load().orc_sliced_offsets(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr),
                                       vec, _p(base), _p(off))
     return base[:32 * S], off[:tot], int(span)
+
+
+def sliced_diag(A, perm, rowlen, sptr):
+    """Offsets column - row of the FP64 sliced layout (0 in padding), the
+    largest |offset| over the rows in the slices, and the bytes per stored
+    index that largest offset allows (1, 2 or 4)."""
+    rp, ci, _ = _csr(A)
+    tot = int(sptr[-1])
+    d = np.empty(max(tot, 1), np.int32)
+    perm = _np(perm, np.int32)
+    rowlen = _np(rowlen, np.int32)
+    sptr = _np(sptr, np.int64)
+    reach = int(_load().orc_sliced_diag(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr), _p(d)))
+    return d[:tot], reach, int(_load().orc_sliced_index_bytes(reach))
+
+
+def sliced_index_bytes(reach: int) -> int:
+    return int(_load().orc_sliced_index_bytes(int(reach)))
 
 
 def mlp_forward_f32(params: dict, v) -> np.ndarray:

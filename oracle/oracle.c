@@ -11,7 +11,8 @@
  * Compiled with -O2 -ffp-contract=off: every floating-point operation below
  * is rounded as written (no fused multiply-add unless fmaf is called).
  *
- * Readings of the paper where it is silent or garbled (numbered O1..O20):
+ * Readings of the paper where it is silent or garbled (numbered O1..O23; the
+ * ones that concern a single function are stated beside it):
  *   O1  Algorithm 1 writes an assignment over an inclusive, 1-based range; the
  *       product is read as y_i = sum over the half-open 0-based range
  *       [rowptr_i, rowptr_{i+1}), with y_i = 0 for an empty row.
@@ -29,6 +30,10 @@
  *       names the class; none above -> CMP.  s_inflate = T_inflate / T_base.
  *   O15 empty rows take part in the row statistics with nnz = bw = 0 and
  *       disp = clust = 0.
+ *   O23 Table 2's delta coding of column indices (8 or 16 bits) takes, for
+ *       the FP64 sliced layout, the offset of each column from its row's
+ *       index: 8 bits when every |column - row| in the slices is at most 127,
+ *       16 bits when at most 32767.
  */
 #include <math.h>
 #include <stdint.h>
@@ -474,6 +479,36 @@ void orc_sliced_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
  * it holds col - base; padding slots hold 0.  Returns the largest span
  * (last - first column) over the rows in slices; offsets are meaningful only
  * when it is below 65536.                                                     */
+/* Column offsets from the row index for the FP64 sliced layout (reading
+ * O23): d = column - row at every element's slot (vec = 1 placement), 0 in
+ * padding, and the largest |d| over the rows in the slices.  The library
+ * keeps d in 8 bits when that largest |d| is at most 127, in 16 bits when at
+ * most 32767, and 32-bit columns otherwise (orc_sliced_index_bytes).          */
+int64_t orc_sliced_diag(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                        const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
+                        int32_t *d_out)
+{
+    int64_t n_slices = (n_rows + 31) / 32, reach = 0;
+    int64_t tot = slice_ptr[n_slices];
+    for (int64_t q = 0; q < tot; ++q) d_out[q] = 0;
+    for (int64_t p = 0; p < 32 * n_slices; ++p) {
+        if (p >= n_rows || rowlen[p] <= 0) continue;
+        int64_t r = perm[p], b = rowptr[r];
+        for (int64_t k = 0; k < rowlen[p]; ++k) {
+            int64_t d = (int64_t)colind[b + k] - r;
+            d_out[slot_of(slice_ptr, p, k, 1)] = (int32_t)d;
+            if (d > reach) reach = d;
+            if (-d > reach) reach = -d;
+        }
+    }
+    return reach;
+}
+
+int32_t orc_sliced_index_bytes(int64_t reach)
+{
+    return reach <= 127 ? 1 : (reach <= 32767 ? 2 : 4);
+}
+
 int64_t orc_sliced_offsets(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
                            const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
                            int32_t vec, int32_t *rowbase_pos, uint16_t *off_out)

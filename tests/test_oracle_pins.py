@@ -567,6 +567,63 @@ def test_sliced_layout_against_numpy_sort_and_reconstruction(sigma, cap, vec):
     assert np.count_nonzero(val) == np.count_nonzero(va[np.repeat(lengths <= cap, lengths)])
 
 
+def _csr_rows(rows, n_cols):
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.array([c for r in rows for c in r], np.int32)
+    va = np.arange(1, len(ci) + 1, dtype=np.float64)
+    return synth.HostCSR(len(rows), n_cols, torch.from_numpy(rp), torch.from_numpy(ci),
+                         torch.from_numpy(va), "rows")
+
+
+def test_sliced_diag_hand_example():
+    """Rows {0, 2}, {1}, {0, 1, 300} in order, one slice of length 3, element
+    k of position p at slot 32 k + p: offsets column - row are 0, 2 (row 0),
+    0 (row 1), -2, -1, 298 (row 2); the largest is 298, so 16-bit offsets.
+    Without column 300 the largest is 2: 8-bit offsets."""
+    A = _csr_rows([[0, 2], [1], [0, 1, 300]], 400)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=1, cap=1024)
+    d, reach, nb = oracle.sliced_diag(A, perm, rowlen, sptr)
+    expect = np.zeros(96, np.int32)
+    expect[[0, 32]] = [0, 2]
+    expect[1] = 0
+    expect[[2, 34, 66]] = [-2, -1, 298]
+    assert np.array_equal(d, expect) and reach == 298 and nb == 2
+    B = _csr_rows([[0, 2], [1], [0, 1]], 400)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(B, sigma=1, cap=1024)
+    assert oracle.sliced_diag(B, perm, rowlen, sptr)[1:] == (2, 1)
+    # the width rule at its boundaries
+    assert [oracle.sliced_index_bytes(r) for r in (0, 127, 128, 32767, 32768, 1 << 30)] == [1, 1, 2, 2, 4, 4]
+
+
+@pytest.mark.parametrize("sigma,cap", [(1, 1000), (64, 20)])
+def test_sliced_diag_decodes_to_the_columns(sigma, cap):
+    """row + offset gives back every column in the slices (rows sorted or
+    not, long rows left out), padding holds 0, and the reach is the largest
+    |column - row| over the rows in the slices."""
+    g = np.random.default_rng(5 + sigma)
+    lengths = np.minimum(g.zipf(1.7, 500), 30)
+    lengths[:4] = [0, 1, 31, 2]
+    A = _csr_from_lengths(lengths.tolist(), n_cols=700, seed=6)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=sigma, cap=cap)
+    col, _ = oracle.sliced_fill(A, perm, rowlen, sptr)
+    d, reach, nb = oracle.sliced_diag(A, perm, rowlen, sptr)
+    rows = np.full(len(d), 0, np.int64)
+    real = np.zeros(len(d), bool)
+    far = 0
+    rp, ci = A.rowptr.numpy(), A.colind.numpy()
+    for p in range(A.n_rows):
+        if rowlen[p] <= 0:
+            continue
+        k = np.arange(rowlen[p])
+        idx = sptr[p // 32] + 32 * k + p % 32
+        rows[idx] = perm[p]
+        real[idx] = True
+        far = max(far, int(np.abs(ci[rp[perm[p]]:rp[perm[p] + 1]].astype(np.int64) - perm[p]).max()))
+    assert np.array_equal((rows + d)[real], col[real].astype(np.int64))
+    assert not d[~real].any()
+    assert reach == far and nb == (1 if far <= 127 else 2 if far <= 32767 else 4)
+
+
 @pytest.mark.parametrize("vec", [1, 4])
 def test_sliced_offsets_decode_to_the_columns(vec):
     """base + offset gives back every column of every row in the slices,
