@@ -206,6 +206,14 @@ typedef struct {
     int32_t source;
     int32_t accumulate;  /* COMPRESSED: 0 by value type (FP64 values -> FP64,
                             FP32/BF16 values -> FP32), 1 FP64, 2 FP32 */
+    int32_t index_bytes; /* SLICED with FP64 values: narrowest stored column
+                            allowed -- 0 or 4: 32-bit columns; 2 or 1: the
+                            column minus the row index in int16 or int8 when
+                            every row in the slices stays that close to its
+                            diagonal (else the next wider form).  Measured on
+                            GB300 the 32-bit form is as fast or faster (the
+                            narrower index stream does not shorten the
+                            FP64-issue-bound kernel), hence the default. */
 } spmv_choice_t;
 
 /* A matrix prepared for one variant (opaque).  It borrows A's arrays and owns
@@ -225,6 +233,9 @@ typedef struct {
     int32_t bulk_copy;     /* 1 when the pipelined bulk-copy kernel is used     */
     int32_t accumulate;    /* 1 FP64, 2 FP32 (COMPRESSED with FP32 accumulation) */
     int32_t launches;      /* kernels one spmv call launches (0 when n_rows = 0) */
+    int32_t index_bytes;   /* SLICED with FP64 values: bytes per stored column,
+                              4 (the column), 2 or 1 (column - row, int16 or
+                              int8); 4 for the other variants                 */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */
@@ -245,12 +256,16 @@ typedef enum {
                                    ptr[s] + 128 (k / 4) + 4 l + k % 4 (slices padded
                                    to a multiple of 4 elements per row)                */
     SPMV_EXPORT_SLICE_COL = 10, /* SLICED: int32 [slice_ptr[S]] columns, column-major
-                                   (absent with 16-bit offsets)                        */
+                                   (absent with 16-bit offsets and with index_bytes
+                                   2 or 1)                                           */
     SPMV_EXPORT_SLICE_VAL = 11, /* SLICED: [slice_ptr[S]] values in value_type          */
     SPMV_EXPORT_SLICE_OFF16 = 12, /* SLICED, 16-bit offsets: uint16 [slice_ptr[S]]
                                    column - row base                                   */
-    SPMV_EXPORT_SLICE_ROWBASE = 13 /* SLICED, 16-bit offsets: int32 [32 S] first column
+    SPMV_EXPORT_SLICE_ROWBASE = 13, /* SLICED, 16-bit offsets: int32 [32 S] first column
                                    of each position's row (0 where none)               */
+    SPMV_EXPORT_SLICE_DIAG = 14   /* SLICED, FP64 values, index_bytes 2 or 1: int16 or
+                                     int8 [slice_ptr[S]] column - row, column-major
+                                     like SLICE_COL, 0 in padding                  */
 } spmv_export;
 
 /* ---- status ---------------------------------------------------------- */
@@ -442,8 +457,10 @@ spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
  * matrix as work items of 4 slices (its long rows one item each); a MERGE or
  * DYNAMIC matrix (imbalance class) as slices of rows sorted by length in
  * windows of 256, which the batch prepares and owns (CSR rows would make a
- * warp run as many DFMAs as its longest row); any other variant as CSR row
- * items with its prepared lanes per row.  Synchronizes `stream`. */
+ * warp run as many DFMAs as its longest row); a SLICED matrix with FP32 or
+ * BF16 values as the FP64 sliced form, which the batch prepares and owns;
+ * any other variant as CSR row items with its prepared lanes per row.
+ * Synchronizes `stream`. */
 spmv_status spmv_batch_create_prepared(const spmv_prepared_t *const *P, int32_t count,
                                        spmv_batch_t **out, spmv_stream_t stream);
 /* Sets the vectors: x[m], y[m] are device pointers (host arrays of count

@@ -18,7 +18,8 @@ from ._abi import (  # noqa: F401  (re-exported)
     SPMV_OK, STATUS_NAMES, VARIANTS, VARIANT_IDS, CLASSES, VAL_F64, VAL_F32, VAL_BF16,
     EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
     EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
-    EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE, declare,
+    EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE, EXPORT_SLICE_DIAG,
+    declare,
 )
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -153,13 +154,14 @@ ACC_DEFAULT, ACC_F64, ACC_F32 = 0, 1, 2
 
 
 def make_choice(variant, threads_per_row=0, block_nnz=0, items_per_warp=0,
-                value_type=VAL_F64, accumulate=ACC_DEFAULT) -> Choice:
+                value_type=VAL_F64, accumulate=ACC_DEFAULT, index_bytes=0) -> Choice:
     v = VARIANT_IDS[variant] if isinstance(variant, str) else int(variant)
     c = Choice()
     c.variant, c.cls = v, -1
     c.threads_per_row, c.block_nnz, c.items_per_warp = threads_per_row, block_nnz, items_per_warp
     c.value_type = value_type
     c.accumulate = accumulate
+    c.index_bytes = index_bytes
     return c
 
 

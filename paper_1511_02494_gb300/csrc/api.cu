@@ -159,7 +159,7 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
         // segment offsets, per segment its bounds and row and a partial
         const SlicedPlan& d = P->sl;
         const int vb = d.value_type == SPMV_VAL_F64 ? 8 : d.value_type == SPMV_VAL_F32 ? 4 : 2;
-        const int cb = d.off16 ? 2 : 4;
+        const int cb = d.value_type == SPMV_VAL_F64 ? d.cbytes : (d.off16 ? 2 : 4);
         return (int64_t)(vb + cb) * A.nnz + 128 * d.n_slices * (d.off16 ? 2 : 1) + 12 * d.n_slices +
                (d.sigma > 1 ? 4 * A.n_rows : 0) + 12 * (int64_t)d.n_long + 36 * (int64_t)d.n_seg +
                8 * A.n_cols + (d.acc32 ? 8 * A.n_cols : 0) + 8 * A.n_rows;
@@ -327,6 +327,11 @@ spmv_status check_choice(const spmv_choice_t* c)
     const bool lowp_ok = c->variant == SPMV_V6_COMPRESSED || c->variant == SPMV_V7_SLICED;
     if (c->value_type != SPMV_VAL_F64 && !lowp_ok)
         return fail(SPMV_ERR_UNSUPPORTED, "low-precision values only in the COMPRESSED and SLICED variants");
+    if (c->index_bytes != 0 && c->index_bytes != 1 && c->index_bytes != 2 && c->index_bytes != 4)
+        return fail(SPMV_ERR_INVALID_ARG, "index_bytes must be 0, 1, 2 or 4");
+    if (c->index_bytes != 0 && c->index_bytes != 4 &&
+        (c->variant != SPMV_V7_SLICED || c->value_type != SPMV_VAL_F64))
+        return fail(SPMV_ERR_UNSUPPORTED, "narrow column indices only in SLICED with FP64 values");
     if (c->accumulate < 0 || c->accumulate > 2)
         return fail(SPMV_ERR_INVALID_ARG, "accumulate must be 0 (by value type), 1 (FP64) or 2 (FP32)");
     if (c->accumulate == 2 && (!lowp_ok || c->value_type == SPMV_VAL_F64))
@@ -606,6 +611,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.bulk_copy = P->bulk ? 1 : 0;
     i.accumulate = P->c.variant == SPMV_V6_COMPRESSED || P->c.variant == SPMV_V7_SLICED ? P->c.accumulate : 1;
     i.launches = launches_of(P);
+    i.index_bytes = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.cbytes : 4;
     *info = i;
     return SPMV_OK;
 }
@@ -667,6 +673,12 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
             break;
         case SPMV_EXPORT_SLICE_ROWBASE:
             if (v == SPMV_V7_SLICED && P->sl.off16) { src = P->sl.rowbase; size = 4 * 32 * P->sl.n_slices; }
+            break;
+        case SPMV_EXPORT_SLICE_DIAG:
+            if (v == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 && P->sl.cbytes < 4) {
+                src = P->sl.scol;
+                size = (int64_t)P->sl.cbytes * P->sl.tot;
+            }
             break;
         default:
             return fail(SPMV_ERR_INVALID_ARG, "unknown export");

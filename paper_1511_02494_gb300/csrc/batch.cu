@@ -36,9 +36,10 @@ struct BatchMat {
     const int* slice_len;
     const int64_t* slice_ptr;
     const int* perm;
-    const int* scol;
+    const void* scol;  // stored columns: int, or int16 / int8 offsets from the row
     const double* sval;
     const int* long_rows;
+    int32_t scb;       // bytes per stored column (4, 2 or 1)
 };
 
 // lg 0..5: rows [r0, r1) with 2^lg lanes per row; kSliceItem: slices
@@ -99,9 +100,17 @@ k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, 
         const BatchMat M = mats[I.m];
         switch (I.lg) {
             case kSliceItem:
-                for (int s = I.r0; s < I.r1; ++s)
-                    slice_rows<4>(s, lane, M.rowlen, M.slice_len, M.slice_ptr, M.perm, M.scol, M.sval,
-                                  M.x, M.y);
+                for (int s = I.r0; s < I.r1; ++s) {
+                    if (M.scb == 1)
+                        slice_rows<4, int8_t>(s, lane, M.rowlen, M.slice_len, M.slice_ptr, M.perm,
+                                              static_cast<const int8_t*>(M.scol), M.sval, M.x, M.y);
+                    else if (M.scb == 2)
+                        slice_rows<4, int16_t>(s, lane, M.rowlen, M.slice_len, M.slice_ptr, M.perm,
+                                               static_cast<const int16_t*>(M.scol), M.sval, M.x, M.y);
+                    else
+                        slice_rows<4, int>(s, lane, M.rowlen, M.slice_len, M.slice_ptr, M.perm,
+                                           static_cast<const int*>(M.scol), M.sval, M.x, M.y);
+                }
                 break;
             case kLongItem:
                 for (int q = I.r0; q < I.r1; ++q) {
@@ -266,12 +275,14 @@ spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t 
         }
         const spmv_csr_t& A = Pm->A;
         // imbalance variants (MERGE, DYNAMIC) run as length-sorted slices: a
-        // warp of CSR rows would run as many DFMAs as its longest row
-        if (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC) {
+        // warp of CSR rows would run as many DFMAs as its longest row; SLICED
+        // with FP32/BF16 values runs as its FP64 form (the batch sums FP64)
+        const bool lp_sliced = Pm->c.variant == SPMV_V7_SLICED && Pm->c.value_type != SPMV_VAL_F64;
+        if (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC || lp_sliced) {
             spmv_choice_t c{};
             c.variant = SPMV_V7_SLICED;
             c.cls = -1;
-            c.block_nnz = 256;
+            c.block_nnz = lp_sliced ? 0 : 256;
             spmv_prepared* Q = nullptr;
             st = spmv_prepare(&A, &c, 1, &Q, stream);
             if (st != SPMV_OK) { spmv_batch_free(B); return st; }
@@ -300,14 +311,15 @@ spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* con
     for (size_t m = 0; m < B->mats.size(); ++m) {
         const spmv_csr_t& A = B->mats[m];
         h[m] = {A.rowptr, A.colind, A.val, x[m], y[m], A.n_rows,
-                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 4};
         if (const spmv_prepared* P = B->preps[m]) {
             const SlicedPlan& d = P->sl;
             h[m].rowlen = d.rowlen;
             h[m].slice_len = d.slice_len;
             h[m].slice_ptr = d.slice_ptr;
             h[m].perm = d.sigma > 1 ? d.perm : nullptr;
-            h[m].scol = d.col;
+            h[m].scol = d.scol;
+            h[m].scb = d.cbytes;
             h[m].sval = d.val;
             h[m].long_rows = d.long_rows;
         }

@@ -228,9 +228,10 @@ struct SlArgs {
     int64_t n_slices;
     const int* rowlen; const int* slice_len; const int64_t* slice_ptr; const int* perm;
     const int* col; const double* val; const uint16_t* off; const int* rowbase; const void* lowval;
+    const void* scol;  // FP64 values: stored columns (int, or int16/int8 offsets from the row)
 };
 
-template <typename VT, bool OFF16, bool ACC32>
+template <typename VT, bool OFF16, bool ACC32, typename CT = int>
 __global__ void __launch_bounds__(kCT, dot_blocks<VT>())
 k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p32,
              double* __restrict__ q, double* __restrict__ part, CgState* st)
@@ -244,7 +245,8 @@ k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p
         int row;
         double v;
         if constexpr (sizeof(VT) == 8)
-            v = dev::slice_value<kDotU>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm, a.col, a.val, p, &row);
+            v = dev::slice_value<kDotU, CT>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
+                                            static_cast<const CT*>(a.scol), a.val, p, &row);
         else
             v = dev::slice_value_lp<OFF16 ? 2 : 1, VT, OFF16, ACC32>(s, lane, a.rowlen, a.slice_len, a.slice_ptr, a.perm,
                                                          a.col, a.off, a.rowbase,
@@ -282,10 +284,15 @@ cudaError_t launch_sliced_dot(const spmv_prepared* P, const double* p, double* q
 {
     const SlicedPlan& d = P->sl;
     SlArgs a{d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, d.sigma > 1 ? d.perm : nullptr,
-             d.col, d.val, d.off, d.rowbase, d.lowval};
+             d.col, d.val, d.off, d.rowbase, d.lowval, d.scol};
     const unsigned grid = sliced_dot_grid(P);
     if (d.value_type == SPMV_VAL_F64) {
-        k_sliced_dot<double, false, false><<<grid, kCT, 0, s>>>(a, p, nullptr, q, part, st);
+        if (d.cbytes == 1)
+            k_sliced_dot<double, false, false, int8_t><<<grid, kCT, 0, s>>>(a, p, nullptr, q, part, st);
+        else if (d.cbytes == 2)
+            k_sliced_dot<double, false, false, int16_t><<<grid, kCT, 0, s>>>(a, p, nullptr, q, part, st);
+        else
+            k_sliced_dot<double, false, false, int><<<grid, kCT, 0, s>>>(a, p, nullptr, q, part, st);
     } else {
 #define SPMV_CG_SL(VT, O16, A32) k_sliced_dot<VT, O16, A32><<<grid, kCT, 0, s>>>(a, p, d.x32, q, part, st)
 #define SPMV_CG_SL_VT(VT)                                                                  \

@@ -67,7 +67,9 @@ struct SlicedPlan {
     int* slice_len = nullptr;    // [n_slices]
     int64_t* slice_ptr = nullptr;  // [n_slices + 1] element offset of each slice
     int* perm = nullptr;         // [n_rows] position -> row (sigma > 1 only)
-    int* col = nullptr;          // [tot] column-major slice contents
+    int* col = nullptr;          // [tot] column-major slice contents (32-bit columns)
+    void* scol = nullptr;        // FP64 values: [tot] stored columns, cbytes each
+    int cbytes = 4;              // 4: columns; 2 / 1: column - row in int16 / int8
     double* val = nullptr;       // [tot]
     int* long_rows = nullptr;    // [n_long], ascending
     int* seg_off = nullptr;      // [n_long + 1] first segment of each long row

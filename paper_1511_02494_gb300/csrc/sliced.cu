@@ -114,10 +114,13 @@ __global__ void k_sl_slice_len(int64_t n_slices, const int* __restrict__ rowlen,
 }
 
 // column-major contents of each slice (padding was zeroed beforehand)
+// FP64 contents: CT int stores the columns, int16_t / int8_t the column
+// minus the row index (the range was checked by k_sl_reach)
+template <typename CT>
 __global__ void k_sl_fill(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
                           const double* __restrict__ v, const int* __restrict__ perm,
                           const int* __restrict__ rowlen, const int64_t* __restrict__ slice_ptr,
-                          int* __restrict__ col, double* __restrict__ val)
+                          CT* __restrict__ col, double* __restrict__ val)
 {
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= n_slices) return;
@@ -129,9 +132,26 @@ __global__ void k_sl_fill(int64_t n_slices, const int* __restrict__ rp, const in
     const int64_t b = rp[r];
     const int64_t q0 = slice_ptr[s] + lane;
     for (int k = 0; k < len; ++k) {
-        col[q0 + (int64_t)k * 32] = ci[b + k];
+        col[q0 + (int64_t)k * 32] = sizeof(CT) == 4 ? (CT)ci[b + k] : (CT)(ci[b + k] - r);
         val[q0 + (int64_t)k * 32] = v[b + k];
     }
+}
+
+// largest |column - row| over the rows in the slices (the first or the last
+// column of a row, its columns being increasing)
+__global__ void k_sl_reach(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const int* __restrict__ perm, const int* __restrict__ rowlen,
+                           unsigned* __restrict__ reach)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 32 * n_slices) return;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int64_t r = perm ? perm[p] : p;
+    const int64_t b = rp[r];
+    const int64_t lo = r - ci[b], hi = (int64_t)ci[b + len - 1] - r;
+    const int64_t m = lo > hi ? lo : hi;
+    atomicMax(reach, (unsigned)(m < 0 ? 0 : (m > 0x7fffffff ? 0x7fffffff : m)));
 }
 
 // rows longer than cap, appended with one atomic per warp
@@ -157,30 +177,31 @@ __global__ void k_sl_long_list(int64_t n_rows, const int* __restrict__ rp, int c
 // form on all three regular test matrices (random columns 0.249 against
 // 0.258 ms, stencil 0.115 against 0.136 ms, 2-nonzero rows 0.080 against
 // 0.093 ms).
-template <int U>
+template <int U, typename CT>
 __global__ void __launch_bounds__(kSB, 8)
 k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
          const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
-         const int* __restrict__ col, const double* __restrict__ val,
+         const CT* __restrict__ col, const double* __restrict__ val,
          const double* __restrict__ x, double* __restrict__ y)
 {
     const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
     if (s >= n_slices) return;  // whole warps only
-    slice_rows<U>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
+    slice_rows<U, CT>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
 }
 
 // R consecutive slices per warp (slice_rows_multi), for short slices whose
 // few loads per lane leave the warp waiting on latency.
-template <int U, int R, int B>
+template <int U, int R, int B, typename CT>
 __global__ void __launch_bounds__(kSB, B)
 k_sliced_multi(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
                const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
-               const int* __restrict__ col, const double* __restrict__ val,
+               const CT* __restrict__ col, const double* __restrict__ val,
                const double* __restrict__ x, double* __restrict__ y)
 {
     const int64_t s0 = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
     if (s0 >= n_slices) return;  // whole warps only
-    slice_rows_multi<U, R>(s0, n_slices, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
+    slice_rows_multi<U, R, CT>(s0, n_slices, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x,
+                               y);
 }
 
 __global__ void k_sl_row_lengths(int n, const int* __restrict__ list, const int* __restrict__ rp,
@@ -449,14 +470,35 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
     if (P->c.accumulate == 0) P->c.accumulate = d.value_type == SPMV_VAL_F64 ? 1 : 2;
     d.acc32 = P->c.accumulate == 2;
     if (d.value_type == SPMV_VAL_F64) {
-        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.col), 4 * tot1)) != SPMV_OK ||
+        // columns as offsets from the row index in 8 or 16 bits when the
+        // caller allows it and every row in the slices stays that close to
+        // its diagonal, else 32-bit
+        const int allowed = P->c.index_bytes == 0 ? 4 : P->c.index_bytes;
+        unsigned reach = 0;
+        if (d.n_slices > 0 && allowed < 4) {
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
+            k_sl_reach<<<(unsigned)((32 * d.n_slices + kSB - 1) / kSB), kSB, 0, s>>>(
+                d.n_slices, A.rowptr, A.colind, permp, d.rowlen, d.count);
+            SPMV_CUDA_TRY(cudaGetLastError());
+            SPMV_CUDA_TRY(cudaMemcpyAsync(&reach, d.count, 4, cudaMemcpyDeviceToHost, s));
+            SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        d.cbytes = std::max(allowed, reach <= 127 ? 1 : (reach <= 32767 ? 2 : 4));
+        P->c.index_bytes = d.cbytes;
+        if ((st = prepared_alloc(P, &d.scol, (int64_t)d.cbytes * tot1)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.val), 8 * tot1)) != SPMV_OK)
             return st;
-        SPMV_CUDA_TRY(cudaMemsetAsync(d.col, 0, 4 * tot1, s));
+        if (d.cbytes == 4) d.col = static_cast<int*>(d.scol);
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.scol, 0, (int64_t)d.cbytes * tot1, s));
         SPMV_CUDA_TRY(cudaMemsetAsync(d.val, 0, 8 * tot1, s));
         if (d.n_slices > 0) {
-            k_sl_fill<<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, d.rowlen,
-                                                 d.slice_ptr, d.col, d.val);
+#define SPMV_SL_FILL64(CT)                                                                           \
+    k_sl_fill<CT><<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, d.rowlen, \
+                                             d.slice_ptr, static_cast<CT*>(d.scol), d.val)
+            if (d.cbytes == 1) SPMV_SL_FILL64(int8_t);
+            else if (d.cbytes == 2) SPMV_SL_FILL64(int16_t);
+            else SPMV_SL_FILL64(int);
+#undef SPMV_SL_FILL64
             SPMV_CUDA_TRY(cudaGetLastError());
         }
     } else {
@@ -559,17 +601,23 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (d.value_type == SPMV_VAL_F64) {
-        // R slices per warp (sliced_prepare chose R, or the caller did)
-#define SPMV_SL_M(U, RR, B) \
-    k_sliced_multi<U, RR, B><<<grid_of(32 * ((d.n_slices + RR - 1) / RR), INT32_MAX), kSB, 0, s>>>( \
-        d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col, d.val, x, y)
-        switch (P->c.threads_per_row) {
-            case 2: SPMV_SL_M(2, 2, 6); break;
-            case 4: SPMV_SL_M(1, 4, 4); break;
-            default:
-                k_sliced<4><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, d.col,
-                                                 d.val, x, y);
+        // R slices per warp (sliced_prepare chose R, or the caller did);
+        // columns stored as CT (sliced_prepare chose the width)
+#define SPMV_SL_M(U, RR, B, CT)                                                                    \
+    k_sliced_multi<U, RR, B, CT><<<grid_of(32 * ((d.n_slices + RR - 1) / RR), INT32_MAX), kSB, 0, s>>>( \
+        d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, perm, static_cast<const CT*>(d.scol), d.val, x, y)
+#define SPMV_SL_CT(CT)                                                                             \
+        switch (P->c.threads_per_row) {                                                            \
+            case 2: SPMV_SL_M(2, 2, 6, CT); break;                                                 \
+            case 4: SPMV_SL_M(1, 4, 4, CT); break;                                                 \
+            default:                                                                               \
+                k_sliced<4, CT><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, \
+                                                     perm, static_cast<const CT*>(d.scol), d.val, x, y); \
         }
+        if (d.cbytes == 1) { SPMV_SL_CT(int8_t) }
+        else if (d.cbytes == 2) { SPMV_SL_CT(int16_t) }
+        else { SPMV_SL_CT(int) }
+#undef SPMV_SL_CT
 #undef SPMV_SL_M
     } else {
 #define SPMV_SL_LP(VT, O16, A32)                                                                   \

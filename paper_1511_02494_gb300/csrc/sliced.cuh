@@ -15,13 +15,22 @@
 namespace spmvlib {
 namespace dev {
 
-// FP64 values and 32-bit columns
-template <int U>
+// FP64 values.  The column of a slot is stored as CT: int (the column
+// itself), or int16_t / int8_t (the column minus the row index: Table 2's
+// 8- and 16-bit compression of column indices, decoded with one add).
+template <typename CT>
+__device__ __forceinline__ int column_of(CT stored, int row)
+{
+    if constexpr (sizeof(CT) == 4) return (int)stored;
+    else return row + (int)stored;
+}
+
+template <int U, typename CT = int>
 __device__ __forceinline__ double slice_value(int64_t s, int lane, const int* __restrict__ rowlen,
                                               const int* __restrict__ slice_len,
                                               const int64_t* __restrict__ slice_ptr,
                                               const int* __restrict__ perm,
-                                              const int* __restrict__ col,
+                                              const CT* __restrict__ col,
                                               const double* __restrict__ val,
                                               const double* __restrict__ x, int* row)
 {
@@ -29,8 +38,12 @@ __device__ __forceinline__ double slice_value(int64_t s, int lane, const int* __
     const int len = rowlen[p];
     const int L = slice_len[s];
     const int64_t q0 = slice_ptr[s] + lane;
-    const int* __restrict__ cp = col + q0;      // element k at cp[32 k] (k < 1025)
+    const CT* __restrict__ cp = col + q0;       // element k at cp[32 k]
     const double* __restrict__ vp = val + q0;
+    // offsets from the row index need the row before the gathers; 32-bit
+    // columns look it up after the loop, off the loads' critical path
+    int r = -1;
+    if constexpr (sizeof(CT) != 4) r = len >= 0 ? (perm ? perm[p] : (int)p) : -1;
     double acc = 0.0;
     for (int k = 0; k < L; k += U) {
         int c[U];
@@ -38,7 +51,7 @@ __device__ __forceinline__ double slice_value(int64_t s, int lane, const int* __
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool ok = k + u < len;
-            c[u] = ok ? __ldcs(cp + (k + u) * 32) : 0;
+            c[u] = ok ? column_of(__ldcs(cp + (k + u) * 32), r) : 0;
             a[u] = ok ? __ldcs(vp + (k + u) * 32) : 0.0;
         }
 #pragma unroll
@@ -47,21 +60,22 @@ __device__ __forceinline__ double slice_value(int64_t s, int lane, const int* __
         for (int u = 0; u < U; ++u)
             if (k + u < len) acc = fma(a[u], xv[u], acc);
     }
-    *row = len >= 0 ? (perm ? perm[p] : (int)p) : -1;
+    if constexpr (sizeof(CT) == 4) r = len >= 0 ? (perm ? perm[p] : (int)p) : -1;
+    *row = r;
     return acc;
 }
 
-template <int U>
+template <int U, typename CT = int>
 __device__ __forceinline__ void slice_rows(int64_t s, int lane, const int* __restrict__ rowlen,
                                            const int* __restrict__ slice_len,
                                            const int64_t* __restrict__ slice_ptr,
                                            const int* __restrict__ perm,
-                                           const int* __restrict__ col,
+                                           const CT* __restrict__ col,
                                            const double* __restrict__ val,
                                            const double* __restrict__ x, double* __restrict__ y)
 {
     int row;
-    const double v = slice_value<U>(s, lane, rowlen, slice_len, slice_ptr, perm, col, val, x, &row);
+    const double v = slice_value<U, CT>(s, lane, rowlen, slice_len, slice_ptr, perm, col, val, x, &row);
     if (row >= 0) y[row] = v;
 }
 
@@ -69,17 +83,17 @@ __device__ __forceinline__ void slice_rows(int64_t s, int lane, const int* __res
 // each (the same FMA chain per row as slice_value), with U elements of every
 // row in flight, so a warp overlaps the R slices' load latencies.  Slices
 // past n_slices are skipped.
-template <int U, int R>
+template <int U, int R, typename CT = int>
 __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, int lane,
                                                  const int* __restrict__ rowlen,
                                                  const int* __restrict__ slice_len,
                                                  const int64_t* __restrict__ slice_ptr,
                                                  const int* __restrict__ perm,
-                                                 const int* __restrict__ col,
+                                                 const CT* __restrict__ col,
                                                  const double* __restrict__ val,
                                                  const double* __restrict__ x, double* __restrict__ y)
 {
-    int len[R];
+    int len[R], row[R];
     int64_t q0[R];
     double acc[R];
     int L = 0;
@@ -87,9 +101,11 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
     for (int r = 0; r < R; ++r) {
         const int64_t s = s0 + r;
         const bool in = s < n_slices;
-        len[r] = in ? rowlen[s * 32 + lane] : -1;
+        const int64_t p = s * 32 + lane;
+        len[r] = in ? rowlen[p] : -1;
         q0[r] = in ? slice_ptr[s] + lane : 0;
         L = max(L, in ? slice_len[s] : 0);
+        row[r] = len[r] >= 0 ? (perm ? perm[p] : (int)p) : -1;
         acc[r] = 0.0;
     }
     for (int k = 0; k < L; k += U) {
@@ -100,7 +116,7 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool ok = k + u < len[r];
-                c[r][u] = ok ? __ldcs(col + q0[r] + (k + u) * 32) : 0;
+                c[r][u] = ok ? column_of(__ldcs(col + q0[r] + (k + u) * 32), row[r]) : 0;
                 a[r][u] = ok ? __ldcs(val + q0[r] + (k + u) * 32) : 0.0;
             }
 #pragma unroll
@@ -114,11 +130,8 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
                 if (k + u < len[r]) acc[r] = fma(a[r][u], xv[r][u], acc[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (len[r] < 0) continue;
-        const int64_t p = (s0 + r) * 32 + lane;
-        y[perm ? perm[p] : (int)p] = acc[r];
-    }
+    for (int r = 0; r < R; ++r)
+        if (row[r] >= 0) y[row[r]] = acc[r];
 }
 
 // FP32 or BF16 values, 32-bit columns or 16-bit offsets from rowbase[p],

@@ -91,12 +91,21 @@ def test_batch_of_prepared_matrices_runs_each_variant(batch_case):
     dev = list(dev) + [sp.DeviceCSR.from_host(A) for A in extra]
     xs = list(xs) + [synth.uniform_vector(A.n_cols, 77 + i).cuda() for i, A in enumerate(extra)]
     ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats]
-    kinds = ["sliced", "subwarp", "dynamic", ("sliced", 256), "latency", "compressed"]
+    kinds = ["sliced", "subwarp", "dynamic", ("sliced", 256), "latency", "compressed",
+             ("sliced", 0, 1), ("sliced", 0, 0, sp.VAL_BF16)]
     preps = []
     for i, dA in enumerate(dev):
         k = kinds[i % len(kinds)]
-        ch = sp.make_choice(k[0], block_nnz=k[1]) if isinstance(k, tuple) else sp.make_choice(k)
+        if isinstance(k, tuple):
+            k = tuple(k) + (0, 0, 0)[len(k) - 1:]
+            ch = sp.make_choice(k[0], block_nnz=k[1], index_bytes=k[2], value_type=k[3] or sp.VAL_F64)
+        else:
+            ch = sp.make_choice(k)
         preps.append(sp.spmv_prepare(dA, ch))
+    # a SLICED matrix with 8- or 16-bit column offsets, and one with BF16
+    # values (run by the batch in its FP64 form)
+    assert any(P.info().index_bytes < 4 for P in preps)
+    assert any(P.info().value_type == sp.VAL_BF16 for P in preps)
     B = sp.spmv_batch_create_prepared(preps)
     sp.spmv_batch_bind(B, xs, ys)
     sp.spmv_batch_run(B)

@@ -38,11 +38,14 @@ def _close(x, r, xo, ro):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-@pytest.mark.parametrize("variant", ["subwarp", "compressed", "dynamic", "stream", "sliced"])
+@pytest.mark.parametrize("variant", ["subwarp", "compressed", "dynamic", "stream", "sliced", "sliced_i8"])
 def test_cg_fp64_matches_oracle(variant, graph):
     A = synth.variable_coeff_laplacian_3d(14, seed=1)
     b = synth.uniform_vector(A.n_rows, 3)
-    x, r = _run(A, b, 60, sp.make_choice(variant), graph=graph)
+    # sliced_i8: the fused kernel with column offsets from the row index
+    # (this matrix's rows reach 196 columns from the diagonal: 16 bits)
+    ch = sp.make_choice("sliced", index_bytes=1) if variant == "sliced_i8" else sp.make_choice(variant)
+    x, r = _run(A, b, 60, ch, graph=graph)
     xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 60)
     _close(x, r, xo, ro)
     assert r[-1] < 1e-6 * r[0]

@@ -74,6 +74,8 @@ CHOICES = [
     ("sliced", {"items_per_warp": 1}), ("sliced", {"threads_per_row": 1}),
     ("sliced", {"threads_per_row": 2}), ("sliced", {"threads_per_row": 4}),
     ("sliced", {"threads_per_row": 4, "block_nnz": 256, "items_per_warp": 8}),
+    ("sliced", {"index_bytes": 1}), ("sliced", {"index_bytes": 2}),
+    ("sliced", {"index_bytes": 1, "threads_per_row": 4}), ("sliced", {"index_bytes": 1, "threads_per_row": 2}),
 ]
 
 
@@ -307,9 +309,23 @@ def test_sliced_layout_bit_exact(sigma, cap, name, A):
             _export(P, sp.EXPORT_SLICE_PERM, A.n_rows, torch.int32)
     col, val = oracle.sliced_fill(A, perm, rowlen, sptr)
     tot = int(sptr[-1])
+    assert info.index_bytes == 4
     if tot:
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_COL, tot, torch.int32), col)
         assert np.array_equal(_export(P, sp.EXPORT_SLICE_VAL, tot, torch.float64), val)
+        with pytest.raises(sp.SpmvError):
+            _export(P, sp.EXPORT_SLICE_DIAG, tot, torch.int16)
+    # the narrowest column form the rows allow (Table 2's 8/16-bit
+    # compression of column indices, reading O23)
+    d, reach, nb = oracle.sliced_diag(A, perm, rowlen, sptr)
+    Q = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, index_bytes=1,
+                                           items_per_warp=0 if cap == 1024 else cap))
+    assert Q.info().index_bytes == nb
+    if tot and nb < 4:
+        got = _export(Q, sp.EXPORT_SLICE_DIAG, tot, torch.int8 if nb == 1 else torch.int16)
+        assert np.array_equal(got.astype(np.int32), d)
+        with pytest.raises(sp.SpmvError):
+            _export(Q, sp.EXPORT_SLICE_COL, tot, torch.int32)
 
 
 @pytest.mark.parametrize("vt", [sp.VAL_F32, sp.VAL_BF16])
@@ -373,6 +389,31 @@ def test_sliced_low_precision_parity(vt, vkind, ipw, name, A):
     assert np.all(np.abs(y64.cpu().numpy() - ref64) <= RTOL * scale * 1.01)
 
 
+@pytest.mark.parametrize("reach,nb", [(127, 1), (128, 2), (-128, 2), (32767, 2), (32768, 4), (-32768, 4)])
+def test_sliced_index_width_at_its_boundaries(reach, nb):
+    """The diagonal plus one element at column row + reach in row 40000:
+    8-bit offsets up to 127, 16-bit up to 32767, then 32-bit columns; the
+    product is bit-exact with the oracle on integer data whatever the width."""
+    n = 80_000
+    r0 = 40_000
+    rows = [[i] for i in range(n)]
+    rows[r0] = sorted([r0, r0 + reach])
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.array([c for r in rows for c in r], np.int32)
+    g = np.random.default_rng(abs(reach))
+    va = g.integers(-9, 10, len(ci)).astype(np.float64)
+    A = synth.HostCSR(n, n, torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(va), "diag")
+    x = torch.from_numpy(g.integers(-20, 21, n).astype(np.float64))
+    dA = sp.DeviceCSR.from_host(A)
+    for R in (0, 1, 2):
+        P = sp.spmv_prepare(dA, sp.make_choice("sliced", threads_per_row=R, index_bytes=1))
+        assert P.info().index_bytes == nb
+        assert sp.spmv_prepare(dA, sp.make_choice("sliced", index_bytes=2)).info().index_bytes == max(nb, 2)
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        sp.spmv(P, x.cuda(), y)
+        assert np.array_equal(y.cpu().numpy(), oracle.spmv(A, x))
+
+
 def test_sliced_auto_window_and_long_rows():
     # regular rows: kept in order, one slice per warp; Zipf rows: sorted in
     # windows of 4096 and every row above 32 nonzeros computed from CSR
@@ -393,6 +434,10 @@ def test_sliced_auto_window_and_long_rows():
     for bad in (3, 8, 32):
         with pytest.raises(sp.SpmvError):
             sp.spmv_prepare(sp.DeviceCSR.from_host(S), sp.make_choice("sliced", threads_per_row=bad))
+    for bad in (dict(variant="sliced", index_bytes=3), dict(variant="compressed", index_bytes=2),
+                dict(variant="sliced", index_bytes=1, value_type=sp.VAL_F32)):
+        with pytest.raises(sp.SpmvError):
+            sp.spmv_prepare(sp.DeviceCSR.from_host(S), sp.make_choice(**bad))
     y, x = _run(Z, sp.make_choice("sliced"))
     _assert_close(y, Z, x)
     for bad in (2, 16, 8192):
