@@ -460,7 +460,7 @@ def _time_ms(fn, reps=10, warm=3):
 
 def run_cg(args):
     """Mixed precision: compressed and sliced SpMV throughput with FP32/BF16
-    values (FP32 or FP64 accumulation), and 300 CG iterations (sliced inner
+    values (FP32 or FP64 accumulation), and CG iterations (300 by default; sliced inner
     and exact SpMV) on the SPD 7-point Laplacian 128^3 (variable
     coefficients) with an FP64, FP32 or BF16 inner SpMV and FP64 residual
     recomputation; errors are against the FP64 GPU solve."""
@@ -497,7 +497,7 @@ def run_cg(args):
     dA = sp.DeviceCSR.from_host(A)
     b = synth.uniform_vector(A.n_rows, 1).cuda()
     exact = sp.spmv_prepare(dA, sp.make_choice("sliced"))
-    iters = 300
+    iters = args.iters
     xs = {}
     for name, vt, refine in (("f64", None, 0), ("f32", sp.VAL_F32, 10), ("bf16", sp.VAL_BF16, 10),
                              ("bf16_no_refine", sp.VAL_BF16, 0)):
@@ -642,6 +642,7 @@ def main():
                     help="VARIANT[:k=v,...]: run only this variant on --matrix (for ncu)")
     ap.add_argument("--matrix", default="stencil", choices=["stencil", "random", "zipf", "short"])
     ap.add_argument("--cg", action="store_true", help="mixed-precision SpMV and CG report")
+    ap.add_argument("--iters", type=int, default=300, help="CG iterations of --cg")
     ap.add_argument("--batch", action="store_true", help="batched persistent SpMV report")
     ap.add_argument("--features", action="store_true", help="feature extraction report")
     args = ap.parse_args()
