@@ -567,9 +567,10 @@ def run_features(args):
 
 
 def run_batch(args):
-    """512 uneven matrices: one launch per matrix with each matrix's own
-    selected variant, against one persistent launch that runs every matrix
-    with its selected variant (plain, graph, autotuned)."""
+    """512 uneven matrices, each with the variant the learned selector picks:
+    one launch per matrix with that variant, against one persistent launch
+    over all of them (plain, graph, autotuned), in which every matrix runs in
+    the sliced layout (spmv_batch_create_prepared)."""
     import numpy as np
     import torch
     import paper_1511_02494_gb300 as sp
@@ -598,8 +599,8 @@ def run_batch(args):
         for P, x, y in zip(preps, xs, ys):
             sp.spmv(P, x, y)
     ms_sep = _time_ms(per_matrix, reps=5, warm=2)
-    # one persistent launch, each matrix with its selected variant (SLICED as
-    # slices, the others as CSR rows with their prepared lanes per row)
+    # one persistent launch over the prepared matrices (each in the sliced
+    # layout: its own when it was prepared as SLICED)
     B = sp.spmv_batch_create_prepared(preps)
     sp.spmv_batch_bind(B, xs, ys)
     ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)

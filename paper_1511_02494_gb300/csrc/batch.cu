@@ -274,15 +274,18 @@ spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t 
             return fail(SPMV_ERR_INVALID_ARG, "prepared on another device");
         }
         const spmv_csr_t& A = Pm->A;
-        // imbalance variants (MERGE, DYNAMIC) run as length-sorted slices: a
-        // warp of CSR rows would run as many DFMAs as its longest row; SLICED
-        // with FP32/BF16 values runs as its FP64 form (the batch sums FP64)
-        const bool lp_sliced = Pm->c.variant == SPMV_V7_SLICED && Pm->c.value_type != SPMV_VAL_F64;
-        if (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC || lp_sliced) {
+        // Inside the one launch the matrices share the FP64 pipe, so every
+        // matrix runs in the sliced layout (one DFMA per element, no
+        // reductions): a matrix prepared for another variant, or for SLICED
+        // with FP32/BF16 values (the batch sums FP64), gets a sliced form
+        // that the batch prepares (automatic layout) and owns.  Measured on
+        // the 512-matrix set: 0.49 ms against 0.60 ms with the CSR variants
+        // run as CSR rows of T lanes.
+        if (Pm->c.variant != SPMV_V7_SLICED || Pm->c.value_type != SPMV_VAL_F64) {
             spmv_choice_t c{};
             c.variant = SPMV_V7_SLICED;
             c.cls = -1;
-            c.block_nnz = lp_sliced ? 0 : 256;
+            c.block_nnz = 0;
             spmv_prepared* Q = nullptr;
             st = spmv_prepare(&A, &c, 1, &Q, stream);
             if (st != SPMV_OK) { spmv_batch_free(B); return st; }
