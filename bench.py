@@ -59,6 +59,22 @@ def _traffic(variant: str, matrix: str):
         return None
 
 
+def _host() -> str:
+    """CPU of the host the oracle runs on: architecture, model, core count."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model} x{os.cpu_count()}".replace("  ", " ")
+
+
 def _max_over_ranks(v: float, ws: int, device) -> float:
     """The slowest rank's value (the job's time); identity on one rank."""
     if ws <= 1:
@@ -200,7 +216,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample, "cores": 1},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": _host()},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -405,7 +421,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         gbs, sample, t = cpu_oracle_rate(mats, args.cpu_seconds, 1.0 / 16)
         line["cpu_baseline"] = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1,
-                                "kind": "oracle", "sample": sample}
+                                "kind": "oracle", "sample": sample, "host": _host()}
     for r in per:
         r["P"].free()
         r["P0"].free()

@@ -183,7 +183,9 @@ def soft_targets(times: np.ndarray, beta: float) -> np.ndarray:
 def train(z: np.ndarray, targets: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000, lr=3e-3,
           wd=1e-4, seed=0, log=print):
     """Full-batch Adam with the library's loss/gradient and Adam kernels;
-    targets are integer labels [n] or target distributions [n][k]."""
+    targets are integer labels [n] or target distributions [n][k].  Returns
+    the parameters, the loss history and the steps' elapsed time on the
+    stream (ms, CUDA events; host launch gaps included)."""
     p = torch.from_numpy(init_params(h1, h2, k, seed)).cuda()
     g = torch.zeros_like(p)
     m = torch.zeros_like(p)
@@ -193,6 +195,9 @@ def train(z: np.ndarray, targets: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000,
     soft = targets.ndim == 2
     dl = torch.from_numpy(np.ascontiguousarray(targets, np.float32 if soft else np.int32)).cuda()
     hist = []
+    gpu_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
     for step in range(1, steps + 1):
         if soft:
             sp.spmv_mlp_loss_grad_soft(p, h1, h2, k, dz, dl, g, loss)
@@ -200,9 +205,15 @@ def train(z: np.ndarray, targets: np.ndarray, h1=64, h2=64, k=N_VAR, steps=3000,
             sp.spmv_mlp_loss_grad(p, h1, h2, k, dz, dl, g, loss)
         sp.spmv_mlp_adam(p, g, m, v, step, lr=lr, weight_decay=wd)
         if step % 500 == 0 or step == 1:
-            hist.append((step, float(loss.item())))
+            e1.record()
+            hist.append((step, float(loss.item())))  # synchronizes
+            gpu_ms += e0.elapsed_time(e1)
             log(f"step {step} loss {hist[-1][1]:.4f}")
-    return p.cpu().numpy(), hist
+            e0.record()
+    e1.record()
+    e1.synchronize()
+    gpu_ms += e0.elapsed_time(e1)
+    return p.cpu().numpy(), hist, gpu_ms
 
 
 def logits_of(params, mean, istd, vec, h1, h2, k):
@@ -307,14 +318,14 @@ def main():
     z_f = ((vec - mean_f) * istd_f).astype(np.float32)
     beta_scores = {}
     for beta in args.betas:
-        pf, _ = train(z_f[fit], soft_targets(d["times"][fit], beta), h1, h2, k, steps=args.steps,
+        pf, _, _ = train(z_f[fit], soft_targets(d["times"][fit], beta), h1, h2, k, steps=args.steps,
                       log=lambda *_: None)
         lg = logits_of(pf, mean_f, istd_f, vec[val], h1, h2, k)
         t_val = d["times"][val]
         beta_scores[str(beta)] = geomean(t_val[np.arange(len(val)), lg.argmax(1)] / t_val.min(1))
         print(f"beta {beta}: validation slowdown {beta_scores[str(beta)]:.4f}", flush=True)
     beta = float(min(args.betas, key=lambda b_: beta_scores[str(b_)]))
-    params, hist = train(z[tr], soft_targets(d["times"][tr], beta), h1, h2, k, steps=args.steps)
+    params, hist, train_ms = train(z[tr], soft_targets(d["times"][tr], beta), h1, h2, k, steps=args.steps)
     # fallback margin: smallest value whose training slowdown is within 0.5 %
     # of the best any margin achieves
     lg = logits_of(params, mean, istd, vec[tr], h1, h2, k)
@@ -332,6 +343,8 @@ def main():
               "test": evaluate(d, params, mean, istd, mu, h1, h2, k, test),
               "min_margin": mu, "loss_history": hist, "variants": list(sp.VARIANTS),
               "beta": beta, "beta_validation_slowdown": beta_scores,
+              "training_stream_ms": round(train_ms, 2),
+              "training_ms_per_step": round(train_ms / max(args.steps, 1), 4),
               "network": [16, h1, h2, k]}
     with open(os.path.join(args.out, "selector_report.json"), "w") as f:
         json.dump(report, f, indent=1)
