@@ -14,7 +14,7 @@
 // last block to finish (an atomic ticket, no waiting) adds the partials in
 // block order and updates the scalars.
 //
-// With a SLICED inner matrix (no rows above 1024 nonzeros) q = A p and p.q
+// With a SLICED inner matrix without long rows (none above its cap) q = A p and p.q
 // are one kernel, and when that matrix sums in FP32 the p update also writes
 // p's FP32 copy, so no separate conversion of p runs per iteration.
 #include <math.h>
