@@ -307,6 +307,14 @@ spmv_status spmv_profile(const spmv_csr_t *A, const double *x, int32_t reps,
 spmv_status spmv_gather_probe(const spmv_csr_t *A, const double *x, uint64_t *sum,
                               spmv_stream_t stream);
 
+/* Self-test of failure detection without a GPU fault: one warp waits on a
+ * shared-memory mbarrier with the bounded wait (a %globaltimer limit) that the
+ * STREAM and MERGE pipelines use.  arrive != 0: the barrier's one arrival is
+ * made first and the call returns SPMV_OK; arrive == 0: nothing arrives, the
+ * wait gives up after limit_ns (1..2e9 nanoseconds) and the call returns
+ * SPMV_ERR_TIMEOUT with the device context intact.  Synchronizes `stream`. */
+spmv_status spmv_wait_check(int64_t limit_ns, int32_t arrive, spmv_stream_t stream);
+
 /* ---- selection (Sections 3.1-3.3) ----------------------------------------- */
 spmv_thresholds_t spmv_default_thresholds(void);
 

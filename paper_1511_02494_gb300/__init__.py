@@ -119,6 +119,11 @@ def spmv_profile(A: DeviceCSR, x, reps: int = 5, stream=None) -> Profile:
     return out
 
 
+def spmv_wait_check(limit_ns: int, arrive: bool, stream=None) -> None:
+    """Bounded-wait self-test; raises SpmvError (TIMEOUT) when nothing arrives."""
+    _check(lib().spmv_wait_check(int(limit_ns), 1 if arrive else 0, _stream(stream)))
+
+
 def spmv_gather_probe(A: DeviceCSR, x, out, stream=None) -> None:
     """out (device, one int64 / uint64) = sum modulo 2^64 of the bit patterns
     of x over A's column indices; its time is the cost of A's gathers of x

@@ -267,4 +267,53 @@ cudaError_t launch_window(const spmv_csr_t& A, int block_nnz, const int32_t* blo
     }
 }
 
+namespace {
+
+// Self-test of the bounded wait the pipelined kernels use: one warp waits on
+// a shared-memory mbarrier that expects one arrival.  arrive != 0: thread 0
+// arrives first and the wait completes; arrive == 0: nothing arrives, the
+// wait gives up after limit_ns and thread 0 records the timeout.  No copy is
+// in flight, so the kernel simply returns.
+__global__ void k_wait_check(uint64_t limit_ns, int arrive, unsigned* __restrict__ status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) ptx::mbar_arrive(&bar);
+    const bool done = ptx::wait_bounded(&bar, 0u, limit_ns);
+    if (!done && threadIdx.x == 0) *status = 1u;
+}
+
+}  // namespace
 }  // namespace spmvlib
+
+using namespace spmvlib;
+
+extern "C" spmv_status spmv_wait_check(int64_t limit_ns, int32_t arrive, spmv_stream_t stream)
+{
+    clear_error();
+    if (limit_ns <= 0 || limit_ns > 2000000000ll)
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_wait_check: limit_ns must be in 1..2e9");
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned* d = nullptr;
+    unsigned h = 0;
+    SPMV_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(unsigned), s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        k_wait_check<<<1, 32, 0, s>>>((uint64_t)limit_ns, arrive ? 1 : 0, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_wait_check");
+    if (h) return fail(SPMV_ERR_TIMEOUT, "spmv_wait_check: the bounded wait gave up, as the test asks");
+    return SPMV_OK;
+}

@@ -149,6 +149,7 @@ def test_gpu_calls_fail_loudly_without_gpu(lib):
     ch = sp.make_choice("scalar")
     assert lib.spmv_prepare(C.byref(desc), C.byref(ch), 1, C.byref(h), None) == 5
     assert not h.value
+    assert lib.spmv_wait_check(1000, 0, None) == 5
 
 
 def test_invalid_arguments_rejected_before_device_use(lib):
@@ -164,3 +165,5 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert lib.spmv_prepare(C.byref(desc), C.byref(bad), 0, C.byref(h), None) == 3
     bad = sp.make_choice("merge", items_per_warp=100)
     assert lib.spmv_prepare(C.byref(desc), C.byref(bad), 0, C.byref(h), None) == 1
+    for limit in (0, -5, 3_000_000_000):
+        assert lib.spmv_wait_check(limit, 0, None) == 1
