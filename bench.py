@@ -59,6 +59,16 @@ def _traffic(variant: str, matrix: str):
         return None
 
 
+def _models(sp):
+    """The committed selector networks: the first level (variant) and the
+    second level (SLICED's launch configuration), when present."""
+    data = os.path.join(ROOT, "paper_1511_02494_gb300", "data")
+    first, second = os.path.join(data, "selector_mlp.bin"), os.path.join(data, "selector_sliced_mlp.bin")
+    model = sp.spmv_model_load(first) if os.path.exists(first) else None
+    sub = sp.spmv_model_load(second) if model is not None and os.path.exists(second) else None
+    return model, sub
+
+
 def _host() -> str:
     """CPU of the host the oracle runs on: architecture, model, core count."""
     import platform
@@ -261,8 +271,7 @@ def run_ours(args):
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    model_path = os.path.join(ROOT, "paper_1511_02494_gb300", "data", "selector_mlp.bin")
-    model = sp.spmv_model_load(model_path) if os.path.exists(model_path) else None
+    model, sub = _models(sp)
     per = []
     candidates = [("scalar", {}), ("subwarp", {}), ("stream", {}), ("merge", {}),
                   ("dynamic", {}), ("latency", {}), ("compressed", {}), ("sliced", {})]
@@ -278,7 +287,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         f = sp.spmv_features(dA)
-        ch_model = sp.spmv_select_model(f, model) if model is not None else None
+        ch_model = sp.spmv_select_model_refined(f, model, sub) if model is not None else None
         rec["features_ms"] = (time.perf_counter() - t0) * 1e3
         # profiling runs + rule (Section 3.2.1)
         t0 = time.perf_counter()
@@ -295,6 +304,9 @@ def run_ours(args):
         P = sp.spmv_prepare(dA, ch)
         rec["prepare_ms"] = (time.perf_counter() - t0) * 1e3
         rec["selected_min_bytes"] = P.info().min_bytes
+        inf = P.info()
+        rec["launch"] = {"threads_per_row": inf.threads_per_row, "block_nnz": inf.block_nnz,
+                         "items_per_warp": inf.items_per_warp}
         # every variant, for the "best possible" comparison
         times = {}
         for v, kw in ([] if args.no_variant_sweep else candidates):
@@ -375,7 +387,7 @@ def run_ours(args):
     matrices = []
     for r, km, s in zip(per, kern_ms, speedups):
         matrices.append({
-            "matrix": r["matrix"], "class": r["class"], "variant": r["variant"],
+            "matrix": r["matrix"], "class": r["class"], "variant": r["variant"], "launch": r["launch"],
             "variant_rule": r["variant_rule"],
             "best_variant": r["best_variant"], "ms": round(km, 5),
             "gbs": round(r["min_bytes"] / (km * 1e-3) / 1e9, 1),
@@ -396,8 +408,9 @@ def run_ours(args):
         "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.scale == 0 else WORKLOAD + f" (rows / 2^{args.scale})",
-                   "selection": ("learned selector on Table 1 features" if model is not None
-                                 else "profiling-based rule (Section 3.2.1)"),
+                   "selection": (("learned selector on Table 1 features" +
+                                  (", two levels (variant, then SLICED launch configuration)" if sub else ""))
+                                 if model is not None else "profiling-based rule (Section 3.2.1)"),
                    "l2": "no flush: every matrix (>= 369 MB) is larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "frac_of_hbm_peak": round(value / peak, 4),
@@ -598,18 +611,16 @@ def run_batch(args):
     xs = [synth.uniform_vector(A.n_cols, i).cuda() for i, A in enumerate(mats)]
     ys = [torch.empty(A.n_rows, dtype=torch.float64, device="cuda") for A in mats]
     total_bytes = sum(A.min_bytes() for A in mats)
-    model_path = os.path.join(ROOT, "paper_1511_02494_gb300", "data", "selector_mlp.bin")
-    model = sp.spmv_model_load(model_path) if os.path.exists(model_path) else None
+    model, sub = _models(sp)
     t0 = time.perf_counter()
-    choices = []
+    sel = []
     for dA in dev:
         f = sp.spmv_features(dA)
-        if model is not None:
-            choices.append(sp.spmv_select_model(f, model).variant)
-        else:
-            choices.append(sp.VARIANT_IDS["subwarp"])
+        sel.append(sp.spmv_select_model_refined(f, model, sub) if model is not None
+                   else sp.make_choice("subwarp"))
     select_s = time.perf_counter() - t0
-    preps = [sp.spmv_prepare(dA, sp.make_choice(int(v)), trusted=True) for dA, v in zip(dev, choices)]
+    choices = [c.variant for c in sel]
+    preps = [sp.spmv_prepare(dA, c, trusted=True) for dA, c in zip(dev, sel)]
 
     def per_matrix():
         for P, x, y in zip(preps, xs, ys):
@@ -629,7 +640,8 @@ def run_batch(args):
     out = {"mode": "batched", "matrices": len(mats), "nnz": int(sum(A.nnz for A in mats)),
            "rows_range": [min(A.n_rows for A in mats), max(A.n_rows for A in mats)],
            "min_bytes": total_bytes,
-           "selection": "learned selector" if model is not None else "sub-warp default",
+           "selection": (("learned selector" + (", two levels" if sub else "")) if model is not None
+                         else "sub-warp default"),
            "selection_s": round(select_s, 3),
            "variant_counts": {sp.VARIANTS[v]: int(c) for v, c in
                               zip(*np.unique(np.array(choices), return_counts=True))},

@@ -360,6 +360,14 @@ spmv_status spmv_model_save(const spmv_model_t *m, const char *path);
 spmv_status spmv_model_load(const char *path, spmv_model_t **out);
 void spmv_model_free(spmv_model_t *m);
 
+/* Attaches launch parameters to each output of m (host [k][3]: for output o,
+ * threads_per_row, block_nnz, items_per_warp of the output's variant, each
+ * as in spmv_choice_t), making m a second-level model that chooses among one
+ * variant's launch configurations.  SPMV_ERR_MODEL when a triple is not a
+ * valid choice for its variant.  spmv_model_save then writes the file as
+ * "SPMVMLP2" with the int32 table appended; spmv_model_load reads both. */
+spmv_status spmv_model_set_launch(spmv_model_t *m, const int32_t *launch);
+
 /* Logits of one host 16-vector (host computation, k outputs). */
 spmv_status spmv_model_logits(const spmv_model_t *m, const float *vec16, float *logits);
 
@@ -370,6 +378,16 @@ spmv_status spmv_model_logits(const spmv_model_t *m, const float *vec16, float *
 spmv_status spmv_select_model(const spmv_features_t *f, const spmv_model_t *m,
                               const spmv_profile_t *p, const spmv_thresholds_t *th,
                               spmv_choice_t *out);
+
+/* Two levels (the multi-level selection the paper proposes as future work):
+ * spmv_select_model with m, then, when every output of sub names the variant
+ * chosen, sub's forward on the same features picks that variant's launch
+ * parameters (threads_per_row, block_nnz, items_per_warp of the choice).
+ * sub may be NULL (first level only).  A choice from a model with launch
+ * parameters carries them; a profile fallback carries none.  Host-only. */
+spmv_status spmv_select_model_refined(const spmv_features_t *f, const spmv_model_t *m,
+                                      const spmv_model_t *sub, const spmv_profile_t *p,
+                                      const spmv_thresholds_t *th, spmv_choice_t *out);
 
 /* Device forward for n host-layout 16-vectors v (device, [n][16]) into
  * logits (device, [n][k]); params, mean16, istd16 are device arrays.

@@ -368,6 +368,23 @@ def spmv_model_free(m: Model) -> None:
     m.free()
 
 
+def spmv_model_set_launch(m: Model, launch) -> None:
+    import numpy as np
+    launch = np.ascontiguousarray(launch, dtype=np.int32)
+    _check(lib().spmv_model_set_launch(m.handle, launch.ctypes.data_as(C.c_void_p)))
+
+
+def spmv_select_model_refined(features: Features, model: Model, sub: Model | None = None,
+                              profile: Profile | None = None,
+                              thresholds: Thresholds | None = None) -> Choice:
+    out = Choice()
+    _check(lib().spmv_select_model_refined(C.byref(features), model.handle,
+                                           sub.handle if sub is not None else None,
+                                           C.byref(profile) if profile else None,
+                                           C.byref(thresholds) if thresholds else None, C.byref(out)))
+    return out
+
+
 def spmv_model_logits(m: Model, vec16, k: int):
     import numpy as np
     v, pv = _fptr(vec16)

@@ -115,6 +115,9 @@ def declare(lib):
         "spmv_model_save": (I32, [P, C.c_char_p]),
         "spmv_model_load": (I32, [C.c_char_p, C.POINTER(P)]),
         "spmv_model_free": (None, [P]),
+        "spmv_model_set_launch": (I32, [P, P]),
+        "spmv_select_model_refined": (I32, [C.POINTER(Features), P, P, C.POINTER(Profile),
+                                            C.POINTER(Thresholds), C.POINTER(Choice)]),
         "spmv_model_logits": (I32, [P, P, P]),
         "spmv_select_model": (I32, [C.POINTER(Features), P, C.POINTER(Profile),
                                     C.POINTER(Thresholds), C.POINTER(Choice)]),

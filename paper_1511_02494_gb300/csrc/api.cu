@@ -297,6 +297,10 @@ spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
     }
 }
 
+}  // namespace
+
+namespace spmvlib {
+
 spmv_status check_choice(const spmv_choice_t* c)
 {
     if (c->variant < 0 || c->variant >= SPMV_NUM_VARIANTS)
@@ -338,6 +342,10 @@ spmv_status check_choice(const spmv_choice_t* c)
         return fail(SPMV_ERR_UNSUPPORTED, "FP32 accumulation needs COMPRESSED or SLICED with FP32 or BF16 values");
     return SPMV_OK;
 }
+
+}  // namespace spmvlib
+
+namespace {
 
 spmv_status run_impl(const spmv_prepared_t* P, const double* x, double* y, cudaStream_t s)
 {

@@ -39,6 +39,7 @@ spmv_status current_device(DeviceInfo* out);
 
 // ---- matrix checks on the host side of the ABI ----------------------------------
 spmv_status check_csr_args(const spmv_csr_t* A);
+spmv_status check_choice(const spmv_choice_t* c);
 
 // ---- the prepared object ----------------------------------------------------------
 }  // namespace spmvlib

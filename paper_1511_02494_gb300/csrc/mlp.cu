@@ -26,6 +26,10 @@ struct spmv_model {
     std::vector<float> params;
     std::vector<int32_t> variants;
     float min_margin = 0.f;
+    // optional launch parameters per output: threads_per_row, block_nnz,
+    // items_per_warp (a second-level model choosing among one variant's
+    // launch configurations); empty when the model names variants only
+    std::vector<int32_t> launch;
 };
 
 namespace spmvlib {
@@ -308,6 +312,18 @@ bool shape_ok(int h1, int h2, int k, int max_h)
 }
 
 const char kMagic[8] = {'S', 'P', 'M', 'V', 'M', 'L', 'P', '1'};
+const char kMagic2[8] = {'S', 'P', 'M', 'V', 'M', 'L', 'P', '2'};  // + launch parameters
+
+// output o's launch parameters as a choice of its variant (validated)
+spmv_status launch_choice(const spmv_model_t* m, int o, spmv_choice_t* c)
+{
+    c->variant = m->variants[o];
+    c->threads_per_row = m->launch[3 * o];
+    c->block_nnz = m->launch[3 * o + 1];
+    c->items_per_warp = m->launch[3 * o + 2];
+    c->value_type = SPMV_VAL_F64;
+    return check_choice(c);
+}
 
 }  // namespace
 
@@ -339,6 +355,23 @@ spmv_status spmv_model_create(int32_t h1, int32_t h2, int32_t k, const float* me
     return SPMV_OK;
 }
 
+spmv_status spmv_model_set_launch(spmv_model_t* m, const int32_t* launch)
+{
+    clear_error();
+    if (!m || !launch) return fail(SPMV_ERR_INVALID_ARG, "spmv_model_set_launch: NULL argument");
+    std::vector<int32_t> keep;
+    keep.swap(m->launch);
+    m->launch.assign(launch, launch + 3 * m->k);
+    for (int o = 0; o < m->k; ++o) {
+        spmv_choice_t c = {};
+        if (launch_choice(m, o, &c) != SPMV_OK) {
+            m->launch.swap(keep);
+            return fail(SPMV_ERR_MODEL, "launch parameters not valid for the output's variant");
+        }
+    }
+    return SPMV_OK;
+}
+
 spmv_status spmv_model_save(const spmv_model_t* m, const char* path)
 {
     clear_error();
@@ -346,11 +379,13 @@ spmv_status spmv_model_save(const spmv_model_t* m, const char* path)
     FILE* f = fopen(path, "wb");
     if (!f) return fail(SPMV_ERR_INVALID_ARG, std::string("cannot open ") + path);
     const int32_t hdr[3] = {m->h1, m->h2, m->k};
-    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 3, f) == 3 &&
+    const bool v2 = !m->launch.empty();
+    bool ok = fwrite(v2 ? kMagic2 : kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 3, f) == 3 &&
               fwrite(m->mean, 4, 16, f) == 16 && fwrite(m->istd, 4, 16, f) == 16 &&
               fwrite(m->params.data(), 4, m->params.size(), f) == m->params.size() &&
               fwrite(m->variants.data(), 4, m->variants.size(), f) == m->variants.size() &&
               fwrite(&m->min_margin, 4, 1, f) == 1;
+    if (v2) ok = ok && fwrite(m->launch.data(), 4, m->launch.size(), f) == m->launch.size();
     ok = (fclose(f) == 0) && ok;
     return ok ? SPMV_OK : fail(SPMV_ERR_INVALID_ARG, std::string("write failed: ") + path);
 }
@@ -366,9 +401,10 @@ spmv_status spmv_model_load(const char* path, spmv_model_t** out)
     int32_t hdr[3];
     float mean[16], istd[16], margin = 0.f;
     std::vector<float> params;
-    std::vector<int32_t> variants;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+    std::vector<int32_t> variants, launch;
+    bool ok = fread(magic, 1, 8, f) == 8 && (memcmp(magic, kMagic, 8) == 0 || memcmp(magic, kMagic2, 8) == 0) &&
               fread(hdr, 4, 3, f) == 3 && shape_ok(hdr[0], hdr[1], hdr[2], kMaxH);
+    const bool v2 = ok && memcmp(magic, kMagic2, 8) == 0;
     if (ok) {
         params.resize((size_t)n_params(hdr[0], hdr[1], hdr[2]));
         variants.resize((size_t)hdr[2]);
@@ -376,13 +412,23 @@ spmv_status spmv_model_load(const char* path, spmv_model_t** out)
              fread(params.data(), 4, params.size(), f) == params.size() &&
              fread(variants.data(), 4, variants.size(), f) == variants.size() &&
              fread(&margin, 4, 1, f) == 1;
+        if (ok && v2) {
+            launch.resize(3 * (size_t)hdr[2]);
+            ok = fread(launch.data(), 4, launch.size(), f) == launch.size();
+        }
         char extra;
         if (ok && fread(&extra, 1, 1, f) != 0) ok = false;  // trailing bytes: corrupt
     }
     fclose(f);
     if (!ok) return fail(SPMV_ERR_MODEL, std::string("corrupt or truncated model file ") + path);
-    return spmv_model_create(hdr[0], hdr[1], hdr[2], mean, istd, params.data(), variants.data(),
-                             margin, out);
+    spmv_status st = spmv_model_create(hdr[0], hdr[1], hdr[2], mean, istd, params.data(), variants.data(),
+                                       margin, out);
+    if (st != SPMV_OK || !v2) return st;
+    if ((st = spmv_model_set_launch(*out, launch.data())) != SPMV_OK) {
+        spmv_model_free(*out);
+        *out = nullptr;
+    }
+    return st;
 }
 
 void spmv_model_free(spmv_model_t* m) { delete m; }
@@ -411,6 +457,10 @@ spmv_status spmv_select_model(const spmv_features_t* f, const spmv_model_t* m,
         if (o != best && logits[o] > second) second = logits[o];
     spmv_choice_t c = {};
     c.variant = m->variants[best];
+    if (!m->launch.empty()) {
+        spmv_status st = launch_choice(m, best, &c);
+        if (st != SPMV_OK) return st;
+    }
     c.cls = -1;
     c.value_type = SPMV_VAL_F64;
     c.margin = logits[best] - second;
@@ -421,10 +471,27 @@ spmv_status spmv_select_model(const spmv_features_t* f, const spmv_model_t* m,
         if (st != SPMV_OK) return st;
         c.cls = cls;
         c.variant = spmv_class_variant(cls);
+        c.threads_per_row = c.block_nnz = c.items_per_warp = 0;
         c.used_fallback = 1;
         c.source = 1;
     }
     *out = c;
+    return SPMV_OK;
+}
+
+spmv_status spmv_select_model_refined(const spmv_features_t* f, const spmv_model_t* m,
+                                      const spmv_model_t* sub, const spmv_profile_t* p,
+                                      const spmv_thresholds_t* th, spmv_choice_t* out)
+{
+    spmv_status st = spmv_select_model(f, m, p, th, out);
+    if (st != SPMV_OK || !sub || sub->launch.empty()) return st;
+    for (int o = 0; o < sub->k; ++o)
+        if (sub->variants[o] != out->variant) return SPMV_OK;  // another variant: first level only
+    spmv_choice_t c2;
+    if ((st = spmv_select_model(f, sub, nullptr, nullptr, &c2)) != SPMV_OK) return st;
+    out->threads_per_row = c2.threads_per_row;
+    out->block_nnz = c2.block_nnz;
+    out->items_per_warp = c2.items_per_warp;
     return SPMV_OK;
 }
 

@@ -271,6 +271,124 @@ def evaluate(d, params, mean, istd, mu, h1, h2, k, idx):
     }
 
 
+# Launch configurations of SLICED among which the second-level network
+# chooses (threads_per_row = slices per warp, block_nnz = sort window,
+# items_per_warp = row-length cap; 0 = the prepare step's own rule)
+SLICED_CONFIGS = (
+    (0, 0, 0),        # the structural rules
+    (1, 1, 1024),     # rows in order
+    (4, 1, 1024),     # rows in order, four slices per warp
+    (1, 4096, 32),    # sorted, cap 32
+    (4, 4096, 32),    # sorted, cap 32, four slices per warp
+    (1, 256, 1024),   # sorted in windows of 256
+    (1, 4096, 64),    # sorted, cap 64
+    (1, 4096, 1024),  # sorted, cap 1024
+    (2, 1, 1024),     # rows in order, two slices per warp
+)
+
+
+def time_choice(dA, ch, x, y, budget_ms: float = 25.0):
+    P = sp.spmv_prepare(dA, ch, trusted=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp.spmv(P, x, y)  # warm-up
+    ts = []
+    for _ in range(4):
+        e0.record()
+        sp.spmv(P, x, y)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        if ts[0] >= budget_ms:
+            break
+    P.free()
+    return float(np.median(ts))
+
+
+def sliced_dataset(d, out_path: str, log=print):
+    """Times every SLICED launch configuration on the stored matrices
+    (regenerated from their seeds), in the stored order."""
+    if os.path.exists(out_path):
+        s = np.load(out_path)
+        if np.array_equal(s["seed"], d["seed"]) and s["times"].shape[1] == len(SLICED_CONFIGS):
+            return s["times"]
+    times = np.empty((len(d["seed"]), len(SLICED_CONFIGS)))
+    t0 = time.time()
+    for row, i in enumerate(d["seed"]):
+        family, n_rows = matrix_spec(int(i))
+        A = synth.family_matrix(family, n_rows, seed=int(i), device="cuda")
+        dA = sp.DeviceCSR(A.n_rows, A.n_cols, A.rowptr.contiguous(), A.colind.contiguous(),
+                          A.val.contiguous())
+        x = synth.uniform_vector(A.n_cols, int(i), device="cuda")
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        for j, (r, sigma, cap) in enumerate(SLICED_CONFIGS):
+            ch = sp.make_choice("sliced", threads_per_row=r, block_nnz=sigma, items_per_warp=cap)
+            times[row, j] = time_choice(dA, ch, x, y)
+        del dA, A, x, y
+        if (row + 1) % 200 == 0:
+            torch.cuda.empty_cache()
+            log(f"{row + 1}/{len(d['seed'])} matrices, {time.time() - t0:.0f} s")
+    np.savez(out_path, seed=d["seed"], times=times, configs=np.array(SLICED_CONFIGS, np.int32))
+    return times
+
+
+def train_second_level(args, d, first):
+    """The second level of selection: a 16-64-64-C network choosing SLICED's
+    launch configuration from the same features, trained like the first
+    level (cost-sensitive targets, beta on a validation quarter), saved with
+    its launch table; the report compares it with the structural rules."""
+    tcfg = sliced_dataset(d, os.path.join(args.out, "sliced_dataset.npz"))
+    seeds, vec = d["seed"], d["vec"].astype(np.float32)
+    tr, te = np.where(seeds % 5 != 0)[0], np.where(seeds % 5 == 0)[0]
+    fit, val = np.where((seeds % 5 != 0) & (seeds % 5 != 4))[0], np.where(seeds % 5 == 4)[0]
+    h1, h2, k = 64, 64, len(SLICED_CONFIGS)
+
+    def norm(idx):
+        mean = vec[idx].mean(0).astype(np.float32)
+        sd = vec[idx].std(0)
+        return mean, np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 0.0).astype(np.float32)
+
+    mean_f, istd_f = norm(fit)
+    scores = {}
+    for beta in args.betas:
+        pf, _, _ = train(((vec - mean_f) * istd_f)[fit], soft_targets(tcfg[fit], beta), h1, h2, k,
+                         steps=args.steps, log=lambda *_: None)
+        lg = logits_of(pf, mean_f, istd_f, vec[val], h1, h2, k)
+        scores[str(beta)] = geomean(tcfg[val, lg.argmax(1)] / tcfg[val].min(1))
+    beta = float(min(args.betas, key=lambda b_: scores[str(b_)]))
+    mean, istd = norm(tr)
+    params, _, train_ms = train(((vec - mean) * istd)[tr], soft_targets(tcfg[tr], beta), h1, h2, k,
+                                steps=args.steps, log=lambda *_: None)
+    sl = sp.VARIANT_IDS["sliced"]
+    model = sp.spmv_model_create(h1, h2, k, mean, istd, params, [sl] * k, 0.0)
+    sp.spmv_model_set_launch(model, np.array(SLICED_CONFIGS, np.int32))
+    sp.spmv_model_save(model, os.path.join(args.out, "selector_sliced_mlp.bin"))
+    pick = logits_of(params, mean, istd, vec, h1, h2, k).argmax(1)
+    # two levels against the best over every variant and every SLICED configuration
+    first_pick = np.array([int(np.argmax(sp.spmv_model_logits(first, v, N_VAR))) for v in vec])
+    var_t = d["times"]
+    one = var_t[np.arange(len(vec)), first_pick]
+    two = np.where(first_pick == sl, tcfg[np.arange(len(vec)), pick], one)
+    overall = np.minimum(var_t.min(1), tcfg.min(1))
+    rep = {"configs": [list(c) for c in SLICED_CONFIGS], "beta": beta, "beta_validation_slowdown": scores,
+           "training_stream_ms": round(train_ms, 2)}
+    for name, idx in (("train", tr), ("test", te)):
+        best = tcfg[idx].min(1)
+        rep[name] = {
+            "matrices": int(len(idx)),
+            "best_config_counts": np.bincount(tcfg[idx].argmin(1), minlength=k).tolist(),
+            "sliced_slowdown_vs_best_config": {
+                "network": geomean(tcfg[idx, pick[idx]] / best),
+                "structural_rules": geomean(tcfg[idx, 0] / best),
+                "each_config": [geomean(tcfg[idx, j] / best) for j in range(k)]},
+            "slowdown_vs_best_overall": {
+                "first_level_only": geomean(one[idx] / overall[idx]),
+                "two_levels": geomean(two[idx] / overall[idx])},
+            "first_level_picks_sliced": float(np.mean(first_pick[idx] == sl))}
+    with open(os.path.join(args.out, "sliced_report.json"), "w") as f:
+        json.dump(rep, f, indent=1)
+    print(json.dumps(rep["test"], indent=1))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -280,6 +398,8 @@ def main():
     ap.add_argument("--betas", type=float, nargs="+", default=[2.0, 4.0, 8.0, 16.0, 32.0, math.inf])
     ap.add_argument("--retime", nargs="+", default=[], choices=list(sp.VARIANTS),
                     help="variants whose kernels changed: time them again on every stored matrix")
+    ap.add_argument("--second-level", action="store_true",
+                    help="also time SLICED's launch configurations and train the second-level network")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     from paper_1511_02494_gb300.build import build
@@ -349,6 +469,8 @@ def main():
     with open(os.path.join(args.out, "selector_report.json"), "w") as f:
         json.dump(report, f, indent=1)
     print(json.dumps(report["test"], indent=1))
+    if args.second_level:
+        train_second_level(args, d, model)
 
 
 if __name__ == "__main__":

@@ -103,3 +103,75 @@ def test_select_model_margin_fallback_matches_oracle():
                 assert ch.used_fallback == 0 and ch.variant == [6, 5, 4, 3, 2, 1, 0][best]
             ch2 = sp.spmv_select_model(f, m)  # no profile: never falls back
             assert ch2.used_fallback == 0 and ch2.variant == [6, 5, 4, 3, 2, 1, 0][best]
+
+
+_LAUNCH = np.array([[0, 0, 0], [1, 1, 1024], [4, 1, 1024], [1, 4096, 32], [4, 4096, 32]], np.int32)
+
+
+def test_second_level_model_file_and_launch_table(tmp_path):
+    """A model with a launch table (the second level of selection) is saved
+    as SPMVMLP2, loads back with its table, and its choice carries the
+    launch parameters of the output the oracle's forward ranks first."""
+    P = _params(32, 32, 5, seed=11)
+    sl = sp.VARIANT_IDS["sliced"]
+    m = _model(P, variants=[sl] * 5)
+    sp.spmv_model_set_launch(m, _LAUNCH)
+    path = tmp_path / "sub.bin"
+    sp.spmv_model_save(m, path)
+    assert path.read_bytes()[:8] == b"SPMVMLP2"
+    m2 = sp.spmv_model_load(path)
+    g = np.random.default_rng(12)
+    for _ in range(30):
+        f = _abi.Features()
+        vec = (g.standard_normal(16) * 2).astype(np.float32)
+        for i in range(16):
+            f.vec[i] = float(vec[i])
+        best, _ = oracle.argmax(oracle.mlp_forward_f32(P, vec)[0])
+        for mm in (m, m2):
+            ch = sp.spmv_select_model(f, mm)
+            assert ch.variant == sl
+            assert [ch.threads_per_row, ch.block_nnz, ch.items_per_warp] == _LAUNCH[best].tolist()
+    # a truncated table is a corrupt file; a plain model still saves as version 1
+    (tmp_path / "cut.bin").write_bytes(path.read_bytes()[:-4])
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_model_load(tmp_path / "cut.bin")
+    sp.spmv_model_save(_model(P), tmp_path / "v1.bin")
+    assert (tmp_path / "v1.bin").read_bytes()[:8] == b"SPMVMLP1"
+
+
+def test_second_level_rejects_invalid_launch_parameters():
+    P = _params(16, 16, 5, seed=13)
+    bad = _LAUNCH.copy()
+    bad[2] = [3, 1, 1024]  # three slices per warp: not a SLICED choice
+    m = _model(P, variants=[sp.VARIANT_IDS["sliced"]] * 5)
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_model_set_launch(m, bad)
+    m = _model(P, variants=[sp.VARIANT_IDS["subwarp"]] * 5)
+    with pytest.raises(sp.SpmvError):  # items_per_warp 7: not a valid choice
+        sp.spmv_model_set_launch(m, np.array([[0, 0, 7]] * 5, np.int32))
+
+
+def test_refined_selection_applies_the_second_level_to_its_variant():
+    """Two levels: the first model's choice, then, when it names SLICED, the
+    second model's launch parameters; another variant keeps none."""
+    sl, sw = sp.VARIANT_IDS["sliced"], sp.VARIANT_IDS["subwarp"]
+    P1, P2 = _params(16, 16, 2, seed=21), _params(16, 16, 5, seed=22)
+    first = _model(P1, variants=[sl, sw])
+    sub = _model(P2, variants=[sl] * 5)
+    sp.spmv_model_set_launch(sub, _LAUNCH)
+    g = np.random.default_rng(23)
+    seen = set()
+    for _ in range(60):
+        f = _abi.Features()
+        vec = (g.standard_normal(16) * 2).astype(np.float32)
+        for i in range(16):
+            f.vec[i] = float(vec[i])
+        b1, _ = oracle.argmax(oracle.mlp_forward_f32(P1, vec)[0])
+        b2, _ = oracle.argmax(oracle.mlp_forward_f32(P2, vec)[0])
+        ch = sp.spmv_select_model_refined(f, first, sub)
+        assert ch.variant == [sl, sw][b1]
+        got = [ch.threads_per_row, ch.block_nnz, ch.items_per_warp]
+        assert got == (_LAUNCH[b2].tolist() if b1 == 0 else [0, 0, 0])
+        assert sp.spmv_select_model_refined(f, first, None).variant == ch.variant
+        seen.add(b1)
+    assert seen == {0, 1}

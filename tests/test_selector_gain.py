@@ -18,9 +18,9 @@ DATA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                     "paper_1511_02494_gb300", "data")
 
 
-def _read_model(path):
+def _read_model(path, version=b"SPMVMLP1"):
     raw = open(path, "rb").read()
-    assert raw[:8] == b"SPMVMLP1"
+    assert raw[:8] == version
     h1, h2, k = np.frombuffer(raw, np.int32, 3, 8)
     f = np.frombuffer(raw, np.float32, offset=20)
     mean, istd = f[:16], f[16:32]
@@ -32,6 +32,10 @@ def _read_model(path):
         P[name] = f[o:o + n].reshape(shape)
         o += n
     variants = np.frombuffer(raw, np.int32, k, 20 + 4 * o)
+    if version == b"SPMVMLP2":
+        launch = np.frombuffer(raw, np.int32, 3 * k, 20 + 4 * o + 4 * k + 4).reshape(k, 3)
+        assert len(raw) == 20 + 4 * o + 4 * k + 4 + 12 * k
+        return P, variants, int(k), launch
     return P, variants, int(k)
 
 
@@ -100,3 +104,35 @@ def test_class_variant_table_is_the_per_class_best_on_training_data(data):
             continue
         slow = [_geomean(times[m, v] / best[m]) for v in range(k)]
         assert oracle.class_variant(c) == int(np.argmin(slow)), (c, slow)
+
+
+def test_second_level_network_beats_the_structural_rules_on_held_out_matrices(data):
+    """The second level (SLICED's launch configuration from the same
+    features): on the held-out matrices the committed network's choice,
+    computed with the oracle's forward pass, is nearer the best
+    configuration than SLICED's structural rules (configuration 0), and the
+    two levels together nearer the best over every variant and
+    configuration than the first level alone; the report states the same."""
+    import json
+    d, P1, variants, k = data
+    s = np.load(os.path.join(DATA, "sliced_dataset.npz"))
+    assert np.array_equal(s["seed"], d["seed"])
+    P2, v2, k2, launch = _read_model(os.path.join(DATA, "selector_sliced_mlp.bin"), b"SPMVMLP2")
+    sl = sp.VARIANT_IDS["sliced"]
+    assert np.all(v2 == sl) and np.array_equal(launch, s["configs"]) and k2 == len(s["configs"])
+    assert launch[0].tolist() == [0, 0, 0]  # configuration 0: the structural rules
+    test = np.where(d["seed"] % 5 == 0)[0]
+    tc = s["times"][test]
+    pick = oracle.mlp_forward_f32(P2, d["vec"][test]).argmax(1)
+    net = _geomean(tc[np.arange(len(test)), pick] / tc.min(1))
+    rules = _geomean(tc[:, 0] / tc.min(1))
+    assert net < rules
+    first = variants[oracle.mlp_forward_f32(P1, d["vec"][test]).argmax(1)]
+    one = d["times"][test][np.arange(len(test)), first]
+    two = np.where(first == sl, tc[np.arange(len(test)), pick], one)
+    overall = np.minimum(d["times"][test].min(1), tc.min(1))
+    assert _geomean(two / overall) < _geomean(one / overall)
+    rep = json.load(open(os.path.join(DATA, "sliced_report.json")))["test"]
+    assert abs(rep["sliced_slowdown_vs_best_config"]["network"] - net) < 1e-9
+    assert abs(rep["sliced_slowdown_vs_best_config"]["structural_rules"] - rules) < 1e-9
+    assert abs(rep["slowdown_vs_best_overall"]["two_levels"] - _geomean(two / overall)) < 1e-9
