@@ -391,6 +391,7 @@ def run_ours(args):
             "variant_rule": r["variant_rule"],
             "best_variant": r["best_variant"], "ms": round(km, 5),
             "gbs": round(r["min_bytes"] / (km * 1e-3) / 1e9, 1),
+            "gflops": round(2 * r["nnz"] / (km * 1e-3) / 1e9, 1),
             "frac_hbm": round(r["min_bytes"] / (km * 1e-3) / 1e9 / peak, 4),
             "plain_gbs": round(r["min_bytes"] / (r["plain_ms"] * 1e-3) / 1e9, 1),
             "speedup_vs_plain": round(s, 3),
@@ -414,6 +415,7 @@ def run_ours(args):
                    "l2": "no flush: every matrix (>= 369 MB) is larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "frac_of_hbm_peak": round(value / peak, 4),
+        "gflops": round(2 * sum(r["nnz"] for r in per) * args.steps * ws / (total_ms * 1e-3) / 1e9, 1),
         "plain_csr_gbs": round(step_bytes / (plain_total * 1e-3) / 1e9, 2),
         "speedup_vs_plain_csr": round(plain_total / sel_total, 3),
         "speedup_geomean": round(math.exp(sum(map(math.log, speedups)) / len(speedups)), 3),
