@@ -402,6 +402,7 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
     std::vector<int> slen((size_t)std::max<int64_t>(d.n_slices, 1));
     std::vector<int64_t> sptr((size_t)d.n_slices + 1, 0);
     unsigned n_long = 0;
+    int64_t slots = 0;  // sum of 32 x slice length: padding by unequal rows only
     // one layout pass for window length sigma (1 = rows in order)
     auto layout = [&](int sigma) -> spmv_status {
         SPMV_CUDA_TRY(cudaMemsetAsync(d.rowlen, 0xFF, 4 * std::max<int64_t>(n_pos, 1), s));
@@ -425,8 +426,11 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         }
         SPMV_CUDA_TRY(cudaMemcpyAsync(&n_long, d.count, 4, cudaMemcpyDeviceToHost, s));
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < d.n_slices; ++i)
+        slots = 0;
+        for (int64_t i = 0; i < d.n_slices; ++i) {
             sptr[i + 1] = sptr[i] + 32 * (int64_t)((slen[i] + d.vec - 1) / d.vec * d.vec);
+            slots += 32 * (int64_t)slen[i];
+        }
         return SPMV_OK;
     };
     // FP64 values: one element per slot row; FP32/BF16: four side by side
@@ -438,7 +442,7 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         // was chosen) every row above 32 nonzeros computed by a warp, so that
         // no lane's chain is longer than one element per lane of a warp
         if ((st = layout(1)) != SPMV_OK) return st;
-        if (sptr[d.n_slices] > A.nnz + A.nnz / 4) {
+        if (slots > A.nnz + A.nnz / 4) {
             sigma = 4096;
             if (P->c.items_per_warp == 0) cap = 32;
             if ((st = layout(sigma)) != SPMV_OK) return st;
