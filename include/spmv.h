@@ -372,9 +372,11 @@ spmv_status spmv_model_set_launch(spmv_model_t *m, const int32_t *launch);
 spmv_status spmv_model_logits(const spmv_model_t *m, const float *vec16, float *logits);
 
 /* Variant for the features f: argmax of the logits (ties to the lower
- * output), margin = best - second logit.  When margin < min_margin and a
- * profile p is given, the profiling rule decides instead (used_fallback = 1,
- * source = 1); otherwise source = 2.  Host-only; th may be NULL. */
+ * output), margin = best - second logit; when m carries launch parameters
+ * (spmv_model_set_launch) the choice takes the chosen output's.  When
+ * margin < min_margin and a profile p is given, the profiling rule decides
+ * instead (used_fallback = 1, source = 1, no launch parameters); otherwise
+ * source = 2.  Host-only; th may be NULL. */
 spmv_status spmv_select_model(const spmv_features_t *f, const spmv_model_t *m,
                               const spmv_profile_t *p, const spmv_thresholds_t *th,
                               spmv_choice_t *out);
