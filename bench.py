@@ -600,8 +600,9 @@ def run_features(args):
 def run_batch(args):
     """512 uneven matrices, each with the variant the learned selector picks:
     one launch per matrix with that variant, against one persistent launch
-    over all of them (plain, graph, autotuned), in which every matrix runs in
-    the sliced layout (spmv_batch_create_prepared)."""
+    over all of them (plain, graph, autotuned) with each matrix in the
+    persistent form of its variant, and the same with every matrix in the
+    sliced layout."""
     import numpy as np
     import torch
     import paper_1511_02494_gb300 as sp
@@ -628,8 +629,7 @@ def run_batch(args):
         for P, x, y in zip(preps, xs, ys):
             sp.spmv(P, x, y)
     ms_sep = _time_ms(per_matrix, reps=5, warm=2)
-    # one persistent launch over the prepared matrices (each in the sliced
-    # layout: its own when it was prepared as SLICED)
+    # one persistent launch, each matrix in the persistent form of its variant
     B = sp.spmv_batch_create_prepared(preps)
     sp.spmv_batch_bind(B, xs, ys)
     ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)
@@ -639,6 +639,11 @@ def run_batch(args):
     tune_s = time.perf_counter() - t0
     ms_tuned = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
     t, _ = sp.spmv_batch_config(B)
+    # the same with every matrix in the sliced layout
+    Bs = sp.spmv_batch_create_sliced(preps)
+    sp.spmv_batch_bind(Bs, xs, ys)
+    sp.spmv_batch_autotune(Bs, reps=3)
+    ms_sliced = _time_ms(lambda: sp.spmv_batch_run(Bs, use_graph=True), reps=10)
     out = {"mode": "batched", "matrices": len(mats), "nnz": int(sum(A.nnz for A in mats)),
            "rows_range": [min(A.n_rows for A in mats), max(A.n_rows for A in mats)],
            "min_bytes": total_bytes,
@@ -652,6 +657,8 @@ def run_batch(args):
            "ms_persistent_graph_autotuned": round(ms_tuned, 4), "autotune_s": round(tune_s, 2),
            "gbs_one_launch_per_matrix": round(total_bytes / ms_sep / 1e6, 1),
            "gbs_persistent_graph_autotuned": round(total_bytes / ms_tuned / 1e6, 1),
+           "ms_persistent_sliced_graph_autotuned": round(ms_sliced, 4),
+           "gbs_persistent_sliced_graph_autotuned": round(total_bytes / ms_sliced / 1e6, 1),
            "autotuned_lanes_per_row_counts": {int(k): int(c) for k, c in
                                               zip(*np.unique(t, return_counts=True))}}
     print(json.dumps(out), flush=True)

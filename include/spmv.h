@@ -480,17 +480,24 @@ typedef struct spmv_batch spmv_batch_t;
 spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
                               const int32_t *threads_per_row, const int32_t *rows_per_item,
                               spmv_batch_t **out, spmv_stream_t stream);
-/* A batch of prepared matrices (borrowed; they must outlive the batch) in
- * one persistent launch, every matrix in the sliced layout: a matrix
- * prepared as SLICED with FP64 values runs its own layout, as work items of
- * 4 slices (its long rows one item each); any other (another variant, or
- * SLICED with FP32/BF16 values) runs the sliced form with the automatic
- * layout, which the batch prepares and owns.  In the shared launch the FP64
- * pipe is the common bottleneck, and slices spend one DFMA per element with
- * no reductions (CSR rows of T lanes measured 1.2x slower over a batch).
- * Synchronizes `stream`. */
+/* A batch of prepared matrices (borrowed; they must outlive the batch), each
+ * run in the persistent form of its own variant inside the one launch: a
+ * SLICED matrix with FP64 values as work items of 4 slices (its long rows
+ * one item each); a MERGE or DYNAMIC matrix (imbalance class), or a SLICED
+ * one with FP32/BF16 values (the batch sums FP64), as the sliced form with
+ * the automatic layout, which the batch prepares and owns (CSR rows would
+ * make a warp run as many DFMAs as its longest row); any other variant as
+ * CSR row items with its prepared lanes per row.  Synchronizes `stream`. */
 spmv_status spmv_batch_create_prepared(const spmv_prepared_t *const *P, int32_t count,
                                        spmv_batch_t **out, spmv_stream_t stream);
+/* The same batch with every matrix in the sliced layout: a matrix prepared
+ * as SLICED with FP64 values runs its own layout, any other the sliced form
+ * with the automatic layout (prepared and owned by the batch).  Inside the
+ * shared launch the FP64 pipe is the common bottleneck, and slices spend one
+ * DFMA per element with no reductions: on a batch of 512 uneven matrices
+ * this ran 1.2x faster than each matrix's own variant. */
+spmv_status spmv_batch_create_sliced(const spmv_prepared_t *const *P, int32_t count,
+                                     spmv_batch_t **out, spmv_stream_t stream);
 /* Sets the vectors: x[m], y[m] are device pointers (host arrays of count
  * pointers).  Must precede spmv_batch_run; synchronizes `stream`. */
 spmv_status spmv_batch_bind(spmv_batch_t *B, const double *const *x, double *const *y,

@@ -278,14 +278,26 @@ def spmv_batch_create(mats, threads_per_row=None, rows_per_item=None, stream=Non
     return Batch(h, list(mats))
 
 
-def spmv_batch_create_prepared(preps, stream=None) -> Batch:
-    """A batch whose matrices run with their own prepared variant (SLICED as
-    slices, any other as CSR rows with its lanes per row)."""
+def _prepared_array(preps):
     n = len(preps)
-    arr = (C.c_void_p * max(n, 1))(*[P.handle.value if isinstance(P.handle, C.c_void_p) else P.handle
-                                     for P in preps])
+    return (C.c_void_p * max(n, 1))(*[P.handle.value if isinstance(P.handle, C.c_void_p) else P.handle
+                                      for P in preps]), n
+
+
+def spmv_batch_create_prepared(preps, stream=None) -> Batch:
+    """A batch whose matrices run in the persistent form of their own
+    prepared variant."""
+    arr, n = _prepared_array(preps)
     h = C.c_void_p()
     _check(lib().spmv_batch_create_prepared(arr, n, C.byref(h), _stream(stream)))
+    return Batch(h, list(preps))
+
+
+def spmv_batch_create_sliced(preps, stream=None) -> Batch:
+    """A batch whose matrices all run in the sliced layout."""
+    arr, n = _prepared_array(preps)
+    h = C.c_void_p()
+    _check(lib().spmv_batch_create_sliced(arr, n, C.byref(h), _stream(stream)))
     return Batch(h, list(preps))
 
 

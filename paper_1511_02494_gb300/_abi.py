@@ -106,6 +106,7 @@ def declare(lib):
         "spmv_cg": (I32, [P, P, P, P, I32, I32, P, I32, P]),
         "spmv_batch_create": (I32, [C.POINTER(CSR), I32, P, P, C.POINTER(P), P]),
         "spmv_batch_create_prepared": (I32, [P, I32, P, P]),
+        "spmv_batch_create_sliced": (I32, [P, I32, P, P]),
         "spmv_batch_bind": (I32, [P, P, P, P]),
         "spmv_batch_run": (I32, [P, I32, P]),
         "spmv_batch_autotune": (I32, [P, I32, P]),

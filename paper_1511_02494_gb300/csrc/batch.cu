@@ -251,8 +251,14 @@ spmv_status spmv_batch_create(const spmv_csr_t* mats, int32_t count, const int32
     return finish_create(B, count, s, out);
 }
 
-spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t count,
-                                       spmv_batch_t** out, spmv_stream_t stream)
+}  // extern "C"
+
+namespace {
+
+// all_sliced: every matrix in the sliced layout; otherwise each matrix in
+// the persistent form of its own variant
+spmv_status create_from_prepared(const spmv_prepared_t* const* P, int32_t count, bool all_sliced,
+                                 spmv_batch_t** out, spmv_stream_t stream)
 {
     clear_error();
     if (!out || count < 0 || (count > 0 && !P))
@@ -274,14 +280,19 @@ spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t 
             return fail(SPMV_ERR_INVALID_ARG, "prepared on another device");
         }
         const spmv_csr_t& A = Pm->A;
-        // Inside the one launch the matrices share the FP64 pipe, so every
-        // matrix runs in the sliced layout (one DFMA per element, no
-        // reductions): a matrix prepared for another variant, or for SLICED
-        // with FP32/BF16 values (the batch sums FP64), gets a sliced form
-        // that the batch prepares (automatic layout) and owns.  Measured on
-        // the 512-matrix set: 0.49 ms against 0.60 ms with the CSR variants
-        // run as CSR rows of T lanes.
-        if (Pm->c.variant != SPMV_V7_SLICED || Pm->c.value_type != SPMV_VAL_F64) {
+        // The sliced form the batch prepares and owns (automatic layout):
+        // all_sliced -- for every matrix not prepared as FP64 SLICED (inside
+        // the one launch the matrices share the FP64 pipe, and slices spend
+        // one DFMA per element with no reductions); otherwise for the
+        // imbalance variants (MERGE, DYNAMIC: as CSR rows a warp would run as
+        // many DFMAs as its longest row) and for SLICED with FP32/BF16 values
+        // (the batch sums FP64).  The other variants run as CSR rows of their
+        // prepared lanes.
+        const bool own_sliced = all_sliced
+            ? (Pm->c.variant != SPMV_V7_SLICED || Pm->c.value_type != SPMV_VAL_F64)
+            : (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC ||
+               (Pm->c.variant == SPMV_V7_SLICED && Pm->c.value_type != SPMV_VAL_F64));
+        if (own_sliced) {
             spmv_choice_t c{};
             c.variant = SPMV_V7_SLICED;
             c.cls = -1;
@@ -302,6 +313,22 @@ spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t 
         B->preps.push_back(sliced ? Pm : nullptr);
     }
     return finish_create(B, count, s, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+spmv_status spmv_batch_create_prepared(const spmv_prepared_t* const* P, int32_t count,
+                                       spmv_batch_t** out, spmv_stream_t stream)
+{
+    return create_from_prepared(P, count, false, out, stream);
+}
+
+spmv_status spmv_batch_create_sliced(const spmv_prepared_t* const* P, int32_t count,
+                                     spmv_batch_t** out, spmv_stream_t stream)
+{
+    return create_from_prepared(P, count, true, out, stream);
 }
 
 spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* const* y,

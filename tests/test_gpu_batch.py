@@ -83,9 +83,10 @@ def test_batch_explicit_shapes(batch_case):
 
 
 def test_batch_of_prepared_matrices(batch_case):
-    """SLICED matrices run their own slices (sorted, with long rows, and in
-    order); matrices prepared for other variants, or with BF16 values, run a
-    sliced form the batch prepares: every matrix one lane per row."""
+    """Each matrix in the persistent form of its own variant (SLICED as its
+    slices; MERGE, DYNAMIC and BF16 SLICED as a sliced form the batch
+    prepares; the others as CSR rows), and every matrix in the sliced layout
+    (spmv_batch_create_sliced)."""
     mats, dev, xs, ys = batch_case
     extra = [synth.zipf_rows(20_000, 20_000, 1.4, 5_000, seed=11), synth.stencil_27pt(12, seed=2)]
     mats = list(mats) + extra
@@ -107,22 +108,27 @@ def test_batch_of_prepared_matrices(batch_case):
     # values (run by the batch in its FP64 form)
     assert any(P.info().index_bytes < 4 for P in preps)
     assert any(P.info().value_type == sp.VAL_BF16 for P in preps)
-    B = sp.spmv_batch_create_prepared(preps)
-    sp.spmv_batch_bind(B, xs, ys)
-    sp.spmv_batch_run(B)
-    torch.cuda.synchronize()
-    _check(mats, xs, ys)
-    for y in ys:
-        y.fill_(float("nan"))
-    sp.spmv_batch_run(B, use_graph=True)
-    torch.cuda.synchronize()
-    _check(mats, xs, ys)
-    sp.spmv_batch_autotune(B, reps=2)
-    t, r = sp.spmv_batch_config(B)
-    assert all(t[i] == 1 and r[i] % 32 == 0 for i in range(len(preps)))
-    for y in ys:
-        y.fill_(float("nan"))
-    sp.spmv_batch_run(B, use_graph=True)
-    torch.cuda.synchronize()
-    _check(mats, xs, ys)
-    B.free()
+    for create in (sp.spmv_batch_create_prepared, sp.spmv_batch_create_sliced):
+        B = create(preps)
+        sp.spmv_batch_bind(B, xs, ys)
+        sp.spmv_batch_run(B)
+        torch.cuda.synchronize()
+        _check(mats, xs, ys)
+        for y in ys:
+            y.fill_(float("nan"))
+        sp.spmv_batch_run(B, use_graph=True)
+        torch.cuda.synchronize()
+        _check(mats, xs, ys)
+        sp.spmv_batch_autotune(B, reps=2)
+        t, r = sp.spmv_batch_config(B)
+        # sliced matrices (all of them in the sliced batch) take one lane a row
+        sl = [i for i, P in enumerate(preps)
+              if create is sp.spmv_batch_create_sliced or
+              P.info().variant in (sp.VARIANT_IDS["sliced"], sp.VARIANT_IDS["dynamic"])]
+        assert sl and all(t[i] == 1 and r[i] % 32 == 0 for i in sl)
+        for y in ys:
+            y.fill_(float("nan"))
+        sp.spmv_batch_run(B, use_graph=True)
+        torch.cuda.synchronize()
+        _check(mats, xs, ys)
+        B.free()
