@@ -629,21 +629,31 @@ def run_batch(args):
         for P, x, y in zip(preps, xs, ys):
             sp.spmv(P, x, y)
     ms_sep = _time_ms(per_matrix, reps=5, warm=2)
-    # one persistent launch, each matrix in the persistent form of its variant
-    B = sp.spmv_batch_create_prepared(preps)
-    sp.spmv_batch_bind(B, xs, ys)
-    ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)
-    ms_graph = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
-    t0 = time.perf_counter()
-    sp.spmv_batch_autotune(B, reps=3)
-    tune_s = time.perf_counter() - t0
-    ms_tuned = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
-    t, _ = sp.spmv_batch_config(B)
-    # the same with every matrix in the sliced layout
-    Bs = sp.spmv_batch_create_sliced(preps)
-    sp.spmv_batch_bind(Bs, xs, ys)
-    sp.spmv_batch_autotune(Bs, reps=3)
-    ms_sliced = _time_ms(lambda: sp.spmv_batch_run(Bs, use_graph=True), reps=10)
+    ms_plain = ms_graph = ms_tuned = ms_sliced = tune_s = None
+    t = np.zeros(0, np.int32)
+    if args.batch_form in ("both", "variant"):
+        # one persistent launch, each matrix in the persistent form of its variant
+        B = sp.spmv_batch_create_prepared(preps)
+        sp.spmv_batch_bind(B, xs, ys)
+        ms_plain = _time_ms(lambda: sp.spmv_batch_run(B), reps=10)
+        ms_graph = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
+        t0 = time.perf_counter()
+        sp.spmv_batch_autotune(B, reps=3)
+        tune_s = time.perf_counter() - t0
+        ms_tuned = _time_ms(lambda: sp.spmv_batch_run(B, use_graph=True), reps=10)
+        t, _ = sp.spmv_batch_config(B)
+    if args.batch_form in ("both", "sliced"):
+        # the same with every matrix in the sliced layout
+        Bs = sp.spmv_batch_create_sliced(preps)
+        sp.spmv_batch_bind(Bs, xs, ys)
+        sp.spmv_batch_autotune(Bs, reps=3)
+        ms_sliced = _time_ms(lambda: sp.spmv_batch_run(Bs, use_graph=True), reps=10)
+
+    def r4(v):
+        return None if v is None else round(v, 4)
+
+    def gbs(v):
+        return None if v is None else round(total_bytes / v / 1e6, 1)
     out = {"mode": "batched", "matrices": len(mats), "nnz": int(sum(A.nnz for A in mats)),
            "rows_range": [min(A.n_rows for A in mats), max(A.n_rows for A in mats)],
            "min_bytes": total_bytes,
@@ -653,12 +663,13 @@ def run_batch(args):
            "variant_counts": {sp.VARIANTS[v]: int(c) for v, c in
                               zip(*np.unique(np.array(choices), return_counts=True))},
            "ms_one_launch_per_matrix": round(ms_sep, 4),
-           "ms_persistent": round(ms_plain, 4), "ms_persistent_graph": round(ms_graph, 4),
-           "ms_persistent_graph_autotuned": round(ms_tuned, 4), "autotune_s": round(tune_s, 2),
+           "ms_persistent": r4(ms_plain), "ms_persistent_graph": r4(ms_graph),
+           "ms_persistent_graph_autotuned": r4(ms_tuned),
+           "autotune_s": None if tune_s is None else round(tune_s, 2),
            "gbs_one_launch_per_matrix": round(total_bytes / ms_sep / 1e6, 1),
-           "gbs_persistent_graph_autotuned": round(total_bytes / ms_tuned / 1e6, 1),
-           "ms_persistent_sliced_graph_autotuned": round(ms_sliced, 4),
-           "gbs_persistent_sliced_graph_autotuned": round(total_bytes / ms_sliced / 1e6, 1),
+           "gbs_persistent_graph_autotuned": gbs(ms_tuned),
+           "ms_persistent_sliced_graph_autotuned": r4(ms_sliced),
+           "gbs_persistent_sliced_graph_autotuned": gbs(ms_sliced),
            "autotuned_lanes_per_row_counts": {int(k): int(c) for k, c in
                                               zip(*np.unique(t, return_counts=True))}}
     print(json.dumps(out), flush=True)
@@ -682,6 +693,8 @@ def main():
     ap.add_argument("--cg", action="store_true", help="mixed-precision SpMV and CG report")
     ap.add_argument("--iters", type=int, default=300, help="CG iterations of --cg")
     ap.add_argument("--batch", action="store_true", help="batched persistent SpMV report")
+    ap.add_argument("--batch-form", default="both", choices=["both", "variant", "sliced"],
+                    help="--batch: which persistent form(s) to run")
     ap.add_argument("--features", action="store_true", help="feature extraction report")
     args = ap.parse_args()
     if args.warmup < 3:
