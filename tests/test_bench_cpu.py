@@ -1,0 +1,58 @@
+"""The benchmark's host side without a GPU: the reference arm's JSON line
+(the oracle timed on a row sample of the four-class set), the whole-job
+throughput arithmetic, and the DRAM-traffic record that is only reported
+while the kernel sources it was measured on are unchanged."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GB/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["steps"] == 1 and d["warmup"] >= 3 and d["n_gpus"] == 1 and d["ms_per_step"] > 0
+    assert d["config"]["workload"] == bench.WORKLOAD and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_job_throughput_counts_every_replica():
+    # 1 GB per replica per step, 10 steps, 4 replicas, 2 s for the slowest: 20 GB/s
+    assert bench._job_gbs(10**9, 10, 4, 2000.0) == pytest.approx(20.0)
+
+
+def test_traffic_record_needs_unchanged_sources(tmp_path, monkeypatch):
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    key = next(k for k in rec if "@" in k)
+    variant, matrix = key.split("@", 1)
+    assert bench._traffic(variant, matrix) == rec[key]["dram_bytes"]
+    assert bench._traffic("no_such_variant", matrix) is None
+    # a copy of the tree in which one of the measured sources changed
+    os.makedirs(tmp_path / "profiles")
+    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), tmp_path / "profiles")
+    for path in rec[key]["sources"]:
+        os.makedirs(os.path.dirname(tmp_path / path), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, path), tmp_path / path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic(variant, matrix) == rec[key]["dram_bytes"]
+    first = next(iter(rec[key]["sources"]))
+    with open(tmp_path / first, "a") as f:
+        f.write("\n// changed\n")
+    assert bench._traffic(variant, matrix) is None
