@@ -5,6 +5,8 @@ scale is 0 must be exactly 0); integer-valued, identity and permutation
 inputs must match bit for bit.  Integer work (features, prepared arrays,
 selections) must be bit-exact.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -670,7 +672,7 @@ def _sample_rows(A, k=3000, seed=0):
 
 
 FULL_CHOICES = [("scalar", {}), ("subwarp", {}), ("stream", {}), ("merge", {}), ("dynamic", {}),
-                ("latency", {}), ("compressed", {})]
+                ("latency", {}), ("compressed", {}), ("sliced", {}), ("sliced", {"threads_per_row": 2})]
 
 
 @pytest.mark.parametrize("variant,params", FULL_CHOICES, ids=[v for v, _ in FULL_CHOICES])
@@ -679,6 +681,21 @@ def test_full_size_sampled_parity(four_class, variant, params):
     in the launch configuration the benchmark times; rows sampled."""
     for A in four_class:
         y, x = _run(A, sp.make_choice(variant, **params))
+        _assert_close(y, A, x, rows=_sample_rows(A))
+
+
+def test_full_size_selected_configuration_parity(four_class):
+    """Each four-class matrix at full size with the choice the benchmark
+    makes: Table 1 features, the committed selector's two levels, prepare,
+    one SpMV; rows sampled."""
+    data = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_1511_02494_gb300", "data")
+    model = sp.spmv_model_load(os.path.join(data, "selector_mlp.bin"))
+    sub = sp.spmv_model_load(os.path.join(data, "selector_sliced_mlp.bin"))
+    for A in four_class:
+        dA = sp.DeviceCSR.from_host(A)
+        ch = sp.spmv_select_model_refined(sp.spmv_features(dA), model, sub)
+        y, x = _run(A, ch)
         _assert_close(y, A, x, rows=_sample_rows(A))
 
 
