@@ -10,9 +10,11 @@ ctypes and marshals numpy arrays.  Each wrapper names the passage of the paper
 it follows.
 
 Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
-every function below is pinned except the profile-rule *thresholds*, which the
-paper never prints ("empirically set", Section 3.2.1): the rule's logic is
-pinned, its default thresholds are parity unpinned.
+every function below is pinned.  The oracle holds no value measured on a GPU:
+the profile rule's thresholds, which the paper never prints ("empirically
+set", Section 3.2.1), and the class -> variant table are inputs of
+``profile_class`` and ``class_variant`` (the latter defaults to the paper's
+Table 2); the library's calibrated values are passed in by the tests.
 """
 from __future__ import annotations
 
@@ -78,7 +80,7 @@ def _load():
                 "orc_round_f32_array": (None, [i64, P, P]),
                 "orc_features": (None, [i64, i64, P, P, i64, i64, C.POINTER(Features)]),
                 "orc_profile_class": (i32, [C.c_double] * 6),
-                "orc_class_variant": (i32, [i32]),
+                "orc_class_variant": (i32, [i32, P]),
                 "orc_static_partition": (None, [i64, P, i64, P]),
                 "orc_row_blocks": (None, [i64, P, i64, i64, P]),
                 "orc_merge_path": (None, [i64, P, i64, i64, P, P]),
@@ -192,13 +194,29 @@ def features(A, line_bytes: int = 128, l2_bytes: int = 0) -> dict:
 CML, MB, IMB, CMP = 0, 1, 2, 3
 
 
-def profile_class(s_noxmiss, s_inflate, s_balance, tau=(1.15, 1.25, 3.0)) -> int:
-    """Section 3.2.1 profiling-based classification rule (readings O9-O12)."""
-    return int(_load().orc_profile_class(s_noxmiss, s_inflate, s_balance, *tau))
+# Table 2 (Section 3.3), class -> optimization, in the library's variant ids:
+# CML -> latency (software prefetch), MB -> compressed (delta-coded indices),
+# IMB -> dynamic (dynamic schedule), CMP -> sub-warp (unrolled, vectorised rows)
+TABLE2 = (5, 6, 4, 1)
 
 
-def class_variant(cls: int) -> int:
-    return int(_load().orc_class_variant(cls))
+def profile_class(s_noxmiss, s_inflate, s_balance, tau) -> int:
+    """Section 3.2.1 profiling-based classification rule (readings O9-O12).
+    tau = (tau_noxmiss, tau_inflate, tau_balance) must be given: the paper
+    sets its thresholds empirically and prints none."""
+    t = tuple(float(v) for v in tau)
+    if len(t) != 3:
+        raise ValueError("tau needs three thresholds")
+    return int(_load().orc_profile_class(s_noxmiss, s_inflate, s_balance, *t))
+
+
+def class_variant(cls: int, table=None) -> int:
+    """Variant serving a class: table[cls] (4 variant ids, indexed by class),
+    or the paper's Table 2 (TABLE2) when table is None."""
+    if table is None:
+        return int(_load().orc_class_variant(cls, None))
+    m = np.ascontiguousarray(np.asarray(table, dtype=np.int32).reshape(4))
+    return int(_load().orc_class_variant(cls, _p(m)))
 
 
 def static_partition(A, n_workers: int) -> np.ndarray:

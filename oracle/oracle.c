@@ -270,7 +270,8 @@ void orc_features(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
 /* ------------------------------------------------------------------------ */
 /* Section 3.2.1 profiling-based classifier, readings O9-O12.
  * Classes in the fixed tie order: 0 CML, 1 MB, 2 IMB; 3 CMP when no probe's
- * speedup is strictly above its threshold.  NaN counts as -infinity.          */
+ * speedup is strictly above its threshold.  NaN counts as -infinity.  The
+ * thresholds are inputs: the paper sets them empirically and prints none.    */
 int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
                           double tau_noxmiss, double tau_inflate, double tau_balance)
 {
@@ -291,16 +292,22 @@ int32_t orc_profile_class(double s_noxmiss, double s_inflate, double s_balance,
     return 3;
 }
 
-/* Table 2 analogue on the GPU: class -> variant id.  Variant ids:
- * 0 scalar, 1 sub-warp, 2 stream, 3 merge-path, 4 dynamic, 5 latency,
- * 6 compressed, 7 sliced.  The table is calibrated, like the thresholds: for
- * each class named by the rule, the variant with the lowest geometric-mean
- * slowdown against the exhaustive best on the training matrices measured on
- * GB300 -- sliced for every class (CML, MB, IMB, CMP).                      */
-int32_t orc_class_variant(int32_t cls)
+/* Table 2: the optimization assigned to each class, as a variant id of the
+ * library's enumeration (0 scalar, 1 sub-warp, 2 stream, 3 merge-path,
+ * 4 dynamic, 5 latency, 6 compressed, 7 sliced).  map (4 entries, indexed by
+ * class) is an input: the paper fixes the classes but its optimizations are
+ * CPU techniques, so which GPU variant serves a class is a choice of the
+ * caller.  map == NULL takes the paper's own Table 2 row by row:
+ *   CML -> software prefetching of x      -> latency (5)
+ *   MB  -> delta-coded column indices     -> compressed (6)
+ *   IMB -> dynamic / auto scheduling      -> dynamic (4)
+ *   CMP -> inner-loop unrolling + SIMD    -> sub-warp (1)
+ * An unknown class gives -1.                                                 */
+int32_t orc_class_variant(int32_t cls, const int32_t *map)
 {
-    static const int32_t map[4] = {7, 7, 7, 7};
-    return (cls >= 0 && cls < 4) ? map[cls] : -1;
+    static const int32_t table2[4] = {5, 6, 4, 1};
+    const int32_t *m = map ? map : table2;
+    return (cls >= 0 && cls < 4) ? m[cls] : -1;
 }
 
 /* ------------------------------------------------------------------------ */

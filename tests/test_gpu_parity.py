@@ -623,7 +623,7 @@ def test_profile_runs_and_selection_consistent():
     t = sp.spmv_default_thresholds()
     cls = oracle.profile_class(d["s_noxmiss"], d["s_inflate"], d["s_balance"],
                                tau=(t.tau_noxmiss, t.tau_inflate, t.tau_balance))
-    assert ch.cls == cls and ch.variant == oracle.class_variant(cls)
+    assert ch.cls == cls and ch.variant == oracle.class_variant(cls, [sp.spmv_class_variant(c) for c in range(4)])
     # one giant row among short ones: the balance probe must see the imbalance
     assert d["s_balance"] > 2.0
 

@@ -305,14 +305,35 @@ def test_profile_rule_golden(golden_dir):
 
 
 def test_profile_rule_nan_never_selected():
-    assert oracle.profile_class(float("nan"), 1.0, 1.0) == oracle.CMP
-    assert oracle.profile_class(float("nan"), 2.0, 1.0) == oracle.MB
+    tau = (1.1, 1.1, 1.1)
+    assert oracle.profile_class(float("nan"), 1.0, 1.0, tau) == oracle.CMP
+    assert oracle.profile_class(float("nan"), 2.0, 1.0, tau) == oracle.MB
 
 
-def test_class_to_variant_table():
-    # Table 2 analogue, calibrated on GB300 (checked against the committed
-    # training data in test_selector_gain): sliced (7) for every class
-    assert [oracle.class_variant(c) for c in range(4)] == [7, 7, 7, 7]
+def test_profile_rule_needs_explicit_thresholds():
+    # the paper prints no threshold values, so the oracle holds none
+    with pytest.raises(TypeError):
+        oracle.profile_class(2.0, 1.0, 1.0)
+    # the same speedups classify differently under different thresholds
+    assert oracle.profile_class(1.3, 1.2, 1.0, (1.25, 1.5, 3.0)) == oracle.CML
+    assert oracle.profile_class(1.3, 1.2, 1.0, (1.4, 1.1, 3.0)) == oracle.MB
+    assert oracle.profile_class(1.3, 1.2, 1.0, (1.4, 1.5, 3.0)) == oracle.CMP
+
+
+def test_class_to_variant_default_is_table2():
+    # Table 2 (Section 3.3): CML -> software prefetching of x, MB -> delta
+    # coding of column indices, IMB -> dynamic scheduling, CMP -> unrolling
+    # with vectorisation; in the library's variant names
+    names = ("scalar", "subwarp", "stream", "merge", "dynamic", "latency", "compressed", "sliced")
+    got = [names[oracle.class_variant(c)] for c in range(4)]
+    assert got == ["latency", "compressed", "dynamic", "subwarp"]
+    assert oracle.class_variant(4) == -1 and oracle.class_variant(-1) == -1
+
+
+def test_class_to_variant_follows_the_given_table():
+    table = (3, 0, 7, 2)
+    assert [oracle.class_variant(c, table) for c in range(4)] == list(table)
+    assert oracle.class_variant(5, table) == -1
 
 
 # --------------------------------------------------------------- partitions

@@ -82,7 +82,9 @@ def test_model_create_rejects_bad_models():
 def test_select_model_margin_fallback_matches_oracle():
     P = _params(seed=7)
     g = np.random.default_rng(3)
-    tau = (1.15, 1.25, 3.0)
+    t = sp.spmv_default_thresholds()
+    tau = (t.tau_noxmiss, t.tau_inflate, t.tau_balance)
+    table = [sp.spmv_class_variant(c) for c in range(4)]
     for margin_thr in (0.0, 0.5, 100.0):
         m = _model(P, margin=margin_thr, variants=[6, 5, 4, 3, 2, 1, 0])
         for _ in range(40):
@@ -98,7 +100,7 @@ def test_select_model_margin_fallback_matches_oracle():
             assert ch.margin == np.float32(margin)
             if margin < margin_thr:
                 cls = oracle.profile_class(prof.s_noxmiss, prof.s_inflate, prof.s_balance, tau)
-                assert ch.used_fallback == 1 and ch.variant == oracle.class_variant(cls)
+                assert ch.used_fallback == 1 and ch.variant == oracle.class_variant(cls, table)
             else:
                 assert ch.used_fallback == 0 and ch.variant == [6, 5, 4, 3, 2, 1, 0][best]
             ch2 = sp.spmv_select_model(f, m)  # no profile: never falls back

@@ -97,13 +97,15 @@ def test_class_variant_table_is_the_per_class_best_on_training_data(data):
     tr = np.where(d["seed"] % 5 != 0)[0]
     times = d["times"][tr]
     best = times.min(1)
-    cls = np.array([oracle.profile_class(*p) for p in d["prof"][tr]])
+    t = sp.spmv_default_thresholds()
+    tau = (t.tau_noxmiss, t.tau_inflate, t.tau_balance)
+    cls = np.array([oracle.profile_class(*p, tau) for p in d["prof"][tr]])
     for c in range(4):
         m = cls == c
         if m.sum() < 20:
             continue
         slow = [_geomean(times[m, v] / best[m]) for v in range(k)]
-        assert oracle.class_variant(c) == int(np.argmin(slow)), (c, slow)
+        assert sp.spmv_class_variant(c) == int(np.argmin(slow)), (c, slow)
 
 
 def test_second_level_network_beats_the_structural_rules_on_held_out_matrices(data):
