@@ -295,6 +295,30 @@ spmv_status spmv_features(const spmv_csr_t *A, int32_t line_bytes, spmv_features
 spmv_status spmv_profile(const spmv_csr_t *A, const double *x, int32_t reps,
                          spmv_profile_t *out, spmv_stream_t stream);
 
+/* The products and the partition of the profiling runs, which spmv_profile
+ * only times (Section 3.2.1 defines each run by what it changes in the
+ * baseline SpMV; this call returns what each computes, so that it can be
+ * checked).  One untimed run of each requested probe, on the kernels and the
+ * set-up spmv_profile uses:
+ *   bounds     device int64 [n_workers + 1] or NULL: the baseline's static
+ *              partition, bounds[w] = smallest row i with
+ *              rowptr[i] >= floor(w * nnz / n_workers), bounds[n_workers] =
+ *              n_rows (worker w walks rows bounds[w] .. bounds[w+1] - 1)
+ *   y_base     device [n_rows] or NULL: the baseline's y = A x
+ *   y_noxmiss  device [n_rows] or NULL: the same with every column index 0,
+ *              i.e. y_i = x[0] * sum_j a_ij (summed in the baseline's order)
+ *   y_inflate  device [n_rows] or NULL: the baseline with 64-bit rowptr and
+ *              colind (the same arithmetic in the same order as y_base)
+ *   y_balance  device [n_rows] or NULL: the baseline with the per-worker
+ *              time stamps (the same arithmetic as y_base)
+ * n_workers: 0 = the count spmv_profile uses (spmv_profile_t.n_workers),
+ * else 1 .. 2^26.  Validates A; allocates (stream-ordered) and frees the
+ * probes' temporary buffers as spmv_profile does.  Synchronizes `stream`.
+ * SPMV_ERR_UNSUPPORTED for a matrix without rows or nonzeros. */
+spmv_status spmv_profile_outputs(const spmv_csr_t *A, const double *x, int64_t n_workers,
+                                 int64_t *bounds, double *y_base, double *y_noxmiss,
+                                 double *y_inflate, double *y_balance, spmv_stream_t stream);
+
 /* Gather probe (a measurement aid in the spirit of the probes above, with no
  * counterpart in the paper): *sum (device, one uint64) = the sum modulo 2^64
  * of the 64-bit patterns of x[colind[j]] over every nonzero, read in storage
@@ -314,6 +338,19 @@ spmv_status spmv_gather_probe(const spmv_csr_t *A, const double *x, uint64_t *su
  * wait gives up after limit_ns (1..2e9 nanoseconds) and the call returns
  * SPMV_ERR_TIMEOUT with the device context intact.  Synchronizes `stream`. */
 spmv_status spmv_wait_check(int64_t limit_ns, int32_t arrive, spmv_stream_t stream);
+
+/* Self-test of the carry fix-ups that follow the pipelined kernels (a test
+ * aid; the paper has no counterpart).  Runs the STREAM (kind 0) or MERGE
+ * (kind 1) fix-up alone on caller-filled device arrays: carry_row int32
+ * [n_parts] (the row of each part's carried partial sum, -1 = none; the
+ * parts carrying one row are consecutive), carry_val [n_parts], status (one
+ * uint32) and y [n_rows].  It adds each row's carries to y[row] in part
+ * order, skips entries outside [0, n_rows), and leaves y untouched when
+ * *status != 0: after a bounded wait gave up, the parts the kernel skipped
+ * hold carry rows of an earlier call.  Asynchronous on `stream`. */
+spmv_status spmv_fixup_check(int32_t kind, int64_t n_parts, int64_t n_rows,
+                             const int32_t *carry_row, const double *carry_val,
+                             const uint32_t *status, double *y, spmv_stream_t stream);
 
 /* ---- selection (Sections 3.1-3.3) ----------------------------------------- */
 spmv_thresholds_t spmv_default_thresholds(void);
@@ -561,10 +598,19 @@ spmv_status spmv_cg(const spmv_prepared_t *A_inner, const spmv_prepared_t *A_exa
  *   - Every call shares the one scratch array and leaves its contents there;
  *     calls whose kernels overlap on the GPU (other streams, other host
  *     threads) race on it and must be serialized by the caller.
- *   - Bounded device waits that give up leave y incomplete; this call never
- *     synchronizes, so it does not report them. */
+ *   - Bounded device waits that give up leave y incomplete (the carry
+ *     fix-up then adds nothing); this call never synchronizes, so it does
+ *     not report them: spmv_stream_noalloc_status does. */
 spmv_status spmv_stream_noalloc(const spmv_csr_t *A, const double *x, double *y,
                                 spmv_stream_t stream);
+
+/* Whether the last spmv_stream_noalloc call on the current device finished:
+ * SPMV_ERR_TIMEOUT when one of its bounded device waits gave up (its y is
+ * then incomplete), else SPMV_OK (also when no call has run).  Reads the
+ * scratch's status word into a host variable with cudaMemcpyAsync on
+ * `stream` -- the stream of that call -- and synchronizes it; it allocates
+ * nothing.  The next spmv_stream_noalloc call clears the word. */
+spmv_status spmv_stream_noalloc_status(spmv_stream_t stream);
 
 /* Releases everything P owns (device sync first).  NULL is ignored. */
 void spmv_prepared_free(spmv_prepared_t *P);

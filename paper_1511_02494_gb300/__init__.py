@@ -119,9 +119,28 @@ def spmv_profile(A: DeviceCSR, x, reps: int = 5, stream=None) -> Profile:
     return out
 
 
+def spmv_profile_outputs(A: DeviceCSR, x, n_workers: int, bounds=None, y_base=None,
+                         y_noxmiss=None, y_inflate=None, y_balance=None, stream=None) -> None:
+    """What the profiling runs compute: the static partition (int64 CUDA
+    tensor [n_workers + 1]) and one product per probe (float64 CUDA tensors
+    [n_rows]); any may be None.  n_workers 0 = spmv_profile's count."""
+    _check(lib().spmv_profile_outputs(C.byref(A.desc), _ptr(x), int(n_workers), _ptr(bounds),
+                                      _ptr(y_base), _ptr(y_noxmiss), _ptr(y_inflate),
+                                      _ptr(y_balance), _stream(stream)))
+
+
 def spmv_wait_check(limit_ns: int, arrive: bool, stream=None) -> None:
     """Bounded-wait self-test; raises SpmvError (TIMEOUT) when nothing arrives."""
     _check(lib().spmv_wait_check(int(limit_ns), 1 if arrive else 0, _stream(stream)))
+
+
+def spmv_fixup_check(kind: int, carry_row, carry_val, status, y, stream=None) -> None:
+    """Carry fix-up self-test (kind 0 STREAM, 1 MERGE) on device tensors:
+    carry_row int32 [n_parts], carry_val float64 [n_parts], status int32 [1],
+    y float64 [n_rows] (updated in place)."""
+    _check(lib().spmv_fixup_check(int(kind), int(carry_row.numel()), int(y.numel()),
+                                  _ptr(carry_row), _ptr(carry_val), _ptr(status), _ptr(y),
+                                  _stream(stream)))
 
 
 def spmv_gather_probe(A: DeviceCSR, x, out, stream=None) -> None:
@@ -236,6 +255,12 @@ def spmv_stream_noalloc(A: DeviceCSR, x, y, stream=None) -> None:
     """y = A x with the pipelined STREAM kernel and no device allocation
     (scratch in a fixed static device array; see include/spmv.h)."""
     _check(lib().spmv_stream_noalloc(C.byref(A.desc), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def spmv_stream_noalloc_status(stream=None) -> None:
+    """Raises SpmvError (TIMEOUT) when the last spmv_stream_noalloc call on
+    this device gave up a bounded wait; synchronizes the stream."""
+    _check(lib().spmv_stream_noalloc_status(_stream(stream)))
 
 
 def spmv_cg(A_inner: Prepared, b, x, iters: int, refine_every: int = 0,

@@ -89,6 +89,9 @@ def declare(lib):
         "spmv_features": (I32, [C.POINTER(CSR), I32, C.POINTER(Features), P]),
         "spmv_profile": (I32, [C.POINTER(CSR), P, I32, C.POINTER(Profile), P]),
         "spmv_gather_probe": (I32, [C.POINTER(CSR), P, P, P]),
+        "spmv_profile_outputs": (I32, [C.POINTER(CSR), P, I64, P, P, P, P, P, P]),
+        "spmv_fixup_check": (I32, [I32, I64, I64, P, P, P, P, P]),
+        "spmv_stream_noalloc_status": (I32, [P]),
         "spmv_wait_check": (I32, [C.c_int64, I32, P]),
         "spmv_default_thresholds": (Thresholds, []),
         "spmv_classify_profile": (I32, [C.POINTER(Profile), C.POINTER(Thresholds), C.POINTER(I32)]),

@@ -141,6 +141,14 @@ cudaError_t launch_merge_tma(const spmv_csr_t& A, int tile_items, const int32_t*
 cudaError_t launch_window(const spmv_csr_t& A, int block_nnz, const int32_t* blocks, int64_t n_win,
                           int32_t* carry_row, double* carry_val, unsigned* status, int sm_count,
                           const double* x, double* y, cudaStream_t s);
+// The carry fix-ups of the two pipelined kernels on their own (they run
+// inside launch_window / launch_merge_tma; exported for the fix-up self-test)
+cudaError_t launch_window_fixup(int64_t n_win, int64_t n_rows, const int32_t* carry_row,
+                                const double* carry_val, const unsigned* status, double* y,
+                                cudaStream_t s);
+cudaError_t launch_tile_fixup(int64_t n_tiles, int64_t n_rows, const int32_t* carry_row,
+                              const double* carry_val, const unsigned* status, double* y,
+                              cudaStream_t s);
 spmv_status prepared_alloc(spmv_prepared* P, void** p, int64_t bytes);
 spmv_status dyn_prepare(spmv_prepared* P, cudaStream_t s);
 cudaError_t launch_dyn(const spmv_prepared* P, const double* x, double* y, cudaStream_t s);

@@ -232,13 +232,18 @@ k_merge_tma(int64_t n_tiles, int nnz, int n_rows, const int* __restrict__ rp,
 
 // Adds each tile's trailing partial row to that row, summing the tiles of one
 // row in tile order (deterministic).  carry_row is non-decreasing.
+// Adds each tile's carry to its row in tile order.  As in k_window_fixup:
+// nothing when a bounded wait of the tile kernel gave up (*status != 0,
+// carry_row then holds entries of an earlier call), and no entry outside
+// [0, n_rows) is used.
 __global__ void k_tile_fixup(int64_t n_tiles, int64_t n_rows, const int32_t* __restrict__ carry_row,
-                             const double* __restrict__ carry_val, double* __restrict__ y)
+                             const double* __restrict__ carry_val,
+                             const unsigned* __restrict__ status, double* __restrict__ y)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_tiles) return;
+    if (p >= n_tiles || (status && *status != 0u)) return;
     const int r = carry_row[p];
-    if (r >= n_rows) return;
+    if (r < 0 || r >= n_rows) return;
     if (p > 0 && carry_row[p - 1] == r) return;
     double s = 0.0;
     for (int64_t q = p; q < n_tiles && carry_row[q] == r; ++q) s += carry_val[q];
@@ -264,11 +269,21 @@ cudaError_t launch_tma_cfg(const spmv_csr_t& A, const int32_t* mrow, const int32
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_tile_fixup<<<(unsigned)((n_tiles + 255) / 256), 256, 0, s>>>(n_tiles, A.n_rows, carry_row,
-                                                                  carry_val, y);
+                                                                  carry_val, status, y);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_tile_fixup(int64_t n_tiles, int64_t n_rows, const int32_t* carry_row,
+                              const double* carry_val, const unsigned* status, double* y,
+                              cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    k_tile_fixup<<<(unsigned)((n_tiles + 255) / 256), 256, 0, s>>>(n_tiles, n_rows, carry_row,
+                                                                  carry_val, status, y);
+    return cudaGetLastError();
+}
 
 bool tma_aligned(const spmv_csr_t& A)
 {

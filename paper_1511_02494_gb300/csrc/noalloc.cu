@@ -81,3 +81,23 @@ extern "C" spmv_status spmv_stream_noalloc(const spmv_csr_t* A, const double* x,
                                 scratch->carry_val, &scratch->status, dev.sm_count, x, y, s));
     return SPMV_OK;
 }
+
+extern "C" spmv_status spmv_stream_noalloc_status(spmv_stream_t stream)
+{
+    clear_error();
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    NoAllocScratch* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (dev.device < kNaMaxDevices) scratch = g_na_addr[dev.device];
+    }
+    if (!scratch) return SPMV_OK;  // no call has run on this device
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    SPMV_CUDA_TRY(cudaMemcpyAsync(&h, &scratch->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return fail(SPMV_ERR_TIMEOUT, "spmv_stream_noalloc: a bounded device wait gave up; y is incomplete");
+    return SPMV_OK;
+}

@@ -187,16 +187,93 @@ extern "C" spmv_status spmv_gather_probe(const spmv_csr_t* A, const double* x, u
     return SPMV_OK;
 }
 
+namespace spmvlib {
+namespace {
+
+// The probes' shared set-up: the static equal-nonzero partition over W
+// workers, the zeroed column indices (noxmiss) and the 64-bit index copies
+// (inflate), all stream-ordered buffers released with the object.
+struct Probes {
+    int64_t W = 0;
+    int T = 1;
+    DevBuf b_bounds, b_zero, b_rp64, b_ci64, b_st;
+    int64_t* bounds = nullptr;
+    int* zero_ci = nullptr;
+    int64_t* rp64 = nullptr;
+    int64_t* ci64 = nullptr;
+    unsigned long long* stamps = nullptr;
+
+    spmv_status setup(const spmv_csr_t* A, int64_t n_workers, cudaStream_t s)
+    {
+        W = n_workers;
+        const int64_t N = A->n_rows, NNZ = A->nnz;
+        T = auto_threads_per_row((double)NNZ / (double)N / 4.0);
+        b_bounds.s = b_zero.s = b_rp64.s = b_ci64.s = b_st.s = s;
+        SPMV_CUDA_TRY(cudaMallocAsync(&b_bounds.p, sizeof(int64_t) * (W + 1), s));
+        SPMV_CUDA_TRY(cudaMallocAsync(&b_zero.p, sizeof(int) * NNZ, s));
+        SPMV_CUDA_TRY(cudaMallocAsync(&b_rp64.p, sizeof(int64_t) * (N + 1), s));
+        SPMV_CUDA_TRY(cudaMallocAsync(&b_ci64.p, sizeof(int64_t) * NNZ, s));
+        SPMV_CUDA_TRY(cudaMallocAsync(&b_st.p, sizeof(unsigned long long) * 2 * W, s));
+        bounds = static_cast<int64_t*>(b_bounds.p);
+        zero_ci = static_cast<int*>(b_zero.p);
+        rp64 = static_cast<int64_t*>(b_rp64.p);
+        ci64 = static_cast<int64_t*>(b_ci64.p);
+        stamps = static_cast<unsigned long long*>(b_st.p);
+        k_static_bounds<<<(unsigned)((W + 1 + 255) / 256), 256, 0, s>>>(N, NNZ, A->rowptr, W, bounds);
+        SPMV_CUDA_TRY(cudaGetLastError());
+        SPMV_CUDA_TRY(cudaMemsetAsync(zero_ci, 0, sizeof(int) * NNZ, s));
+        k_widen<int64_t><<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(N + 1, A->rowptr, rp64);
+        SPMV_CUDA_TRY(cudaGetLastError());
+        k_widen<int64_t><<<(unsigned)((NNZ + 255) / 256), 256, 0, s>>>(NNZ, A->colind, ci64);
+        SPMV_CUDA_TRY(cudaGetLastError());
+        return SPMV_OK;
+    }
+
+    // One run of probe `which`: 0 baseline, 1 noxmiss, 2 inflate, 3 balance
+    // (the baseline recording each worker's start and end time).
+    cudaError_t run(int which, const spmv_csr_t* A, const double* x, double* y, cudaStream_t s) const
+    {
+        switch (which) {
+            case 0: return launch_base<int, false>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, nullptr, s);
+            case 1: return launch_base<int, false>(T, W, bounds, A->rowptr, zero_ci, A->val, x, y, nullptr, s);
+            case 2: return launch_base<int64_t, false>(T, W, bounds, rp64, ci64, A->val, x, y, nullptr, s);
+            case 3: return launch_base<int, true>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, stamps, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+};
+
+// Workers of the probes: as many warps as the device keeps resident.
+spmv_status default_workers(const DeviceInfo& dev, int64_t* W)
+{
+    int per_sm = 0;
+    SPMV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_base<int, false, 4>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    *W = (int64_t)dev.sm_count * per_sm * 8;
+    return SPMV_OK;
+}
+
+spmv_status probe_args(const spmv_csr_t* A, const double* x, const char* who)
+{
+    if (!x) return fail(SPMV_ERR_INVALID_ARG, std::string(who) + ": NULL argument");
+    spmv_status st = check_csr_args(A);
+    if (st != SPMV_OK) return st;
+    if (A->n_rows == 0 || A->nnz == 0)
+        return fail(SPMV_ERR_UNSUPPORTED, std::string(who) + ": empty matrix has nothing to profile");
+    return SPMV_OK;
+}
+
+}  // namespace
+}  // namespace spmvlib
+
 extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_t reps,
                                     spmv_profile_t* out, spmv_stream_t stream)
 {
     clear_error();
     const auto wall0 = std::chrono::steady_clock::now();
-    if (!out || !x) return fail(SPMV_ERR_INVALID_ARG, "spmv_profile: NULL argument");
-    spmv_status st = check_csr_args(A);
+    if (!out) return fail(SPMV_ERR_INVALID_ARG, "spmv_profile: NULL argument");
+    spmv_status st = probe_args(A, x, "spmv_profile");
     if (st != SPMV_OK) return st;
-    if (A->n_rows == 0 || A->nnz == 0)
-        return fail(SPMV_ERR_UNSUPPORTED, "spmv_profile: empty matrix has nothing to profile");
     if (reps <= 0) reps = 5;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     DeviceInfo dev;
@@ -205,35 +282,14 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
     st = run_feature_pass(A, 128, nullptr, s);  // validation only
     if (st != SPMV_OK) return st;
 
-    int per_sm = 0;
-    SPMV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_base<int, false, 4>, 256, 0));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t W = (int64_t)dev.sm_count * per_sm * 8;
-    const int64_t N = A->n_rows, NNZ = A->nnz;
-    const int T = auto_threads_per_row((double)NNZ / (double)N / 4.0);
-
-    DevBuf b_bounds, b_zero, b_rp64, b_ci64, b_y, b_st;
-    b_bounds.s = b_zero.s = b_rp64.s = b_ci64.s = b_y.s = b_st.s = s;
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_bounds.p, sizeof(int64_t) * (W + 1), s));
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_zero.p, sizeof(int) * NNZ, s));
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_rp64.p, sizeof(int64_t) * (N + 1), s));
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_ci64.p, sizeof(int64_t) * NNZ, s));
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_y.p, sizeof(double) * N, s));
-    SPMV_CUDA_TRY(cudaMallocAsync(&b_st.p, sizeof(unsigned long long) * 2 * W, s));
-    int64_t* bounds = static_cast<int64_t*>(b_bounds.p);
-    int* zero_ci = static_cast<int*>(b_zero.p);
-    int64_t* rp64 = static_cast<int64_t*>(b_rp64.p);
-    int64_t* ci64 = static_cast<int64_t*>(b_ci64.p);
+    int64_t W = 0;
+    if ((st = default_workers(dev, &W)) != SPMV_OK) return st;
+    Probes pr;
+    if ((st = pr.setup(A, W, s)) != SPMV_OK) return st;
+    DevBuf b_y;
+    b_y.s = s;
+    SPMV_CUDA_TRY(cudaMallocAsync(&b_y.p, sizeof(double) * A->n_rows, s));
     double* y = static_cast<double*>(b_y.p);
-    unsigned long long* stamps = static_cast<unsigned long long*>(b_st.p);
-
-    k_static_bounds<<<(unsigned)((W + 1 + 255) / 256), 256, 0, s>>>(N, NNZ, A->rowptr, W, bounds);
-    SPMV_CUDA_TRY(cudaGetLastError());
-    SPMV_CUDA_TRY(cudaMemsetAsync(zero_ci, 0, sizeof(int) * NNZ, s));
-    k_widen<int64_t><<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(N + 1, A->rowptr, rp64);
-    SPMV_CUDA_TRY(cudaGetLastError());
-    k_widen<int64_t><<<(unsigned)((NNZ + 255) / 256), 256, 0, s>>>(NNZ, A->colind, ci64);
-    SPMV_CUDA_TRY(cudaGetLastError());
 
     cudaEvent_t e0, e1;
     SPMV_CUDA_TRY(cudaEventCreate(&e0));
@@ -243,13 +299,7 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
         for (int r = 0; r <= reps; ++r) {
             cudaError_t e = cudaEventRecord(e0, s);
             if (e != cudaSuccess) return e;
-            if (which == 0)
-                e = launch_base<int, false>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, nullptr, s);
-            else if (which == 1)
-                e = launch_base<int, false>(T, W, bounds, A->rowptr, zero_ci, A->val, x, y, nullptr, s);
-            else
-                e = launch_base<int64_t, false>(T, W, bounds, rp64, ci64, A->val, x, y, nullptr, s);
-            if (e != cudaSuccess) return e;
+            if ((e = pr.run(which, A, x, y, s)) != cudaSuccess) return e;
             if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
             float ms = 0.f;
@@ -264,10 +314,9 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
     if (e == cudaSuccess) e = time_runs(1, &p.t_noxmiss_ms);
     if (e == cudaSuccess) e = time_runs(2, &p.t_inflate_ms);
     std::vector<unsigned long long> h(2 * W);
+    if (e == cudaSuccess) e = pr.run(3, A, x, y, s);
     if (e == cudaSuccess)
-        e = launch_base<int, true>(T, W, bounds, A->rowptr, A->colind, A->val, x, y, stamps, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h.data(), stamps, sizeof(unsigned long long) * 2 * W,
+        e = cudaMemcpyAsync(h.data(), pr.stamps, sizeof(unsigned long long) * 2 * W,
                             cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaEventDestroy(e0);
@@ -292,5 +341,33 @@ extern "C" spmv_status spmv_profile(const spmv_csr_t* A, const double* x, int32_
     // wall time includes everything up to here
     p.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     *out = p;
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_profile_outputs(const spmv_csr_t* A, const double* x, int64_t n_workers,
+                                            int64_t* bounds, double* y_base, double* y_noxmiss,
+                                            double* y_inflate, double* y_balance,
+                                            spmv_stream_t stream)
+{
+    clear_error();
+    spmv_status st = probe_args(A, x, "spmv_profile_outputs");
+    if (st != SPMV_OK) return st;
+    if (n_workers < 0 || n_workers > ((int64_t)1 << 26))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_profile_outputs: n_workers must be in 0..2^26");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceInfo dev;
+    if ((st = current_device(&dev)) != SPMV_OK) return st;
+    if ((st = run_feature_pass(A, 128, nullptr, s)) != SPMV_OK) return st;  // validation only
+    int64_t W = n_workers;
+    if (W == 0 && (st = default_workers(dev, &W)) != SPMV_OK) return st;
+    Probes pr;
+    if ((st = pr.setup(A, W, s)) != SPMV_OK) return st;
+    double* ys[4] = {y_base, y_noxmiss, y_inflate, y_balance};
+    for (int which = 0; which < 4; ++which)
+        if (ys[which]) SPMV_CUDA_TRY(pr.run(which, A, x, ys[which], s));
+    if (bounds)
+        SPMV_CUDA_TRY(cudaMemcpyAsync(bounds, pr.bounds, sizeof(int64_t) * (W + 1),
+                                      cudaMemcpyDeviceToDevice, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     return SPMV_OK;
 }

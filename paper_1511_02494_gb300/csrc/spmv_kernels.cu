@@ -261,7 +261,7 @@ __global__ void k_merge_fixup(int64_t n_parts, int64_t n_rows, const int32_t* __
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_parts) return;
     const int r = carry_row[p];
-    if (r >= n_rows) return;
+    if (r < 0 || r >= n_rows) return;
     if (p > 0 && carry_row[p - 1] == r) return;
     double s = 0.0;
     for (int64_t q = p; q < n_parts && carry_row[q] == r; ++q) s += carry_val[q];

@@ -213,14 +213,19 @@ k_window(int64_t n_win, int nnz, int n_rows, const int* __restrict__ rp,
 
 // Adds each window's carry to its row, summing the windows of one row in
 // window order.  Windows without a carry hold -1; the windows carrying one
-// row are consecutive.
-__global__ void k_window_fixup(int64_t n_win, const int32_t* __restrict__ carry_row,
-                               const double* __restrict__ carry_val, double* __restrict__ y)
+// row are consecutive.  When a bounded wait of the window kernel gave up
+// (*status != 0) the windows it skipped never wrote their carry_row entry,
+// which then holds whatever an earlier call left: the fix-up does nothing
+// (that call's y is incomplete and reported so).  Entries outside
+// [0, n_rows) are skipped as well, so no store leaves y.
+__global__ void k_window_fixup(int64_t n_win, int64_t n_rows, const int32_t* __restrict__ carry_row,
+                               const double* __restrict__ carry_val,
+                               const unsigned* __restrict__ status, double* __restrict__ y)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_win) return;
+    if (p >= n_win || *status != 0u) return;
     const int r = carry_row[p];
-    if (r < 0) return;
+    if (r < 0 || r >= n_rows) return;
     if (p > 0 && carry_row[p - 1] == r) return;
     double s = 0.0;
     for (int64_t q = p; q < n_win && carry_row[q] == r; ++q) s += carry_val[q];
@@ -244,11 +249,22 @@ cudaError_t launch_win_cfg(const spmv_csr_t& A, const int32_t* blocks, int64_t n
                                                           carry_row, carry_val, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_window_fixup<<<(unsigned)((n_win + 255) / 256), 256, 0, s>>>(n_win, carry_row, carry_val, y);
+    k_window_fixup<<<(unsigned)((n_win + 255) / 256), 256, 0, s>>>(n_win, A.n_rows, carry_row,
+                                                                   carry_val, status, y);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_window_fixup(int64_t n_win, int64_t n_rows, const int32_t* carry_row,
+                                const double* carry_val, const unsigned* status, double* y,
+                                cudaStream_t s)
+{
+    if (n_win <= 0) return cudaSuccess;
+    k_window_fixup<<<(unsigned)((n_win + 255) / 256), 256, 0, s>>>(n_win, n_rows, carry_row,
+                                                                   carry_val, status, y);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_window(const spmv_csr_t& A, int block_nnz, const int32_t* blocks, int64_t n_win,
                           int32_t* carry_row, double* carry_val, unsigned* status, int sm_count,
@@ -315,5 +331,26 @@ extern "C" spmv_status spmv_wait_check(int64_t limit_ns, int32_t arrive, spmv_st
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "spmv_wait_check");
     if (h) return fail(SPMV_ERR_TIMEOUT, "spmv_wait_check: the bounded wait gave up, as the test asks");
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_fixup_check(int32_t kind, int64_t n_parts, int64_t n_rows,
+                                        const int32_t* carry_row, const double* carry_val,
+                                        const uint32_t* status, double* y, spmv_stream_t stream)
+{
+    clear_error();
+    if (kind != 0 && kind != 1)
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_fixup_check: kind must be 0 (STREAM) or 1 (MERGE)");
+    if (n_parts < 0 || n_rows < 0 || n_rows > INT32_MAX)
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_fixup_check: bad size");
+    if (n_parts > 0 && (!carry_row || !carry_val || !status || (n_rows > 0 && !y)))
+        return fail(SPMV_ERR_INVALID_ARG, "spmv_fixup_check: NULL argument");
+    DeviceInfo dev;
+    spmv_status st = current_device(&dev);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned* stw = reinterpret_cast<const unsigned*>(status);
+    SPMV_CUDA_TRY(kind == 0 ? launch_window_fixup(n_parts, n_rows, carry_row, carry_val, stw, y, s)
+                            : launch_tile_fixup(n_parts, n_rows, carry_row, carry_val, stw, y, s));
     return SPMV_OK;
 }

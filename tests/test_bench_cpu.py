@@ -39,20 +39,27 @@ def test_job_throughput_counts_every_replica():
 
 
 def test_traffic_record_needs_unchanged_sources(tmp_path, monkeypatch):
-    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    key = next(k for k in rec if "@" in k)
-    variant, matrix = key.split("@", 1)
-    assert bench._traffic(variant, matrix) == rec[key]["dram_bytes"]
-    assert bench._traffic("no_such_variant", matrix) is None
-    # a copy of the tree in which one of the measured sources changed
+    import hashlib
+    src = tmp_path / "pkg" / "kernel.cu"
+    os.makedirs(src.parent)
+    src.write_text("__global__ void k() {}\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     os.makedirs(tmp_path / "profiles")
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), tmp_path / "profiles")
-    for path in rec[key]["sources"]:
-        os.makedirs(os.path.dirname(tmp_path / path), exist_ok=True)
-        shutil.copy(os.path.join(ROOT, path), tmp_path / path)
+    rec = {"sliced@some_matrix": {"dram_bytes": 123456, "sources": {"pkg/kernel.cu": digest}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic(variant, matrix) == rec[key]["dram_bytes"]
-    first = next(iter(rec[key]["sources"]))
-    with open(tmp_path / first, "a") as f:
-        f.write("\n// changed\n")
-    assert bench._traffic(variant, matrix) is None
+    assert bench._traffic("sliced", "some_matrix") == 123456
+    assert bench._traffic("no_such_variant", "some_matrix") is None
+    with open(src, "a") as f:
+        f.write("// changed\n")
+    assert bench._traffic("sliced", "some_matrix") is None
+
+
+def test_committed_traffic_records_are_well_formed():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for key, r in rec.items():
+        if "@" not in key:
+            continue
+        assert r["dram_bytes"] > 0 and r["sources"]
+        for path in r["sources"]:
+            assert os.path.exists(os.path.join(ROOT, path)), path
