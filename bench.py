@@ -512,7 +512,8 @@ def run_cg(args):
                 ("compressed", "f64", sp.VAL_F64, sp.ACC_F64), ("compressed", "f32", sp.VAL_F32, sp.ACC_F32),
                 ("compressed", "bf16", sp.VAL_BF16, sp.ACC_F32), ("compressed", "f32_acc64", sp.VAL_F32, sp.ACC_F64),
                 ("compressed", "bf16_acc64", sp.VAL_BF16, sp.ACC_F64), ("sliced", "f64", sp.VAL_F64, sp.ACC_F64),
-                ("sliced", "f32", sp.VAL_F32, sp.ACC_F32), ("sliced", "bf16", sp.VAL_BF16, sp.ACC_F32)):
+                ("sliced", "f32", sp.VAL_F32, sp.ACC_F32), ("sliced", "bf16", sp.VAL_BF16, sp.ACC_F32),
+                ("sliced", "f32_acc64", sp.VAL_F32, sp.ACC_F64), ("sliced", "bf16_acc64", sp.VAL_BF16, sp.ACC_F64)):
             P = sp.spmv_prepare(dA, sp.make_choice(var, value_type=vt, accumulate=acc))
             ms = _time_ms(lambda: sp.spmv(P, x, y))
             sp.spmv(P, x, y)
@@ -530,9 +531,14 @@ def run_cg(args):
     exact = sp.spmv_prepare(dA, sp.make_choice("sliced"))
     iters = args.iters
     xs = {}
-    for name, vt, refine in (("f64", None, 0), ("f32", sp.VAL_F32, 10), ("bf16", sp.VAL_BF16, 10),
-                             ("bf16_no_refine", sp.VAL_BF16, 0)):
-        inner = exact if vt is None else sp.spmv_prepare(dA, sp.make_choice("sliced", value_type=vt))
+    for name, vt, acc, refine in (("f64", None, 0, 0), ("f32", sp.VAL_F32, sp.ACC_F32, 10),
+                                  ("bf16", sp.VAL_BF16, sp.ACC_F32, 10),
+                                  ("bf16_no_refine", sp.VAL_BF16, sp.ACC_F32, 0),
+                                  ("f32_acc64", sp.VAL_F32, sp.ACC_F64, 10),
+                                  ("bf16_acc64", sp.VAL_BF16, sp.ACC_F64, 10),
+                                  ("bf16_acc64_no_refine", sp.VAL_BF16, sp.ACC_F64, 0)):
+        inner = exact if vt is None else sp.spmv_prepare(dA, sp.make_choice("sliced", value_type=vt,
+                                                                             accumulate=acc))
         x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
         res = torch.empty(iters + 1, dtype=torch.float64, device="cuda")
         sp.spmv_cg(inner, b, x, iters, refine, A_exact=exact, resid=res, use_graph=True)

@@ -84,6 +84,7 @@ spmv_status prepared_alloc(spmv_prepared* P, void** p, int64_t bytes)
         return fail(SPMV_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    P->owned.push_back(*p);
     P->owned_bytes += bytes;
     return SPMV_OK;
 }
@@ -118,20 +119,18 @@ spmv_status dev_alloc(spmv_prepared_t* P, T** p, int64_t count)
         return fail(SPMV_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    P->owned.push_back(*p);
     P->owned_bytes += (int64_t)bytes;
     return SPMV_OK;
 }
 
+// Frees every device allocation the object made (each one registered itself
+// in P->owned when it was made), whatever the variant.
 void release(spmv_prepared_t* P)
 {
-    void* ptrs[] = {P->blocks, P->merge_nz, P->carry_row, P->carry_val, P->counter,
-                    P->rowbase, P->off16, P->lowval, P->x_stage, P->y_stage, P->status,
-                    P->dyn.m1, P->dyn.m2, P->dyn.lrow, P->dyn.seg_off, P->dyn.partial, P->x32,
-                    P->sl.rowlen, P->sl.slice_len, P->sl.slice_ptr, P->sl.perm, P->sl.col, P->sl.val,
-                    P->sl.long_rows, P->sl.count, P->sl.seg_off, P->sl.partial, P->sl.lowval,
-                    P->sl.off, P->sl.rowbase, P->sl.x32};
-    for (void* p : ptrs)
+    for (void* p : P->owned)
         if (p) cudaFree(p);
+    P->owned.clear();
 }
 
 int32_t launches_of(const spmv_prepared_t* P)

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "spmv.h"
 
@@ -116,6 +117,7 @@ struct spmv_prepared {
     DynPlan dyn;
     float* x32 = nullptr;          // COMPRESSED with FP32 accumulation: FP32 copy of x
     SlicedPlan sl;
+    std::vector<void*> owned;      // every device allocation above, freed by release()
 };
 
 namespace spmvlib {

@@ -23,11 +23,42 @@ __device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ldcs(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ unsigned short ldcs(const unsigned short* p) { return __ldcs(p); }
 
+// Exact FP32 -> FP64 widening in integer arithmetic.  The conversion
+// instruction runs on the FP64 pipe, this GPU's scarce unit (about two FP64
+// operations per clock per SM), so widening each FP32 or BF16 value with it
+// costs as much as the DFMA the value feeds.  The same double is assembled
+// from the float's bits with a few integer operations instead:
+//   exponent e in 1..254: sign, exponent e - 127 + 1023, the 23 mantissa
+//     bits at the top of the 52 (high word (e + 896) << 20 | m >> 3, low
+//     word m << 29);
+//   e = 255 (Inf, NaN): exponent 2047, the mantissa shifted the same way;
+//   zero: the zero of the same sign;
+//   subnormal (e = 0, m != 0): m 2^-149, renormalised from its leading one
+//     at bit p: exponent p + 874, mantissa m << (52 - p) without that bit.
+// A BF16 value is the FP32 value with the bits b << 16.
+__device__ __forceinline__ double widen_f32_bits(uint32_t f)
+{
+    const uint32_t sign = f & 0x80000000u;
+    const uint32_t mag = f & 0x7fffffffu;
+    uint32_t hi = sign | ((mag >> 3) + 0x38000000u);
+    const uint32_t lo = f << 29;
+    if (mag >= 0x7f800000u) hi += 0x38000000u;
+    if (mag < 0x00800000u) {
+        if (mag == 0u) return __hiloint2double((int)sign, 0);
+        const int p = 31 - __clz((int)mag);
+        const uint64_t bits = ((uint64_t)sign << 32) | ((uint64_t)(p + 874) << 52) |
+                              (((uint64_t)mag << (52 - p)) & 0x000fffffffffffffull);
+        return __longlong_as_double((long long)bits);
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen_f32(float a) { return widen_f32_bits(__float_as_uint(a)); }
+
 __device__ __forceinline__ double ldval(const double* p) { return __ldcs(p); }
-__device__ __forceinline__ double ldval(const float* p) { return (double)__ldcs(p); }
+__device__ __forceinline__ double ldval(const float* p) { return widen_f32(__ldcs(p)); }
 __device__ __forceinline__ double ldval(const __nv_bfloat16* p) {
     const unsigned short b = __ldcs(reinterpret_cast<const unsigned short*>(p));
-    return (double)__uint_as_float(((unsigned)b) << 16);
+    return widen_f32_bits(((uint32_t)b) << 16);
 }
 
 __device__ __forceinline__ double group_sum(double s, int width) {

@@ -366,7 +366,7 @@ k_sliced_segments_lp(int n_seg, const int64_t* __restrict__ seg_be, const int* _
     } else {
         double acc = 0.0;
         for (int64_t j = b + lane; j < e; j += 32)
-            acc = fma((double)widen32(round_to(__ldcs(v + j), (VT*)nullptr)), ldx(x + __ldcs(ci + j)), acc);
+            acc = fma(widen_f32(widen32(round_to(__ldcs(v + j), (VT*)nullptr))), ldx(x + __ldcs(ci + j)), acc);
         acc = group_sum(acc, 32);
         if (lane == 0) {
             const int r1 = seg_row[w];

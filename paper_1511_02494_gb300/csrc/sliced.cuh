@@ -139,8 +139,8 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
 // position p = 32 s + l sits at slot slice_ptr[s] + 128 (k / 4) + 4 l + k % 4,
 // so one lane loads four offsets (8 bytes) and four values (8 or 16 bytes)
 // per instruction.  ACC32: x32 is the FP32 copy of x; fmaf chain in row
-// order, one widening per row.  Otherwise each value is widened to FP64 and
-// summed with DFMAs.  Padded slots are loaded with their group but never
+// order, one widening per row.  Otherwise each value is widened to FP64 with
+// integer operations (widen_f32, no FP64 instruction) and summed with DFMAs.  Padded slots are loaded with their group but never
 // multiplied.
 __device__ __forceinline__ void load4(const __nv_bfloat16* p, float* a) {
     const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
@@ -218,7 +218,7 @@ __device__ __forceinline__ double slice_value_lp(int64_t s, int lane, const int*
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (k + 4 * g + u < len) acc64 = fma((double)a[g][u], xv[g][u], acc64);
+                    if (k + 4 * g + u < len) acc64 = fma(widen_f32(a[g][u]), xv[g][u], acc64);
         }
     }
     *row = len >= 0 ? (perm ? perm[p] : (int)p) : -1;

@@ -702,3 +702,21 @@ def test_full_size_selected_configuration_parity(four_class):
 def test_full_size_features_bit_exact(four_class):
     for A in four_class:
         _features_match(A)
+
+
+def test_prepared_free_releases_every_array():
+    # narrow (int16) stored columns and long-row segment tables are owned
+    # arrays too: repeated prepare/free must not lose device memory
+    cases = [(synth.stencil_27pt(40, seed=1), dict(index_bytes=2)),
+             (synth.zipf_rows(50_000, 50_000, 1.5, 20_000, seed=2), dict(block_nnz=4096, items_per_warp=32)),
+             (synth.stencil_27pt(40, seed=1), dict(value_type=sp.VAL_BF16))]
+    dev = [(sp.DeviceCSR.from_host(A), kw) for A, kw in cases]
+    for dA, kw in dev:  # warm-up: scratch kept per thread is allocated once
+        sp.spmv_prepare(dA, sp.make_choice("sliced", **kw)).free()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(20):
+        for dA, kw in dev:
+            sp.spmv_prepare(dA, sp.make_choice("sliced", **kw)).free()
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] < (16 << 20)
