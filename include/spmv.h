@@ -236,6 +236,8 @@ typedef struct {
     int32_t index_bytes;   /* SLICED with FP64 values: bytes per stored column,
                               4 (the column), 2 or 1 (column - row, int16 or
                               int8); 4 for the other variants                 */
+    int64_t n_long_rows;   /* SLICED: rows above the length cap, computed from
+                              CSR in segments; 0 for the other variants       */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */

@@ -73,7 +73,7 @@ class PreparedInfo(C.Structure):
         [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_blocks", "n_wide_rows",
                                   "owned_bytes", "min_bytes")] + \
         [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32),
-         ("launches", C.c_int32), ("index_bytes", C.c_int32)]
+         ("launches", C.c_int32), ("index_bytes", C.c_int32), ("n_long_rows", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

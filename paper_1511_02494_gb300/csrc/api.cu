@@ -140,7 +140,10 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
-        case SPMV_V7_SLICED:  // + x to FP32, + long-row segments, + fix-up of rows with several
+        case SPMV_V7_SLICED:
+            // FP64 values: slices and long rows in one launch.  FP32/BF16:
+            // + x to FP32, + long-row segments, + fix-up of rows with several
+            if (P->sl.value_type == SPMV_VAL_F64) return 1;
             return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0) + (P->sl.n_long > 0 ? 1 : 0) +
                    (P->sl.n_fix > 0 ? 1 : 0);
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
@@ -619,6 +622,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.accumulate = P->c.variant == SPMV_V6_COMPRESSED || P->c.variant == SPMV_V7_SLICED ? P->c.accumulate : 1;
     i.launches = launches_of(P);
     i.index_bytes = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.cbytes : 4;
+    i.n_long_rows = P->c.variant == SPMV_V7_SLICED ? P->sl.n_long : 0;
     *info = i;
     return SPMV_OK;
 }

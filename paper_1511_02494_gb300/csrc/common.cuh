@@ -79,6 +79,8 @@ struct SlicedPlan {
     int64_t* seg_be = nullptr;   // [2 n_seg] CSR begin and end of each segment
     int* seg_row = nullptr;      // [n_seg] row of a segment that is its row's only one, else -1
     int* fix = nullptr;          // [n_fix] long rows (list indices) with several segments
+    int* seg_fix = nullptr;      // [n_seg] index in fix of the segment's row, -1 for a single segment
+    unsigned* ticket = nullptr;  // [n_fix] segments of the row finished in this call (0 between calls)
     int n_fix = 0;
     int n_seg = 0;
     // low-precision values (FP32 / BF16), optionally 16-bit column offsets

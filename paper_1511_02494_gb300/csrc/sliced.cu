@@ -236,26 +236,10 @@ __device__ __forceinline__ longlong2 segment_bounds(const int64_t* seg_be, int w
     return __ldg(reinterpret_cast<const longlong2*>(seg_be) + w);
 }
 
-// One warp per segment writes the segment's sum: to y when it is its row's
-// only segment, else to partial, and k_sliced_fixup adds the partials of
-// each row with several segments in segment order (deterministic).
-__global__ void __launch_bounds__(kSB)
-k_sliced_segments(int n_seg, const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
-                  const int* __restrict__ ci, const double* __restrict__ v,
-                  const double* __restrict__ x, double* __restrict__ partial, double* __restrict__ y)
-{
-    const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
-    if (w >= n_seg) return;
-    const int lane = threadIdx.x & 31;
-    const longlong2 be = segment_bounds(seg_be, w);
-    const int64_t b = be.x, e = be.y;
-    const double sum = group_sum(row_partial<32, 8>(b, e, lane, ColPlain<int>{ci}, v, x), 32);
-    if (lane == 0) {
-        const int r1 = seg_row[w];
-        if (r1 >= 0) y[r1] = sum; else partial[w] = sum;
-    }
-}
-
+// A segment's warp writes its sum to y when it is its row's only segment,
+// else to partial; the partials of a row with several segments are summed
+// in segment order (k_sliced_fixup for FP32/BF16 values, the ticket in
+// k_sliced_long for FP64).
 // fix[t]: index in the long-row list of the t-th row with several segments
 __global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int* __restrict__ list,
                                const int* __restrict__ seg_off, const double* __restrict__ partial,
@@ -267,6 +251,65 @@ __global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int
     double sum = 0.0;
     for (int i = seg_off[q]; i < seg_off[q + 1]; ++i) sum += partial[i];
     y[list[q]] = sum;
+}
+
+// Slices and long-row segments in one launch (FP64 values, rows above the
+// cap present).  Blocks below seg_blocks take one segment per warp, the
+// others the slices (R per warp).  The block scheduler starts blocks
+// roughly in index order, so the segments -- long, bound by their gathers of
+// x -- start first and the short, latency-bound slices fill in around them
+// instead of running as a separate launch after them.  A row with several
+// segments has no fix-up launch either: each of its segments stores its
+// partial, and the warp that finishes the row's last one (an atomic ticket
+// per row) sums the partials in segment order, as k_sliced_fixup does, and
+// resets the ticket for the next call.  Nothing waits on another warp.
+template <int U, int R, int B, typename CT>
+__global__ void __launch_bounds__(kSB, B)
+k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
+              const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
+              const int* __restrict__ seg_fix, const int* __restrict__ fix,
+              const int* __restrict__ list, const int* __restrict__ seg_off,
+              unsigned* __restrict__ ticket, double* __restrict__ partial,
+              const int* __restrict__ ci, const double* __restrict__ v,
+              const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+              const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+              const CT* __restrict__ col, const double* __restrict__ val,
+              const double* __restrict__ x, double* __restrict__ y)
+{
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x < seg_blocks) {
+        const int w = (int)(blockIdx.x * (kSB / 32) + (threadIdx.x >> 5));
+        if (w >= n_seg) return;  // whole warps only
+        const longlong2 be = segment_bounds(seg_be, w);
+        const double sum = group_sum(row_partial<32, 4>(be.x, be.y, lane, ColPlain<int>{ci}, v, x), 32);
+        if (lane != 0) return;
+        const int r1 = seg_row[w];
+        if (r1 >= 0) {
+            y[r1] = sum;
+            return;
+        }
+        partial[w] = sum;
+        __threadfence();
+        const int t = seg_fix[w];
+        const int q = fix[t];
+        const int b = seg_off[q], e = seg_off[q + 1];
+        if (atomicAdd(ticket + t, 1u) != (unsigned)(e - b - 1)) return;
+        __threadfence();
+        double s = 0.0;
+        for (int i = b; i < e; ++i) s += __ldcg(partial + i);
+        y[list[q]] = s;
+        ticket[t] = 0u;
+        return;
+    }
+    const int64_t s0 = ((int64_t)(blockIdx.x - seg_blocks) * kSB + threadIdx.x) >> 5;
+    if constexpr (R == 1) {
+        if (s0 >= n_slices) return;
+        slice_rows<U, CT>(s0, lane, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
+    } else {
+        if (s0 * R >= n_slices) return;
+        slice_rows_multi<U, R, CT>(s0 * R, n_slices, lane, rowlen, slice_len, slice_ptr, perm, col, val,
+                                   x, y);
+    }
 }
 
 // ---- low-precision values (FP32 or BF16), optionally 16-bit column offsets --
@@ -575,13 +618,21 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         for (int q = 0; q < d.n_long; ++q)
             if (off[q + 1] - off[q] > 1) fix.push_back(q);
         d.n_fix = (int)fix.size();
+        // per segment the index of its row in the fix list (-1: the row's only segment)
+        std::vector<int> seg_fix((size_t)d.n_seg, -1);
+        for (int t = 0; t < d.n_fix; ++t)
+            for (int j = off[fix[t]]; j < off[fix[t] + 1]; ++j) seg_fix[j] = t;
         if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)d.n_seg)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_be), 16 * (int64_t)d.n_seg)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_row), 4 * (int64_t)d.n_seg)) != SPMV_OK ||
-            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.fix), 4 * std::max<int64_t>(d.n_fix, 1))) != SPMV_OK)
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_fix), 4 * (int64_t)d.n_seg)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.fix), 4 * std::max<int64_t>(d.n_fix, 1))) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.ticket), 4 * std::max<int64_t>(d.n_fix, 1))) != SPMV_OK)
             return st;
         if (d.n_fix > 0)
             SPMV_CUDA_TRY(cudaMemcpyAsync(d.fix, fix.data(), 4 * (size_t)d.n_fix, cudaMemcpyHostToDevice, s));
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.ticket, 0, 4 * std::max<int64_t>(d.n_fix, 1), s));
+        SPMV_CUDA_TRY(cudaMemcpyAsync(d.seg_fix, seg_fix.data(), 4 * (size_t)d.n_seg, cudaMemcpyHostToDevice, s));
         k_sl_seg_table<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.long_rows, d.seg_off,
                                                                           A.rowptr, d.seg_be, d.seg_row);
         SPMV_CUDA_TRY(cudaGetLastError());
@@ -603,6 +654,27 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     if (d.acc32 && A.n_cols > 0) {
         k_sl_x_to_f32<<<(unsigned)((A.n_cols + kSB - 1) / kSB), kSB, 0, s>>>(A.n_cols, x, d.x32);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (d.value_type == SPMV_VAL_F64 && d.n_long > 0) {
+        // slices and long-row segments in one launch, segments first
+        const unsigned seg_blocks = (unsigned)((d.n_seg + kSB / 32 - 1) / (kSB / 32));
+        const int R = P->c.threads_per_row == 2 || P->c.threads_per_row == 4 ? P->c.threads_per_row : 1;
+        const int64_t slice_warps = (d.n_slices + R - 1) / R;
+        const unsigned blocks = seg_blocks + (unsigned)((slice_warps + kSB / 32 - 1) / (kSB / 32));
+#define SPMV_SL_LONG(U, RR, B, CT)                                                                  \
+    k_sliced_long<U, RR, B, CT><<<blocks, kSB, 0, s>>>(                                           \
+        d.n_seg, seg_blocks, d.n_slices, d.seg_be, d.seg_row, d.seg_fix, d.fix, d.long_rows,       \
+        d.seg_off, d.ticket, d.partial, A.colind, A.val, d.rowlen, d.slice_len, d.slice_ptr, perm,  \
+        static_cast<const CT*>(d.scol), d.val, x, y)
+#define SPMV_SL_LONG_CT(CT)                                                                          \
+        if (R == 4) SPMV_SL_LONG(1, 4, 4, CT); else if (R == 2) SPMV_SL_LONG(2, 2, 6, CT);           \
+        else SPMV_SL_LONG(4, 1, 8, CT);
+        if (d.cbytes == 1) { SPMV_SL_LONG_CT(int8_t) }
+        else if (d.cbytes == 2) { SPMV_SL_LONG_CT(int16_t) }
+        else { SPMV_SL_LONG_CT(int) }
+#undef SPMV_SL_LONG_CT
+#undef SPMV_SL_LONG
+        return cudaGetLastError();
     }
     if (d.value_type == SPMV_VAL_F64) {
         // R slices per warp (sliced_prepare chose R, or the caller did);
@@ -637,20 +709,17 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || d.n_long == 0) return e;
+    // FP32/BF16 values (FP64 values with long rows took k_sliced_long above)
     const unsigned sgrid = grid_of(32 * (int64_t)d.n_seg, INT32_MAX);
-    if (d.value_type == SPMV_VAL_F64) {
-        k_sliced_segments<<<sgrid, kSB, 0, s>>>(d.n_seg, d.seg_be, d.seg_row, A.colind, A.val, x, d.partial, y);
-    } else {
 #define SPMV_SL_SEG(VT, A32)                                                                        \
     k_sliced_segments_lp<VT, A32><<<sgrid, kSB, 0, s>>>(d.n_seg, d.seg_be, d.seg_row, A.colind, A.val, x, \
                                                         d.x32, d.partial, y)
-        if (d.value_type == SPMV_VAL_F32) {
-            if (d.acc32) SPMV_SL_SEG(float, true); else SPMV_SL_SEG(float, false);
-        } else {
-            if (d.acc32) SPMV_SL_SEG(__nv_bfloat16, true); else SPMV_SL_SEG(__nv_bfloat16, false);
-        }
-#undef SPMV_SL_SEG
+    if (d.value_type == SPMV_VAL_F32) {
+        if (d.acc32) SPMV_SL_SEG(float, true); else SPMV_SL_SEG(float, false);
+    } else {
+        if (d.acc32) SPMV_SL_SEG(__nv_bfloat16, true); else SPMV_SL_SEG(__nv_bfloat16, false);
     }
+#undef SPMV_SL_SEG
     e = cudaGetLastError();
     if (e != cudaSuccess || d.n_fix == 0) return e;
     k_sliced_fixup<<<(unsigned)((d.n_fix + 255) / 256), 256, 0, s>>>(d.n_fix, d.fix, d.long_rows, d.seg_off,

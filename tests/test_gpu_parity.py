@@ -132,14 +132,28 @@ def test_identity_and_permutation_bit_exact(variant):
     assert torch.equal(y.cpu(), x[perm])
 
 
-@pytest.mark.parametrize("variant", ["dynamic", "merge", "stream", "latency"])
+@pytest.mark.parametrize("variant", ["dynamic", "merge", "stream", "latency", "sliced"])
 def test_repeated_launches_identical(variant):
-    """Back-to-back launches (counter reset, carry reuse) give the same y."""
+    """Back-to-back launches (counter reset, carry reuse, the per-row ticket of
+    SLICED's rows with several segments) give the same y."""
     A = synth.zipf_rows(20000, 20000, 1.6, 5000, seed=9)
     outs, x = _run(A, sp.make_choice(variant), reps=4)
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
     _assert_close(outs[0], A, x)
+
+
+def test_sliced_rows_of_many_segments_summed_in_order():
+    # rows of up to 60 segments of 2048 nonzeros, each row's segments summed
+    # in order by the warp finishing last: integer values give the exact sum,
+    # and repeated launches give the same bits
+    A = synth.zipf_rows(3000, 200_000, 1.2, 120_000, seed=12)
+    g = np.random.default_rng(3)
+    A.val = torch.from_numpy(g.integers(-3, 4, A.nnz).astype(np.float64))
+    x = torch.from_numpy(g.integers(-2, 3, A.n_cols).astype(np.float64))
+    outs, _ = _run(A, sp.make_choice("sliced", block_nnz=4096, items_per_warp=32), x, reps=3)
+    for o in outs:
+        assert np.array_equal(o.cpu().numpy(), oracle.spmv(A, x))
 
 
 def test_merge_long_row_spans_many_parts():
@@ -296,9 +310,8 @@ def test_sliced_layout_bit_exact(sigma, cap, name, A):
     S = (A.n_rows + 31) // 32
     info = P.info()
     assert info.n_blocks == S and info.block_nnz == sigma and info.items_per_warp == cap
-    lens = (A.rowptr[1:] - A.rowptr[:-1]).numpy()
-    several = bool((lens > max(cap, 2048)).any())  # long rows of several segments: the fix-up
-    assert info.launches == (0 if A.n_rows == 0 else 1 + (n_long > 0) + several)
+    # slices and long-row segments run in one launch
+    assert info.launches == (0 if A.n_rows == 0 else 1) and info.n_long_rows == n_long
     if S == 0:
         return
     assert np.array_equal(_export(P, sp.EXPORT_SLICE_ROWLEN, 32 * S, torch.int32), rowlen)
@@ -424,7 +437,7 @@ def test_sliced_auto_window_and_long_rows():
     assert info.block_nnz == 1 and info.items_per_warp == 1024 and info.threads_per_row == 1
     Z = synth.zipf_rows(60_000, 60_000, 1.4, 20_000, seed=9)
     P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced"))
-    assert P.info().block_nnz == 4096 and P.info().items_per_warp == 32 and P.info().launches == 3
+    assert P.info().block_nnz == 4096 and P.info().items_per_warp == 32 and P.info().launches == 1
     # a chosen cap is kept
     P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced", items_per_warp=512))
     assert P.info().block_nnz == 4096 and P.info().items_per_warp == 512
@@ -451,7 +464,7 @@ def test_sliced_auto_window_and_long_rows():
     # a cap of 32 sends every Zipf row above 32 nonzeros to the segments
     P = sp.spmv_prepare(sp.DeviceCSR.from_host(Z), sp.make_choice("sliced", block_nnz=4096,
                                                                    items_per_warp=32))
-    assert P.info().items_per_warp == 32 and P.info().launches == 3
+    assert P.info().items_per_warp == 32 and P.info().launches == 1
     y, x = _run(Z, sp.make_choice("sliced", block_nnz=4096, items_per_warp=32))
     _assert_close(y, Z, x)
 
