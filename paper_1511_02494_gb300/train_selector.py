@@ -14,7 +14,11 @@ Training: a 16-64-64-K ReLU network, full-batch Adam on the GPU
 (spmv_mlp_loss_grad_soft + spmv_mlp_adam), 80/20 split by seed.  Targets are
 cost-sensitive distributions over the variants built from the measured times
 (soft_targets); their sharpness beta is picked on a validation quarter of
-the training split.  The fallback margin is chosen on the training split.  Outputs (in --out):
+the training split.  The fallback margin (below which the profiling rule
+decides instead of the network) is chosen on out-of-fold logits of the
+training split: four networks, each trained without one quarter of it,
+give every training matrix the margin of a network that has not seen it.
+Outputs (in --out):
 selector_dataset.npz, selector_mlp.bin, selector_report.json.
 
     python -m paper_1511_02494_gb300.train_selector --out DIR [--n 2000]
@@ -271,6 +275,54 @@ def evaluate(d, params, mean, istd, mu, h1, h2, k, idx):
     }
 
 
+def standardize(vec, idx):
+    mean = vec[idx].mean(0).astype(np.float32)
+    sd = vec[idx].std(0)
+    return mean, np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 0.0).astype(np.float32)
+
+
+def margin_curve(times, logits, rule, cands):
+    """Geometric-mean slowdown against the best and fallback rate of the
+    policy 'network, or the profiling rule when the top-two logit margin is
+    below mu', for each mu in cands."""
+    srt = np.sort(logits, 1)
+    margin = srt[:, -1] - srt[:, -2]
+    best = times.min(1)
+    pred = logits.argmax(1)
+    return [{"mu": float(mu), "fallback_rate": float(np.mean(margin < mu)),
+             "slowdown": geomean(policy_times(times, pred, margin, rule, mu)[0] / best)} for mu in cands]
+
+
+def calibrate_margin(d, tr, beta, h1, h2, k, steps):
+    """The fallback margin mu from out-of-fold logits.  The training split is
+    cut into four folds by seed (seed % 5 = 1, 2, 3, 4); a network trained
+    (as the final one, same beta and steps) on three folds gives the logits
+    of the fourth, so every training matrix gets the margin of a network that
+    has not seen it -- the situation of a new matrix.  mu is the candidate
+    (0, or a quantile of those margins) with the lowest out-of-fold slowdown
+    against the best variant; 0 unless a positive mu is strictly better."""
+    vec = d["vec"].astype(np.float32)
+    seeds = d["seed"][tr]
+    oof = np.empty((len(tr), k), np.float32)
+    for f in (1, 2, 3, 4):
+        out_pos = np.where(seeds % 5 == f)[0]
+        fit = tr[seeds % 5 != f]
+        mean, istd = standardize(vec, fit)
+        p, _, _ = train(((vec - mean) * istd)[fit], soft_targets(d["times"][fit], beta), h1, h2, k,
+                        steps=steps, log=lambda *_: None)
+        oof[out_pos] = logits_of(p, mean, istd, vec[tr[out_pos]], h1, h2, k)
+    srt = np.sort(oof, 1)
+    margin = srt[:, -1] - srt[:, -2]
+    cands = [0.0] + sorted(set(np.quantile(margin, np.linspace(0.01, 0.6, 40)).tolist()))
+    curve = margin_curve(d["times"][tr], oof, d["rule_variant"][tr], cands)
+    best = min(curve, key=lambda c: (c["slowdown"], c["mu"]))
+    mu = best["mu"] if best["slowdown"] < curve[0]["slowdown"] else 0.0
+    return float(mu), {"method": "out-of-fold logits, 4 folds of the training split by seed",
+                       "oof_slowdown_without_fallback": curve[0]["slowdown"],
+                       "oof_slowdown_at_mu": next(c["slowdown"] for c in curve if c["mu"] == mu),
+                       "curve": curve}
+
+
 # Launch configurations of SLICED among which the second-level network
 # chooses (threads_per_row = slices per warp, block_nnz = sort window,
 # items_per_warp = row-length cap; 0 = the prepare step's own rule)
@@ -304,16 +356,25 @@ def time_choice(dA, ch, x, y, budget_ms: float = 25.0):
     return float(np.median(ts))
 
 
-def sliced_dataset(d, out_path: str, log=print):
+def sliced_dataset(d, out_path: str, retime: bool = False, log=print):
     """Times every SLICED launch configuration on the stored matrices
-    (regenerated from their seeds), in the stored order."""
+    (regenerated from their seeds), in the stored order; resumable through
+    NaN entries (saved every 200 matrices); retime times every one again."""
+    times = np.full((len(d["seed"]), len(SLICED_CONFIGS)), np.nan)
     if os.path.exists(out_path):
         s = np.load(out_path)
         if np.array_equal(s["seed"], d["seed"]) and s["times"].shape[1] == len(SLICED_CONFIGS):
-            return s["times"]
-    times = np.empty((len(d["seed"]), len(SLICED_CONFIGS)))
+            if not retime:
+                times = s["times"].astype(np.float64)
+    if retime or not os.path.exists(out_path):
+        np.savez(out_path, seed=d["seed"], times=times, configs=np.array(SLICED_CONFIGS, np.int32))
+    todo = np.where(np.isnan(times).any(1))[0]
+    if len(todo) == 0:
+        return times
+    log(f"timing SLICED configurations on {len(todo)} matrices")
     t0 = time.time()
-    for row, i in enumerate(d["seed"]):
+    for n, row in enumerate(todo):
+        i = d["seed"][row]
         family, n_rows = matrix_spec(int(i))
         A = synth.family_matrix(family, n_rows, seed=int(i), device="cuda")
         dA = sp.DeviceCSR(A.n_rows, A.n_cols, A.rowptr.contiguous(), A.colind.contiguous(),
@@ -324,10 +385,10 @@ def sliced_dataset(d, out_path: str, log=print):
             ch = sp.make_choice("sliced", threads_per_row=r, block_nnz=sigma, items_per_warp=cap)
             times[row, j] = time_choice(dA, ch, x, y)
         del dA, A, x, y
-        if (row + 1) % 200 == 0:
+        if (n + 1) % 200 == 0 or n == len(todo) - 1:
+            np.savez(out_path, seed=d["seed"], times=times, configs=np.array(SLICED_CONFIGS, np.int32))
             torch.cuda.empty_cache()
-            log(f"{row + 1}/{len(d['seed'])} matrices, {time.time() - t0:.0f} s")
-    np.savez(out_path, seed=d["seed"], times=times, configs=np.array(SLICED_CONFIGS, np.int32))
+            log(f"{n + 1}/{len(todo)} matrices, {time.time() - t0:.0f} s")
     return times
 
 
@@ -336,7 +397,7 @@ def train_second_level(args, d, first):
     launch configuration from the same features, trained like the first
     level (cost-sensitive targets, beta on a validation quarter), saved with
     its launch table; the report compares it with the structural rules."""
-    tcfg = sliced_dataset(d, os.path.join(args.out, "sliced_dataset.npz"))
+    tcfg = sliced_dataset(d, os.path.join(args.out, "sliced_dataset.npz"), retime=args.retime_configs)
     seeds, vec = d["seed"], d["vec"].astype(np.float32)
     tr, te = np.where(seeds % 5 != 0)[0], np.where(seeds % 5 == 0)[0]
     fit, val = np.where((seeds % 5 != 0) & (seeds % 5 != 4))[0], np.where(seeds % 5 == 4)[0]
@@ -400,6 +461,8 @@ def main():
                     help="variants whose kernels changed: time them again on every stored matrix")
     ap.add_argument("--second-level", action="store_true",
                     help="also time SLICED's launch configurations and train the second-level network")
+    ap.add_argument("--retime-configs", action="store_true",
+                    help="with --second-level: time every SLICED launch configuration again")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     from paper_1511_02494_gb300.build import build
@@ -446,22 +509,13 @@ def main():
         print(f"beta {beta}: validation slowdown {beta_scores[str(beta)]:.4f}", flush=True)
     beta = float(min(args.betas, key=lambda b_: beta_scores[str(b_)]))
     params, hist, train_ms = train(z[tr], soft_targets(d["times"][tr], beta), h1, h2, k, steps=args.steps)
-    # fallback margin: smallest value whose training slowdown is within 0.5 %
-    # of the best any margin achieves
-    lg = logits_of(params, mean, istd, vec[tr], h1, h2, k)
-    srt = np.sort(lg, 1)
-    margin = srt[:, -1] - srt[:, -2]
-    best = d["times"][tr].min(1)
-    cands = [0.0] + sorted(set(np.quantile(margin, np.linspace(0.02, 0.5, 25)).tolist()))
-    slow = [geomean(policy_times(d["times"][tr], lg.argmax(1), margin, d["rule_variant"][tr], mu)[0] / best)
-            for mu in cands]
-    target = min(slow) * 1.005
-    mu = float(next(c for c, s in zip(cands, slow) if s <= target))
+    mu, calib = calibrate_margin(d, tr, beta, h1, h2, k, args.steps)
     model = sp.spmv_model_create(h1, h2, k, mean, istd, params, list(range(k)), mu)
     sp.spmv_model_save(model, os.path.join(args.out, "selector_mlp.bin"))
     report = {"train": evaluate(d, params, mean, istd, mu, h1, h2, k, tr),
               "test": evaluate(d, params, mean, istd, mu, h1, h2, k, test),
-              "min_margin": mu, "loss_history": hist, "variants": list(sp.VARIANTS),
+              "min_margin": mu, "margin_calibration": calib,
+              "loss_history": hist, "variants": list(sp.VARIANTS),
               "beta": beta, "beta_validation_slowdown": beta_scores,
               "training_stream_ms": round(train_ms, 2),
               "training_ms_per_step": round(train_ms / max(args.steps, 1), 4),

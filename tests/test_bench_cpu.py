@@ -63,3 +63,20 @@ def test_committed_traffic_records_are_well_formed():
         assert r["dram_bytes"] > 0 and r["sources"]
         for path in r["sources"]:
             assert os.path.exists(os.path.join(ROOT, path)), path
+
+
+def test_cpu_row_sample_is_strided_over_the_whole_matrix():
+    import numpy as np
+    import synth
+    A = synth.zipf_rows(5000, 5000, 1.5, 3000, seed=1)
+    S = bench._row_sample(A, 4, block=64)
+    rp = A.rowptr.numpy().astype(np.int64)
+    rows = np.concatenate([np.arange(s, min(s + 64, A.n_rows)) for s in range(0, A.n_rows, 256)])
+    assert S.n_rows == len(rows) and S.n_cols == A.n_cols
+    assert rows[-1] >= A.n_rows - 256  # reaches the end of the matrix
+    srp = S.rowptr.numpy().astype(np.int64)
+    for k in (0, 1, len(rows) // 2, len(rows) - 1):
+        r = rows[k]
+        assert np.array_equal(S.colind.numpy()[srp[k]:srp[k + 1]], A.colind.numpy()[rp[r]:rp[r + 1]])
+        assert np.array_equal(S.val.numpy()[srp[k]:srp[k + 1]], A.val.numpy()[rp[r]:rp[r + 1]])
+    assert srp[-1] == S.nnz == sum(rp[r + 1] - rp[r] for r in rows)

@@ -42,3 +42,16 @@ def test_second_level_configurations_are_valid_sliced_choices():
     s = np.load(os.path.join(DATA, "sliced_dataset.npz"))
     assert np.array_equal(s["configs"], np.array(ts.SLICED_CONFIGS, np.int32))
     assert s["times"].shape == (2000, k) and np.all(s["times"] > 0)
+
+
+def test_margin_curve_applies_the_rule_below_the_margin():
+    # three matrices, two variants; the rule always names variant 1
+    times = np.array([[1.0, 2.0], [4.0, 1.0], [1.0, 1.0]])
+    logits = np.array([[3.0, 0.0], [0.5, 0.0], [0.0, 0.1]], np.float32)  # margins 3, 0.5, 0.1
+    rule = np.array([1, 1, 1])
+    c = ts.margin_curve(times, logits, rule, [0.0, 0.2, 1.0, 5.0])
+    assert [e["fallback_rate"] for e in c] == [0.0, 1 / 3, 2 / 3, 1.0]
+    # mu 0: picks 0, 0, 1 -> slowdowns 1, 4, 1; mu 1: the second takes the rule -> 1, 1, 1
+    assert c[0]["slowdown"] == pytest.approx(4 ** (1 / 3))
+    assert c[2]["slowdown"] == pytest.approx(1.0)
+    assert c[3]["slowdown"] == pytest.approx(2 ** (1 / 3))
