@@ -94,6 +94,9 @@ def _load():
                 "orc_sliced_offsets": (i64, [i64, P, P, P, P, P, i32, P, P]),
                 "orc_sliced_diag": (i64, [i64, P, P, P, P, P, P]),
                 "orc_sliced_index_bytes": (i32, [i64]),
+                "orc_sliced_delta": (i64, [i64, P, P, P, P, P, P, P]),
+                "orc_delta_bytes": (i32, [i64]),
+                "orc_sliced_panel": (i64, [i64, P, P, P, P, P, P, P]),
                 "orc_cg": (None, [i64, P, P, P, i32, P, i32, P, P, i32, P, P, P, P]),
                 "orc_adam_f32": (None, [i64, P, P, P, P] + [C.c_float] * 7),
             }
@@ -312,6 +315,44 @@ def sliced_diag(A, perm, rowlen, sptr):
     sptr = _np(sptr, np.int64)
     reach = int(_load().orc_sliced_diag(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr), _p(d)))
     return d[:tot], reach, int(_load().orc_sliced_index_bytes(reach))
+
+
+def sliced_delta(A, perm, rowlen, sptr):
+    """Table 2's delta coding on the FP64 sliced layout (reading O24): the
+    per-position row base (first column), the delta from the previous column
+    at each slot (0 for first elements and padding), the largest delta, and
+    the bytes per delta that largest delta allows (1, 2, or 0 = none)."""
+    rp, ci, _ = _csr(A)
+    S = (A.n_rows + 31) // 32
+    tot = int(sptr[-1])
+    base = np.empty(max(32 * S, 1), np.int32)
+    d = np.empty(max(tot, 1), np.int32)
+    perm = _np(perm, np.int32)
+    rowlen = _np(rowlen, np.int32)
+    sptr = _np(sptr, np.int64)
+    big = int(_load().orc_sliced_delta(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr),
+                                       _p(base), _p(d)))
+    return base[:32 * S], d[:tot], big, int(_load().orc_delta_bytes(big))
+
+
+def delta_bytes(largest: int) -> int:
+    return int(_load().orc_delta_bytes(int(largest)))
+
+
+def sliced_panel(A, perm, rowlen, sptr):
+    """Column-blocked form of the FP64 sliced layout (reading O25): the
+    offset inside each element's 65536-column panel, the panel step from the
+    previous element, and the largest step (the form needs it <= 255)."""
+    rp, ci, _ = _csr(A)
+    tot = int(sptr[-1])
+    lo = np.empty(max(tot, 1), np.uint16)
+    st = np.empty(max(tot, 1), np.int32)
+    perm = _np(perm, np.int32)
+    rowlen = _np(rowlen, np.int32)
+    sptr = _np(sptr, np.int64)
+    big = int(_load().orc_sliced_panel(A.n_rows, _p(rp), _p(ci), _p(perm), _p(rowlen), _p(sptr),
+                                       _p(lo), _p(st)))
+    return lo[:tot], st[:tot], big
 
 
 def sliced_index_bytes(reach: int) -> int:

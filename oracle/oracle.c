@@ -34,6 +34,13 @@
  *       the FP64 sliced layout, the offset of each column from its row's
  *       index: 8 bits when every |column - row| in the slices is at most 127,
  *       16 bits when at most 32767.
+ *   O24 Table 2's delta coding proper: each column minus the previous
+ *       column of its row, the row's first column kept whole; one width per
+ *       matrix ("never both"), 8 bits when every delta is at most 255, else
+ *       16 bits when at most 65535, else not applicable.
+ *   O25 for rows whose deltas exceed 16 bits, a column-blocked form: a
+ *       16-bit offset inside a panel of 65536 columns and an 8-bit step
+ *       between the panels of consecutive elements.
  */
 #include <math.h>
 #include <stdint.h>
@@ -514,6 +521,75 @@ int64_t orc_sliced_diag(int64_t n_rows, const int32_t *rowptr, const int32_t *co
 int32_t orc_sliced_index_bytes(int64_t reach)
 {
     return reach <= 127 ? 1 : (reach <= 32767 ? 2 : 4);
+}
+
+/* Table 2's delta coding of column indices for the FP64 sliced layout
+ * (reading O24): every column of a row is kept as its difference from the
+ * previous column of the same row, and the row's first column as an
+ * absolute base at its position.  d_out: the delta at each element's slot
+ * (vec = 1 placement), 0 for a row's first element and in padding;
+ * rowbase_pos: the first column per position, 0 where no row sits in the
+ * slices.  Returns the largest delta over the rows in the slices (0 when no
+ * row has two elements).                                                     */
+int64_t orc_sliced_delta(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                         const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
+                         int32_t *rowbase_pos, int32_t *d_out)
+{
+    int64_t n_slices = (n_rows + 31) / 32, largest = 0;
+    int64_t tot = slice_ptr[n_slices];
+    for (int64_t q = 0; q < tot; ++q) d_out[q] = 0;
+    for (int64_t p = 0; p < 32 * n_slices; ++p) {
+        rowbase_pos[p] = 0;
+        if (p >= n_rows || rowlen[p] <= 0) continue;
+        int64_t b = rowptr[perm[p]];
+        rowbase_pos[p] = colind[b];
+        for (int64_t k = 1; k < rowlen[p]; ++k) {
+            int64_t d = (int64_t)colind[b + k] - colind[b + k - 1];
+            d_out[slot_of(slice_ptr, p, k, 1)] = (int32_t)d;
+            if (d > largest) largest = d;
+        }
+    }
+    return largest;
+}
+
+/* "8- or 16-bit deltas wherever possible, but never both" (Section 3.3), per
+ * matrix: 1 byte when every delta is at most 255, 2 when at most 65535, 0
+ * when some delta needs more (the delta coding does not apply).               */
+int32_t orc_delta_bytes(int64_t largest_delta)
+{
+    return largest_delta <= 255 ? 1 : (largest_delta <= 65535 ? 2 : 0);
+}
+
+/* Column-blocked form of the FP64 sliced layout's columns, for rows whose
+ * deltas do not fit 16 bits (reading O25): the column space is cut into
+ * panels of 65536 columns; each element keeps its offset inside its panel
+ * (column mod 65536) and the step from the previous element's panel to its
+ * own (the first element's from panel 0).  lo_out and step_out at each
+ * element's slot, 0 in padding.  Returns the largest step over the rows in
+ * the slices; the form applies when it is at most 255 (8 bits).             */
+int64_t orc_sliced_panel(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                         const int32_t *perm, const int32_t *rowlen, const int64_t *slice_ptr,
+                         uint16_t *lo_out, int32_t *step_out)
+{
+    int64_t n_slices = (n_rows + 31) / 32, largest = 0;
+    int64_t tot = slice_ptr[n_slices];
+    for (int64_t q = 0; q < tot; ++q) {
+        lo_out[q] = 0;
+        step_out[q] = 0;
+    }
+    for (int64_t p = 0; p < 32 * n_slices; ++p) {
+        if (p >= n_rows || rowlen[p] <= 0) continue;
+        int64_t b = rowptr[perm[p]], panel = 0;
+        for (int64_t k = 0; k < rowlen[p]; ++k) {
+            int64_t c = colind[b + k];
+            int64_t step = c / 65536 - panel;
+            panel = c / 65536;
+            lo_out[slot_of(slice_ptr, p, k, 1)] = (uint16_t)(c % 65536);
+            step_out[slot_of(slice_ptr, p, k, 1)] = (int32_t)step;
+            if (step > largest) largest = step;
+        }
+    }
+    return largest;
 }
 
 int64_t orc_sliced_offsets(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,

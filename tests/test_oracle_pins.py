@@ -645,6 +645,73 @@ def test_sliced_diag_decodes_to_the_columns(sigma, cap):
     assert reach == far and nb == (1 if far <= 127 else 2 if far <= 32767 else 4)
 
 
+def test_sliced_delta_and_panel_hand_example():
+    """Rows {3, 4, 300}, {}, {70000, 70001, 200000} in order, one slice of
+    length 3, element k of position p at slot 32 k + p.
+    Delta coding (O24): bases 3, 0, 70000; deltas 0, 1, 296 (row 0) and
+    0, 1, 129999 (row 2); the largest, 129999, needs more than 16 bits.
+    Panels of 65536 columns (O25): row 0 lies in panel 0 (offsets 3, 4, 300,
+    steps 0, 0, 0); row 2: 70000 = 65536 + 4464 (panel 1, step 1), 70001
+    (offset 4465, step 0), 200000 = 3 * 65536 + 3392 (step 2); largest step 2."""
+    A = _csr_rows([[3, 4, 300], [], [70000, 70001, 200000]], 300000)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=1, cap=1024)
+    base, d, big, nb = oracle.sliced_delta(A, perm, rowlen, sptr)
+    expect = np.zeros(96, np.int32)
+    expect[[32, 64]] = [1, 296]
+    expect[[34, 66]] = [1, 129999]
+    assert np.array_equal(d, expect)
+    assert list(base[:3]) == [3, 0, 70000] and not base[3:].any()
+    assert big == 129999 and nb == 0
+    lo, st, big_step = oracle.sliced_panel(A, perm, rowlen, sptr)
+    e_lo = np.zeros(96, np.uint16)
+    e_st = np.zeros(96, np.int32)
+    e_lo[[0, 32, 64]] = [3, 4, 300]
+    e_lo[[2, 34, 66]] = [4464, 4465, 3392]
+    e_st[[2, 34, 66]] = [1, 0, 2]
+    assert np.array_equal(lo, e_lo) and np.array_equal(st, e_st) and big_step == 2
+    # without column 200000 the largest delta is 296: 16-bit deltas
+    B = _csr_rows([[3, 4, 300], [], [70000, 70001]], 300000)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(B, sigma=1, cap=1024)
+    assert oracle.sliced_delta(B, perm, rowlen, sptr)[2:] == (296, 2)
+    # the width rule ("8 or 16 bits, never both") at its boundaries
+    assert [oracle.delta_bytes(v) for v in (0, 1, 255, 256, 65535, 65536, 1 << 30)] == [1, 1, 1, 2, 2, 0, 0]
+
+
+@pytest.mark.parametrize("sigma,cap,n_cols", [(1, 1000, 700), (64, 20, 700), (1, 1000, 3_000_000)])
+def test_sliced_delta_and_panel_decode_to_the_columns(sigma, cap, n_cols):
+    """A running sum of the deltas from the row base, and panel * 65536 +
+    offset with the panel a running sum of the steps, give back every column
+    in the slices (rows sorted or not, long rows left out); padding holds 0;
+    the reported largest delta and step are the largest over the rows."""
+    g = np.random.default_rng(11 + sigma)
+    lengths = np.minimum(g.zipf(1.7, 400), 30)
+    lengths[:4] = [0, 1, 30, 2]
+    A = _csr_from_lengths(lengths.tolist(), n_cols=n_cols, seed=7)
+    perm, rowlen, slen, sptr, _ = oracle.sliced_layout(A, sigma=sigma, cap=cap)
+    col, _ = oracle.sliced_fill(A, perm, rowlen, sptr)
+    base, d, big, nb = oracle.sliced_delta(A, perm, rowlen, sptr)
+    lo, st, big_step = oracle.sliced_panel(A, perm, rowlen, sptr)
+    real = np.zeros(len(d), bool)
+    want_big = want_step = 0
+    rp, ci = A.rowptr.numpy(), A.colind.numpy().astype(np.int64)
+    for p in range(A.n_rows):
+        if rowlen[p] <= 0:
+            assert base[p] == 0
+            continue
+        idx = sptr[p // 32] + 32 * np.arange(rowlen[p]) + p % 32
+        real[idx] = True
+        cols = ci[rp[perm[p]]:rp[perm[p] + 1]]
+        assert d[idx[0]] == 0 and base[p] == cols[0]
+        assert np.array_equal(base[p] + np.cumsum(d[idx]), cols)
+        assert np.array_equal(np.cumsum(st[idx]) * 65536 + lo[idx], cols)
+        assert np.array_equal(col[idx], cols)
+        want_big = max(want_big, int(np.diff(cols).max(initial=0)))
+        want_step = max(want_step, int(np.diff(np.concatenate([[0], cols // 65536])).max()))
+    assert not d[~real].any() and not st[~real].any() and not lo[~real].any()
+    assert big == want_big and big_step == want_step
+    assert nb == (1 if big <= 255 else 2 if big <= 65535 else 0)
+
+
 @pytest.mark.parametrize("vec", [1, 4])
 def test_sliced_offsets_decode_to_the_columns(vec):
     """base + offset gives back every column of every row in the slices,
