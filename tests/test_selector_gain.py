@@ -138,3 +138,38 @@ def test_second_level_network_beats_the_structural_rules_on_held_out_matrices(da
     assert abs(rep["sliced_slowdown_vs_best_config"]["network"] - net) < 1e-9
     assert abs(rep["sliced_slowdown_vs_best_config"]["structural_rules"] - rules) < 1e-9
     assert abs(rep["slowdown_vs_best_overall"]["two_levels"] - _geomean(two / overall)) < 1e-9
+
+
+def test_fallback_margin_is_calibrated_and_its_effect_is_as_reported(data):
+    """The committed model's fallback margin mu is the best point of the
+    out-of-fold curve in the report (0 unless a positive margin is strictly
+    better there), and the report's held-out fallback rate and slowdown with
+    fallback follow from the committed data: the oracle's logits, and the
+    library's profiling rule where the top-two margin is below mu."""
+    import json
+    build()
+    d, P, variants, k = data
+    raw = open(os.path.join(DATA, "selector_mlp.bin"), "rb").read()
+    n_par = sum(int(np.prod(P[n].shape)) for n in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    mu = float(np.frombuffer(raw, np.float32, 1, 20 + 4 * (32 + n_par) + 4 * k)[0])
+    rep = json.load(open(os.path.join(DATA, "selector_report.json")))
+    assert mu == pytest.approx(rep["min_margin"], abs=1e-7)
+    curve = rep["margin_calibration"]["curve"]
+    chosen = min(curve, key=lambda c: abs(c["mu"] - mu))
+    assert chosen["slowdown"] == min(c["slowdown"] for c in curve)
+    if mu == 0.0:
+        assert all(c["slowdown"] >= curve[0]["slowdown"] for c in curve)
+    test = np.where(d["seed"] % 5 == 0)[0]
+    times = d["times"][test]
+    logits = oracle.mlp_forward_f32(P, d["vec"][test])
+    srt = np.sort(logits, 1)
+    margin = srt[:, -1] - srt[:, -2]
+    rule = []
+    for s in d["prof"][test]:
+        p = sp.Profile()
+        p.s_noxmiss, p.s_inflate, p.s_balance = (float(v) for v in s)
+        rule.append(sp.spmv_select(profile=p).variant)
+    pick = np.where(margin < mu, np.array(rule), variants[logits.argmax(1)])
+    slow = _geomean(times[np.arange(len(test)), pick] / times.min(1))
+    assert slow == pytest.approx(rep["test"]["slowdown_vs_best_geomean"]["mlp_with_fallback"], rel=1e-9)
+    assert float(np.mean(margin < mu)) == rep["test"]["fallback_rate"]
