@@ -600,6 +600,46 @@ def run_cg(args):
     return 0
 
 
+def run_coding(args):
+    """Column-index forms of SLICED with FP64 values on the four benchmark
+    matrices, each in SLICED's automatic layout: 32-bit columns; offsets
+    from the row index in 8 or 16 bits where they fit (index_bytes); Table 2's
+    delta coding, 8 or 16 bits (index_coding 1, which falls back to panels
+    for wide rows); the column-blocked form (index_coding 2).  Time per SpMV
+    (CUDA events, mean of 20 after 3 warm-ups), the format's own bytes, and
+    whether y equals the 32-bit form's bit for bit (the same DFMA chain)."""
+    import torch
+    import paper_1511_02494_gb300 as sp
+    import synth
+    from paper_1511_02494_gb300.build import build
+    build()
+    out = {"mode": "column_coding", "rows": []}
+    for A in synth.four_class_set():
+        dA = sp.DeviceCSR.from_host(A)
+        x = synth.uniform_vector(A.n_cols, 0).cuda()
+        y0 = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(y0)
+        base = None
+        for form, kw in (("int32", {}), ("row_offset", {"index_bytes": 1}),
+                         ("delta", {"index_coding": 1}), ("panel", {"index_coding": 2})):
+            P = sp.spmv_prepare(dA, sp.make_choice("sliced", **kw))
+            info = P.info()
+            ms = _time_ms(lambda: sp.spmv(P, x, y), reps=20)
+            sp.spmv(P, x, y)
+            if base is None:
+                base = ms
+                y0.copy_(y)
+            torch.cuda.synchronize()
+            out["rows"].append({"matrix": A.name, "form": form, "index_coding": info.index_coding,
+                                "index_bytes": info.index_bytes, "ms": round(ms, 5),
+                                "vs_int32": round(base / ms, 3), "format_bytes": info.min_bytes,
+                                "csr_gbs": round(A.min_bytes() / (ms * 1e-3) / 1e9, 1),
+                                "same_y_as_int32": bool(torch.equal(y, y0))})
+            P.free()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_features(args):
     """Feature extraction (Table 1) on the four-class matrices: wall time of
     spmv_features (kernel, readback, host derivation) against the selected
@@ -736,6 +776,7 @@ def main():
     ap.add_argument("--batch-form", default="both", choices=["both", "variant", "sliced"],
                     help="--batch: which persistent form(s) to run")
     ap.add_argument("--features", action="store_true", help="feature extraction report")
+    ap.add_argument("--coding", action="store_true", help="column-index forms of SLICED report")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -745,6 +786,8 @@ def main():
         return run_cg(args)
     if args.features:
         return run_features(args)
+    if args.coding:
+        return run_coding(args)
     if args.batch:
         return run_batch(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)

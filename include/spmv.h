@@ -214,6 +214,20 @@ typedef struct {
                             GB300 the 32-bit form is as fast or faster (the
                             narrower index stream does not shorten the
                             FP64-issue-bound kernel), hence the default. */
+    int32_t index_coding; /* SLICED with FP64 values: 0 = as index_bytes says;
+                            1 = Table 2's delta coding (Section 3.3): each
+                            column stored as its difference from the
+                            previous column of its row, the row's first
+                            column as a 32-bit base per position, in 8 bits
+                            when every delta in the slices' rows is at most
+                            255, else in 16 bits when at most 65535 (one
+                            width per matrix); when neither fits, as 2;
+                            2 = column-blocked: each column as its 16-bit
+                            offset inside a panel of 65536 columns plus an
+                            8-bit step from the previous element's panel,
+                            when every step is at most 255; else 32-bit
+                            columns.  Coded columns run one slice per warp
+                            (threads_per_row 0 or 1). */
 } spmv_choice_t;
 
 /* A matrix prepared for one variant (opaque).  It borrows A's arrays and owns
@@ -235,9 +249,14 @@ typedef struct {
     int32_t launches;      /* kernels one spmv call launches (0 when n_rows = 0) */
     int32_t index_bytes;   /* SLICED with FP64 values: bytes per stored column,
                               4 (the column), 2 or 1 (column - row, int16 or
-                              int8); 4 for the other variants                 */
+                              int8, or with index_coding 1 the delta), 3
+                              (index_coding 2: 16-bit panel offset + 8-bit
+                              step); 4 for the other variants                 */
     int64_t n_long_rows;   /* SLICED: rows above the length cap, computed from
                               CSR in segments; 0 for the other variants       */
+    int32_t index_coding;  /* SLICED with FP64 values: the column coding in
+                              use, 0, 1 (deltas) or 2 (panels), as in
+                              spmv_choice_t; 0 for the other variants         */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */
@@ -263,11 +282,22 @@ typedef enum {
     SPMV_EXPORT_SLICE_VAL = 11, /* SLICED: [slice_ptr[S]] values in value_type          */
     SPMV_EXPORT_SLICE_OFF16 = 12, /* SLICED, 16-bit offsets: uint16 [slice_ptr[S]]
                                    column - row base                                   */
-    SPMV_EXPORT_SLICE_ROWBASE = 13, /* SLICED, 16-bit offsets: int32 [32 S] first column
+    SPMV_EXPORT_SLICE_ROWBASE = 13, /* SLICED, 16-bit offsets (FP32/BF16 values) or
+                                   deltas (index_coding 1): int32 [32 S] first column
                                    of each position's row (0 where none)               */
-    SPMV_EXPORT_SLICE_DIAG = 14   /* SLICED, FP64 values, index_bytes 2 or 1: int16 or
+    SPMV_EXPORT_SLICE_DIAG = 14,  /* SLICED, FP64 values, index_bytes 2 or 1: int16 or
                                      int8 [slice_ptr[S]] column - row, column-major
                                      like SLICE_COL, 0 in padding                  */
+    SPMV_EXPORT_SLICE_DELTA = 15, /* SLICED, index_coding 1: uint8 or uint16
+                                     (index_bytes) [slice_ptr[S]] column - previous
+                                     column of the row, 0 for a row's first element
+                                     and in padding, column-major like SLICE_COL   */
+    SPMV_EXPORT_SLICE_PANEL_LO = 16,   /* SLICED, index_coding 2: uint16 [slice_ptr[S]]
+                                     column mod 65536, 0 in padding                */
+    SPMV_EXPORT_SLICE_PANEL_STEP = 17  /* SLICED, index_coding 2: uint8 [slice_ptr[S]]
+                                     panel (column / 65536) minus the previous
+                                     element's panel (0 before a row's first
+                                     element), 0 in padding                        */
 } spmv_export;
 
 /* ---- status ---------------------------------------------------------- */

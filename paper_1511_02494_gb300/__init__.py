@@ -19,6 +19,7 @@ from ._abi import (  # noqa: F401  (re-exported)
     EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
     EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
     EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE, EXPORT_SLICE_DIAG,
+    EXPORT_SLICE_DELTA, EXPORT_SLICE_PANEL_LO, EXPORT_SLICE_PANEL_STEP,
     declare,
 )
 
@@ -178,7 +179,7 @@ ACC_DEFAULT, ACC_F64, ACC_F32 = 0, 1, 2
 
 
 def make_choice(variant, threads_per_row=0, block_nnz=0, items_per_warp=0,
-                value_type=VAL_F64, accumulate=ACC_DEFAULT, index_bytes=0) -> Choice:
+                value_type=VAL_F64, accumulate=ACC_DEFAULT, index_bytes=0, index_coding=0) -> Choice:
     v = VARIANT_IDS[variant] if isinstance(variant, str) else int(variant)
     c = Choice()
     c.variant, c.cls = v, -1
@@ -186,6 +187,7 @@ def make_choice(variant, threads_per_row=0, block_nnz=0, items_per_warp=0,
     c.value_type = value_type
     c.accumulate = accumulate
     c.index_bytes = index_bytes
+    c.index_coding = index_coding
     return c
 
 

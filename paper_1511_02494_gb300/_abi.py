@@ -14,7 +14,7 @@ VAL_F64, VAL_F32, VAL_BF16 = 0, 1, 2
 (EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
  EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
  EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE,
- EXPORT_SLICE_DIAG) = range(15)
+ EXPORT_SLICE_DIAG, EXPORT_SLICE_DELTA, EXPORT_SLICE_PANEL_LO, EXPORT_SLICE_PANEL_STEP) = range(18)
 
 
 class CSR(C.Structure):
@@ -61,7 +61,8 @@ class Choice(C.Structure):
     _fields_ = [("variant", C.c_int32), ("cls", C.c_int32), ("threads_per_row", C.c_int32),
                 ("block_nnz", C.c_int32), ("items_per_warp", C.c_int32),
                 ("value_type", C.c_int32), ("margin", C.c_float), ("used_fallback", C.c_int32),
-                ("source", C.c_int32), ("accumulate", C.c_int32), ("index_bytes", C.c_int32)]
+                ("source", C.c_int32), ("accumulate", C.c_int32), ("index_bytes", C.c_int32),
+                ("index_coding", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,7 +74,8 @@ class PreparedInfo(C.Structure):
         [(n, C.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_blocks", "n_wide_rows",
                                   "owned_bytes", "min_bytes")] + \
         [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32),
-         ("launches", C.c_int32), ("index_bytes", C.c_int32), ("n_long_rows", C.c_int64)]
+         ("launches", C.c_int32), ("index_bytes", C.c_int32), ("n_long_rows", C.c_int64),
+         ("index_coding", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -162,7 +162,8 @@ int64_t min_bytes_of(const spmv_prepared_t* P)
         const SlicedPlan& d = P->sl;
         const int vb = d.value_type == SPMV_VAL_F64 ? 8 : d.value_type == SPMV_VAL_F32 ? 4 : 2;
         const int cb = d.value_type == SPMV_VAL_F64 ? d.cbytes : (d.off16 ? 2 : 4);
-        return (int64_t)(vb + cb) * A.nnz + 128 * d.n_slices * (d.off16 ? 2 : 1) + 12 * d.n_slices +
+        return (int64_t)(vb + cb) * A.nnz + 128 * d.n_slices * (d.off16 || d.coding == 1 ? 2 : 1) +
+               12 * d.n_slices +
                (d.sigma > 1 ? 4 * A.n_rows : 0) + 12 * (int64_t)d.n_long + 36 * (int64_t)d.n_seg +
                8 * A.n_cols + (d.acc32 ? 8 * A.n_cols : 0) + 8 * A.n_rows;
     }
@@ -338,6 +339,14 @@ spmv_status check_choice(const spmv_choice_t* c)
     if (c->index_bytes != 0 && c->index_bytes != 4 &&
         (c->variant != SPMV_V7_SLICED || c->value_type != SPMV_VAL_F64))
         return fail(SPMV_ERR_UNSUPPORTED, "narrow column indices only in SLICED with FP64 values");
+    if (c->index_coding < 0 || c->index_coding > 2)
+        return fail(SPMV_ERR_INVALID_ARG, "index_coding must be 0, 1 (deltas) or 2 (column panels)");
+    if (c->index_coding != 0 && (c->variant != SPMV_V7_SLICED || c->value_type != SPMV_VAL_F64))
+        return fail(SPMV_ERR_UNSUPPORTED, "coded column indices only in SLICED with FP64 values");
+    if (c->index_coding != 0 && (c->index_bytes == 1 || c->index_bytes == 2))
+        return fail(SPMV_ERR_INVALID_ARG, "index_coding replaces the row offsets of index_bytes 1 or 2");
+    if (c->index_coding != 0 && c->threads_per_row > 1)
+        return fail(SPMV_ERR_UNSUPPORTED, "coded column indices run one slice per warp (threads_per_row 0 or 1)");
     if (c->accumulate < 0 || c->accumulate > 2)
         return fail(SPMV_ERR_INVALID_ARG, "accumulate must be 0 (by value type), 1 (FP64) or 2 (FP32)");
     if (c->accumulate == 2 && (!lowp_ok || c->value_type == SPMV_VAL_F64))
@@ -623,6 +632,7 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.launches = launches_of(P);
     i.index_bytes = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.cbytes : 4;
     i.n_long_rows = P->c.variant == SPMV_V7_SLICED ? P->sl.n_long : 0;
+    i.index_coding = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.coding : 0;
     *info = i;
     return SPMV_OK;
 }
@@ -683,10 +693,26 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
             if (v == SPMV_V7_SLICED && P->sl.off16) { src = P->sl.off; size = 2 * P->sl.tot; }
             break;
         case SPMV_EXPORT_SLICE_ROWBASE:
-            if (v == SPMV_V7_SLICED && P->sl.off16) { src = P->sl.rowbase; size = 4 * 32 * P->sl.n_slices; }
+            if (v == SPMV_V7_SLICED && (P->sl.off16 || P->sl.coding == 1)) {
+                src = P->sl.rowbase;
+                size = 4 * 32 * P->sl.n_slices;
+            }
+            break;
+        case SPMV_EXPORT_SLICE_DELTA:
+            if (v == SPMV_V7_SLICED && P->sl.coding == 1) {
+                src = P->sl.scol;
+                size = (int64_t)P->sl.cbytes * P->sl.tot;
+            }
+            break;
+        case SPMV_EXPORT_SLICE_PANEL_LO:
+            if (v == SPMV_V7_SLICED && P->sl.coding == 2) { src = P->sl.scol; size = 2 * P->sl.tot; }
+            break;
+        case SPMV_EXPORT_SLICE_PANEL_STEP:
+            if (v == SPMV_V7_SLICED && P->sl.coding == 2) { src = P->sl.step; size = P->sl.tot; }
             break;
         case SPMV_EXPORT_SLICE_DIAG:
-            if (v == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 && P->sl.cbytes < 4) {
+            if (v == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 && P->sl.cbytes < 4 &&
+                P->sl.coding == 0) {
                 src = P->sl.scol;
                 size = (int64_t)P->sl.cbytes * P->sl.tot;
             }

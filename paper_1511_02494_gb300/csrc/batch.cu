@@ -288,10 +288,13 @@ spmv_status create_from_prepared(const spmv_prepared_t* const* P, int32_t count,
         // many DFMAs as its longest row) and for SLICED with FP32/BF16 values
         // (the batch sums FP64).  The other variants run as CSR rows of their
         // prepared lanes.
+        // (a SLICED matrix with coded columns, a form the batch kernel does
+        // not decode, is laid out anew like one with FP32/BF16 values)
+        const bool coded = Pm->c.variant == SPMV_V7_SLICED && Pm->sl.coding != 0;
         const bool own_sliced = all_sliced
-            ? (Pm->c.variant != SPMV_V7_SLICED || Pm->c.value_type != SPMV_VAL_F64)
+            ? (Pm->c.variant != SPMV_V7_SLICED || Pm->c.value_type != SPMV_VAL_F64 || coded)
             : (Pm->c.variant == SPMV_V3_MERGE || Pm->c.variant == SPMV_V4_DYNAMIC ||
-               (Pm->c.variant == SPMV_V7_SLICED && Pm->c.value_type != SPMV_VAL_F64));
+               (Pm->c.variant == SPMV_V7_SLICED && (Pm->c.value_type != SPMV_VAL_F64 || coded)));
         if (own_sliced) {
             spmv_choice_t c{};
             c.variant = SPMV_V7_SLICED;

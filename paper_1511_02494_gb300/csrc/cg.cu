@@ -269,7 +269,7 @@ k_sliced_dot(SlArgs a, const double* __restrict__ p, const float* __restrict__ p
 
 bool fusable(const spmv_prepared* P)
 {
-    return P->c.variant == SPMV_V7_SLICED && P->sl.n_long == 0 && P->A.n_rows > 0;
+    return P->c.variant == SPMV_V7_SLICED && P->sl.n_long == 0 && P->sl.coding == 0 && P->A.n_rows > 0;
 }
 
 unsigned sliced_dot_grid(const spmv_prepared* P)

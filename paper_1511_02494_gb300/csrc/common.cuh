@@ -71,7 +71,10 @@ struct SlicedPlan {
     int* perm = nullptr;         // [n_rows] position -> row (sigma > 1 only)
     int* col = nullptr;          // [tot] column-major slice contents (32-bit columns)
     void* scol = nullptr;        // FP64 values: [tot] stored columns, cbytes each
-    int cbytes = 4;              // 4: columns; 2 / 1: column - row in int16 / int8
+    int cbytes = 4;              // bytes per stored column: 4 columns; 2 / 1 column - row (coding 0)
+                                 // or delta (coding 1); 3 panel offset + step (coding 2)
+    int coding = 0;              // FP64 columns: 0 columns / row offsets, 1 deltas, 2 panels
+    uint8_t* step = nullptr;     // [tot] coding 2: panel step from the previous element
     double* val = nullptr;       // [tot]
     int* long_rows = nullptr;    // [n_long], ascending
     int* seg_off = nullptr;      // [n_long + 1] first segment of each long row

@@ -154,6 +154,64 @@ __global__ void k_sl_reach(int64_t n_slices, const int* __restrict__ rp, const i
     atomicMax(reach, (unsigned)(m < 0 ? 0 : (m > 0x7fffffff ? 0x7fffffff : m)));
 }
 
+// Coded columns of the FP64 layout: the largest delta between consecutive
+// columns of a row (MODE 1) or the largest step between the 65536-column
+// panels of consecutive elements, the first from panel 0 (MODE 2), over the
+// rows in the slices
+template <int MODE>
+__global__ void k_sl_code_reach(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const int* __restrict__ perm, const int* __restrict__ rowlen,
+                                unsigned* __restrict__ reach)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 32 * n_slices) return;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int64_t b = rp[perm ? perm[p] : p];
+    unsigned m = 0;
+    int prev = MODE == 1 ? ci[b] : 0;
+    for (int k = MODE == 1 ? 1 : 0; k < len; ++k) {
+        const int c = ci[b + k];
+        const unsigned d = MODE == 1 ? (unsigned)(c - prev) : (unsigned)((c >> 16) - (prev >> 16));
+        m = max(m, d);
+        prev = c;
+    }
+    atomicMax(reach, m);
+}
+
+// coded contents (padding was zeroed beforehand): MODE 1 deltas and row
+// bases, MODE 2 panel offsets and steps; a warp per slice, a lane per row
+template <int MODE, typename DT>
+__global__ void k_sl_fill_coded(int64_t n_slices, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const double* __restrict__ v, const int* __restrict__ perm,
+                                const int* __restrict__ rowlen, const int64_t* __restrict__ slice_ptr,
+                                DT* __restrict__ cs, uint8_t* __restrict__ step, int* __restrict__ rowbase,
+                                double* __restrict__ val)
+{
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    if (len <= 0) return;
+    const int64_t b = rp[perm ? perm[p] : (int)p];
+    const int64_t q0 = slice_ptr[s] + lane;
+    if (MODE == 1) rowbase[p] = ci[b];
+    int prev = MODE == 1 ? ci[b] : 0;
+    for (int k = 0; k < len; ++k) {
+        const int c = ci[b + k];
+        const int64_t q = q0 + (int64_t)k * 32;
+        if (MODE == 1) {
+            cs[q] = (DT)(c - prev);
+        } else {
+            cs[q] = (DT)(c & 0xffff);
+            step[q] = (uint8_t)((c >> 16) - (prev >> 16));
+        }
+        prev = c;
+        val[q] = v[b + k];
+    }
+}
+
 // rows longer than cap, appended with one atomic per warp
 __global__ void k_sl_long_list(int64_t n_rows, const int* __restrict__ rp, int cap,
                                int* __restrict__ list, unsigned* __restrict__ count)
@@ -187,6 +245,23 @@ k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict
     const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
     if (s >= n_slices) return;  // whole warps only
     slice_rows<U, CT>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
+}
+
+// One slice per warp with coded columns (slice_value_coded).
+template <int U, int MODE, typename DT>
+__global__ void __launch_bounds__(kSB, 8)
+k_sliced_coded(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+               const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+               const DT* __restrict__ cs, const uint8_t* __restrict__ step,
+               const int* __restrict__ rowbase, const double* __restrict__ val,
+               const double* __restrict__ x, double* __restrict__ y)
+{
+    const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
+    if (s >= n_slices) return;  // whole warps only
+    int row;
+    const double v = slice_value_coded<U, MODE, DT>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm,
+                                                    cs, step, rowbase, val, x, &row);
+    if (row >= 0) y[row] = v;
 }
 
 // R consecutive slices per warp (slice_rows_multi), for short slices whose
@@ -263,7 +338,7 @@ __global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int
 // partial, and the warp that finishes the row's last one (an atomic ticket
 // per row) sums the partials in segment order, as k_sliced_fixup does, and
 // resets the ticket for the next call.  Nothing waits on another warp.
-template <int U, int R, int B, typename CT>
+template <int U, int R, int B, typename CT, int MODE = 0, typename DT = uint8_t>
 __global__ void __launch_bounds__(kSB, B)
 k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
               const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
@@ -274,7 +349,8 @@ k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
               const int* __restrict__ rowlen, const int* __restrict__ slice_len,
               const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
               const CT* __restrict__ col, const double* __restrict__ val,
-              const double* __restrict__ x, double* __restrict__ y)
+              const double* __restrict__ x, double* __restrict__ y,
+              const uint8_t* __restrict__ step, const int* __restrict__ rowbase)
 {
     const int lane = threadIdx.x & 31;
     if (blockIdx.x < seg_blocks) {
@@ -302,7 +378,14 @@ k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
         return;
     }
     const int64_t s0 = ((int64_t)(blockIdx.x - seg_blocks) * kSB + threadIdx.x) >> 5;
-    if constexpr (R == 1) {
+    if constexpr (MODE != 0) {
+        if (s0 >= n_slices) return;
+        int row;
+        const double v = slice_value_coded<U, MODE, DT>(s0, lane, rowlen, slice_len, slice_ptr, perm,
+                                                        reinterpret_cast<const DT*>(col), step, rowbase,
+                                                        val, x, &row);
+        if (row >= 0) y[row] = v;
+    } else if constexpr (R == 1) {
         if (s0 >= n_slices) return;
         slice_rows<U, CT>(s0, lane, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
     } else {
@@ -520,7 +603,33 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         // columns as offsets from the row index in 8 or 16 bits when the
         // caller allows it and every row in the slices stays that close to
         // its diagonal, else 32-bit
-        const int allowed = P->c.index_bytes == 0 ? 4 : P->c.index_bytes;
+        // coded columns (Table 2's deltas, or panels) when asked for and
+        // every row in the slices fits: deltas in 8 bits, else 16, else (or
+        // when panels were asked for) 16-bit panel offsets with 8-bit steps
+        d.coding = 0;
+        if (P->c.index_coding != 0 && d.n_slices > 0) {
+            auto code_reach = [&](int mode, unsigned* out) -> spmv_status {
+                SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
+                const unsigned g = (unsigned)((32 * d.n_slices + kSB - 1) / kSB);
+                if (mode == 1) k_sl_code_reach<1><<<g, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, permp, d.rowlen, d.count);
+                else k_sl_code_reach<2><<<g, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, permp, d.rowlen, d.count);
+                SPMV_CUDA_TRY(cudaGetLastError());
+                SPMV_CUDA_TRY(cudaMemcpyAsync(out, d.count, 4, cudaMemcpyDeviceToHost, s));
+                SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+                return SPMV_OK;
+            };
+            unsigned r = 0;
+            if (P->c.index_coding == 1) {
+                if ((st = code_reach(1, &r)) != SPMV_OK) return st;
+                if (r <= 255) { d.coding = 1; d.cbytes = 1; }
+                else if (r <= 65535) { d.coding = 1; d.cbytes = 2; }
+            }
+            if (d.coding == 0) {
+                if ((st = code_reach(2, &r)) != SPMV_OK) return st;
+                if (r <= 255) { d.coding = 2; d.cbytes = 3; }
+            }
+        }
+        const int allowed = d.coding != 0 ? 4 : (P->c.index_bytes == 0 ? 4 : P->c.index_bytes);
         unsigned reach = 0;
         if (d.n_slices > 0 && allowed < 4) {
             SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
@@ -530,15 +639,37 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
             SPMV_CUDA_TRY(cudaMemcpyAsync(&reach, d.count, 4, cudaMemcpyDeviceToHost, s));
             SPMV_CUDA_TRY(cudaStreamSynchronize(s));
         }
-        d.cbytes = std::max(allowed, reach <= 127 ? 1 : (reach <= 32767 ? 2 : 4));
+        if (d.coding == 0) d.cbytes = std::max(allowed, reach <= 127 ? 1 : (reach <= 32767 ? 2 : 4));
         P->c.index_bytes = d.cbytes;
-        if ((st = prepared_alloc(P, &d.scol, (int64_t)d.cbytes * tot1)) != SPMV_OK ||
+        P->c.index_coding = d.coding;
+        if (d.coding != 0) P->c.threads_per_row = 1;  // coded columns: one slice per warp
+        const int64_t sbytes = d.coding == 2 ? 2 : d.cbytes;  // panel offsets are 16-bit
+        if ((st = prepared_alloc(P, &d.scol, sbytes * tot1)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.val), 8 * tot1)) != SPMV_OK)
             return st;
         if (d.cbytes == 4) d.col = static_cast<int*>(d.scol);
-        SPMV_CUDA_TRY(cudaMemsetAsync(d.scol, 0, (int64_t)d.cbytes * tot1, s));
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.scol, 0, sbytes * tot1, s));
         SPMV_CUDA_TRY(cudaMemsetAsync(d.val, 0, 8 * tot1, s));
-        if (d.n_slices > 0) {
+        if (d.coding == 2) {
+            if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.step), tot1)) != SPMV_OK) return st;
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.step, 0, tot1, s));
+        }
+        if (d.coding == 1) {
+            if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.rowbase), 4 * std::max<int64_t>(n_pos, 1))) != SPMV_OK)
+                return st;
+            SPMV_CUDA_TRY(cudaMemsetAsync(d.rowbase, 0, 4 * std::max<int64_t>(n_pos, 1), s));
+        }
+        if (d.n_slices > 0 && d.coding != 0) {
+#define SPMV_SL_FILL_CODED(MODE, DT)                                                                  \
+    k_sl_fill_coded<MODE, DT><<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, \
+                                                        d.rowlen, d.slice_ptr, static_cast<DT*>(d.scol), \
+                                                        d.step, d.rowbase, d.val)
+            if (d.coding == 1 && d.cbytes == 1) SPMV_SL_FILL_CODED(1, uint8_t);
+            else if (d.coding == 1) SPMV_SL_FILL_CODED(1, uint16_t);
+            else SPMV_SL_FILL_CODED(2, uint16_t);
+#undef SPMV_SL_FILL_CODED
+            SPMV_CUDA_TRY(cudaGetLastError());
+        } else if (d.n_slices > 0) {
 #define SPMV_SL_FILL64(CT)                                                                           \
     k_sl_fill<CT><<<slice_grid, kSB, 0, s>>>(d.n_slices, A.rowptr, A.colind, A.val, permp, d.rowlen, \
                                              d.slice_ptr, static_cast<CT*>(d.scol), d.val)
@@ -665,15 +796,35 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     k_sliced_long<U, RR, B, CT><<<blocks, kSB, 0, s>>>(                                           \
         d.n_seg, seg_blocks, d.n_slices, d.seg_be, d.seg_row, d.seg_fix, d.fix, d.long_rows,       \
         d.seg_off, d.ticket, d.partial, A.colind, A.val, d.rowlen, d.slice_len, d.slice_ptr, perm,  \
-        static_cast<const CT*>(d.scol), d.val, x, y)
+        static_cast<const CT*>(d.scol), d.val, x, y, nullptr, nullptr)
 #define SPMV_SL_LONG_CT(CT)                                                                          \
         if (R == 4) SPMV_SL_LONG(1, 4, 4, CT); else if (R == 2) SPMV_SL_LONG(2, 2, 6, CT);           \
         else SPMV_SL_LONG(4, 1, 8, CT);
-        if (d.cbytes == 1) { SPMV_SL_LONG_CT(int8_t) }
+#define SPMV_SL_LONG_CODED(MODE, DT)                                                                \
+    k_sliced_long<4, 1, 8, int, MODE, DT><<<blocks, kSB, 0, s>>>(                                   \
+        d.n_seg, seg_blocks, d.n_slices, d.seg_be, d.seg_row, d.seg_fix, d.fix, d.long_rows,       \
+        d.seg_off, d.ticket, d.partial, A.colind, A.val, d.rowlen, d.slice_len, d.slice_ptr, perm,  \
+        static_cast<const int*>(d.scol), d.val, x, y, d.step, d.rowbase)
+        if (d.coding == 1 && d.cbytes == 1) { SPMV_SL_LONG_CODED(1, uint8_t); }
+        else if (d.coding == 1) { SPMV_SL_LONG_CODED(1, uint16_t); }
+        else if (d.coding == 2) { SPMV_SL_LONG_CODED(2, uint16_t); }
+        else if (d.cbytes == 1) { SPMV_SL_LONG_CT(int8_t) }
         else if (d.cbytes == 2) { SPMV_SL_LONG_CT(int16_t) }
         else { SPMV_SL_LONG_CT(int) }
+#undef SPMV_SL_LONG_CODED
 #undef SPMV_SL_LONG_CT
 #undef SPMV_SL_LONG
+        return cudaGetLastError();
+    }
+    if (d.value_type == SPMV_VAL_F64 && d.coding != 0) {
+#define SPMV_SL_CODED(MODE, DT)                                                                     \
+    k_sliced_coded<4, MODE, DT><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr,  \
+                                                     perm, static_cast<const DT*>(d.scol), d.step,    \
+                                                     d.rowbase, d.val, x, y)
+        if (d.coding == 1 && d.cbytes == 1) SPMV_SL_CODED(1, uint8_t);
+        else if (d.coding == 1) SPMV_SL_CODED(1, uint16_t);
+        else SPMV_SL_CODED(2, uint16_t);
+#undef SPMV_SL_CODED
         return cudaGetLastError();
     }
     if (d.value_type == SPMV_VAL_F64) {

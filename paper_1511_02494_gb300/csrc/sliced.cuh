@@ -134,6 +134,66 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
         if (row[r] >= 0) y[row[r]] = acc[r];
 }
 
+// FP64 values with coded columns.  A lane walks its row in order, so a
+// column is decoded from the one before it with integer operations:
+//   MODE 1, Table 2's delta coding: cs (DT = uint8_t or uint16_t) holds the
+//     column minus the previous column of the row (0 for the row's first
+//     element), rowbase[p] the row's first column;
+//   MODE 2, the column-blocked form: cs (uint16_t) holds the column modulo
+//     65536, step the step from the previous element's 65536-column panel
+//     (the first element's from panel 0).
+// Otherwise as slice_value: U elements of the row in flight, one DFMA chain.
+template <int U, int MODE, typename DT>
+__device__ __forceinline__ double slice_value_coded(int64_t s, int lane, const int* __restrict__ rowlen,
+                                                    const int* __restrict__ slice_len,
+                                                    const int64_t* __restrict__ slice_ptr,
+                                                    const int* __restrict__ perm,
+                                                    const DT* __restrict__ cs,
+                                                    const uint8_t* __restrict__ step,
+                                                    const int* __restrict__ rowbase,
+                                                    const double* __restrict__ val,
+                                                    const double* __restrict__ x, int* row)
+{
+    const int64_t p = s * 32 + lane;
+    const int len = rowlen[p];
+    const int L = slice_len[s];
+    const int64_t q0 = slice_ptr[s] + lane;
+    const DT* __restrict__ dp = cs + q0;
+    const double* __restrict__ vp = val + q0;
+    int c = 0;  // MODE 1: the running column; MODE 2: the running panel << 16
+    if constexpr (MODE == 1) c = rowbase[p];
+    double acc = 0.0;
+    for (int k = 0; k < L; k += U) {
+        int cc[U];
+        double a[U], xv[U];
+        int lo[U], hi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = k + u < len;
+            lo[u] = ok ? (int)__ldcs(dp + (k + u) * 32) : 0;
+            if constexpr (MODE == 2) hi[u] = ok ? (int)__ldcs(step + q0 + (k + u) * 32) : 0;
+            a[u] = ok ? __ldcs(vp + (k + u) * 32) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if constexpr (MODE == 1) {
+                c += lo[u];
+                cc[u] = c;
+            } else {
+                c += hi[u] << 16;
+                cc[u] = c | lo[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = k + u < len ? ldx(x + cc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < len) acc = fma(a[u], xv[u], acc);
+    }
+    *row = len >= 0 ? (perm ? perm[p] : (int)p) : -1;
+    return acc;
+}
+
 // FP32 or BF16 values, 32-bit columns or 16-bit offsets from rowbase[p],
 // with four elements of a row side by side: element k of the row at
 // position p = 32 s + l sits at slot slice_ptr[s] + 128 (k / 4) + 4 l + k % 4,
