@@ -82,6 +82,8 @@ def _load():
                 "orc_profile_class": (i32, [C.c_double] * 6),
                 "orc_class_variant": (i32, [i32, P]),
                 "orc_static_partition": (None, [i64, P, i64, P]),
+                "orc_dyn_tiers": (None, [i64, P, i32, i32, P, P, P, P, P]),
+                "orc_sliced_segments": (i64, [i64, P, i32, i32, P, P, P, P, P, P, P]),
                 "orc_row_blocks": (None, [i64, P, i64, i64, P]),
                 "orc_merge_path": (None, [i64, P, i64, i64, P, P]),
                 "orc_compress_u16": (i64, [i64, P, P, P, P]),
@@ -228,6 +230,38 @@ def static_partition(A, n_workers: int) -> np.ndarray:
     out = np.empty(n_workers + 1, np.int64)
     _load().orc_static_partition(A.n_rows, _p(rp), n_workers, _p(out))
     return out
+
+
+def dyn_tiers(A, lim_s: int, seg: int):
+    """Tiers of the dynamic-schedule variant (Table 2, IMB): the rows with
+    lim_s < len <= 64, with 64 < len <= seg, with len > seg (ascending), and
+    the segment count of each long row."""
+    rp = _np(A.rowptr, np.int32)
+    n = max(A.n_rows, 1)
+    m1, m2, lr, sc = (np.empty(n, np.int32) for _ in range(4))
+    cnt = np.zeros(3, np.int64)
+    _load().orc_dyn_tiers(A.n_rows, _p(rp), lim_s, seg, _p(m1), _p(m2), _p(lr), _p(sc), _p(cnt))
+    a, b, c = (int(v) for v in cnt)
+    return m1[:a], m2[:b], lr[:c], sc[:c]
+
+
+def sliced_segments(A, cap: int, seg: int = 2048):
+    """Long rows of the sliced layout and their segment table: list, seg_off,
+    seg_be (n_seg x 2), seg_row, fix, seg_fix."""
+    rp = _np(A.rowptr, np.int32)
+    lens = np.diff(rp.astype(np.int64))
+    n_long = int((lens > cap).sum())
+    n_seg_max = int(((lens[lens > cap] + seg - 1) // seg).sum())
+    lst = np.empty(max(n_long, 1), np.int32)
+    off = np.empty(n_long + 1, np.int32)
+    be = np.empty(max(2 * n_seg_max, 2), np.int64)
+    srow = np.empty(max(n_seg_max, 1), np.int32)
+    fix = np.empty(max(n_long, 1), np.int32)
+    sfix = np.empty(max(n_seg_max, 1), np.int32)
+    nf = C.c_int64()
+    ns = int(_load().orc_sliced_segments(A.n_rows, _p(rp), cap, seg, _p(lst), _p(off), _p(be), _p(srow),
+                                         _p(fix), _p(sfix), C.byref(nf)))
+    return (lst[:n_long], off, be[:2 * ns].reshape(ns, 2), srow[:ns], fix[:nf.value], sfix[:ns])
 
 
 def row_blocks(A, block_nnz: int) -> np.ndarray:

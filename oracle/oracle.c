@@ -335,6 +335,63 @@ void orc_static_partition(int64_t n_rows, const int32_t *rowptr, int64_t n_worke
     bounds[n_workers] = n_rows;
 }
 
+/* Tiers of the dynamic-schedule variant (Table 2's IMB optimization with
+ * the rows split by length): rows with lim_s < len <= 64 (m1), with
+ * 64 < len <= seg (m2) and with len > seg (lrow), each list in ascending row
+ * order; a row of lrow is cut into seg_count = ceil(len / seg) segments.
+ * counts[0..2] = the three list lengths.  Rows of at most lim_s nonzeros
+ * are in no list (they run in contiguous chunks).                           */
+void orc_dyn_tiers(int64_t n_rows, const int32_t *rowptr, int32_t lim_s, int32_t seg,
+                   int32_t *m1, int32_t *m2, int32_t *lrow, int32_t *seg_count, int64_t *counts)
+{
+    int64_t a = 0, b = 0, c = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t len = rowptr[i + 1] - rowptr[i];
+        if (len <= lim_s) continue;
+        if (len <= 64) m1[a++] = (int32_t)i;
+        else if (len <= seg) m2[b++] = (int32_t)i;
+        else {
+            seg_count[c] = (int32_t)((len + seg - 1) / seg);
+            lrow[c++] = (int32_t)i;
+        }
+    }
+    counts[0] = a;
+    counts[1] = b;
+    counts[2] = c;
+}
+
+/* Long rows of the sliced layout (reading O22: rows above the cap are left
+ * out of the slices and computed from CSR): the rows longer than cap in
+ * ascending order (list); each cut into segments of seg nonzeros, seg_off
+ * the exclusive running count of segments per long row; per segment its CSR
+ * bounds seg_be[2j], seg_be[2j+1]; seg_row[j] its row when it is its row's
+ * only segment, else -1; fix the list indices of the rows with several
+ * segments (n_fix of them) and seg_fix[j] the index in fix of segment j's
+ * row, else -1.  Returns the number of segments.                            */
+int64_t orc_sliced_segments(int64_t n_rows, const int32_t *rowptr, int32_t cap, int32_t seg,
+                            int32_t *list, int32_t *seg_off, int64_t *seg_be, int32_t *seg_row,
+                            int32_t *fix, int32_t *seg_fix, int64_t *n_fix)
+{
+    int64_t q = 0, j = 0, t = 0;
+    seg_off[0] = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t b = rowptr[i], e = rowptr[i + 1];
+        if (e - b <= cap) continue;
+        int64_t k = (e - b + seg - 1) / seg;
+        list[q] = (int32_t)i;
+        for (int64_t s = 0; s < k; ++s, ++j) {
+            seg_be[2 * j] = b + s * seg;
+            seg_be[2 * j + 1] = b + (s + 1) * seg < e ? b + (s + 1) * seg : e;
+            seg_row[j] = k == 1 ? (int32_t)i : -1;
+            seg_fix[j] = k == 1 ? -1 : (int32_t)t;
+        }
+        if (k > 1) fix[t++] = (int32_t)q;
+        seg_off[++q] = (int32_t)j;
+    }
+    *n_fix = t;
+    return j;
+}
+
 /* Row blocks for the staged (stream) variant: block k owns the rows whose
  * first nonzero index lies in the window [k B, (k+1) B):
  * R_k = smallest i with rowptr[i] >= k B, R_{n_blocks} = N.  Linear scan.   */

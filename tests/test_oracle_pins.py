@@ -348,6 +348,68 @@ def test_static_partition_is_smallest_row_reaching_target(seed):
         assert b[-1] == A.n_rows and np.all(np.diff(b) >= 0)
 
 
+def _csr_lengths(lengths):
+    rp = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    n = int(rp[-1])
+    ci = np.concatenate([np.arange(L) for L in lengths]).astype(np.int32) if n else np.zeros(0, np.int32)
+    return synth.HostCSR(len(lengths), max(max(lengths, default=1), 1), torch.from_numpy(rp),
+                         torch.from_numpy(ci), torch.ones(n, dtype=torch.float64))
+
+
+def test_sliced_segments_hand_example():
+    """Row lengths 3, 5000, 1, 2048, 2049, 0 with cap 2 and segments of 2048:
+    long rows 0, 1, 3, 4 (ascending); segments 1, 3, 1, 2 -> offsets 0, 1, 4,
+    5, 7; row 1 = [3, 2051), [2051, 4099), [4099, 5003); row 4 starts at
+    7052: [7052, 9100), [9100, 9101); single-segment rows 0 and 3 write y
+    themselves; rows with several segments are list entries 1 and 3."""
+    A = _csr_lengths([3, 5000, 1, 2048, 2049, 0])
+    lst, off, be, srow, fix, sfix = oracle.sliced_segments(A, cap=2, seg=2048)
+    assert list(lst) == [0, 1, 3, 4] and list(off) == [0, 1, 4, 5, 7]
+    assert be.tolist() == [[0, 3], [3, 2051], [2051, 4099], [4099, 5003], [5004, 7052],
+                           [7052, 9100], [9100, 9101]]
+    assert list(srow) == [0, -1, -1, -1, 3, -1, -1]
+    assert list(fix) == [1, 3] and list(sfix) == [-1, 0, 0, 0, -1, 1, 1]
+
+
+@pytest.mark.parametrize("cap,seg", [(32, 2048), (1024, 2048), (0, 256)])
+def test_sliced_segments_cover_each_long_row(cap, seg):
+    A = synth.zipf_rows(4000, 4000, 1.3, 3500, seed=2)
+    lst, off, be, srow, fix, sfix = oracle.sliced_segments(A, cap, seg)
+    rp = A.rowptr.numpy().astype(np.int64)
+    lens = np.diff(rp)
+    assert np.array_equal(lst, np.flatnonzero(lens > cap))
+    for q, r in enumerate(lst):
+        segs = be[off[q]:off[q + 1]]
+        assert segs[0, 0] == rp[r] and segs[-1, 1] == rp[r + 1]
+        assert np.all(segs[1:, 0] == segs[:-1, 1]) and np.all(segs[:, 1] - segs[:, 0] <= seg)
+        assert np.all(segs[:, 1] > segs[:, 0])
+        single = off[q + 1] - off[q] == 1
+        assert np.all(srow[off[q]:off[q + 1]] == (r if single else -1))
+        if not single:
+            t = int(np.flatnonzero(fix == q)[0])
+            assert np.all(sfix[off[q]:off[q + 1]] == t)
+    assert len(fix) == int(np.sum(np.diff(off) > 1))
+
+
+def test_dyn_tiers_hand_example():
+    """lim_s 4, segments of 100: lengths 4 -> none; 5 and 64 -> m1; 65 and
+    100 -> m2; 101 -> long, 2 segments; 250 -> long, 3 segments."""
+    A = _csr_lengths([4, 5, 64, 65, 100, 101, 0, 250])
+    m1, m2, lr, sc = oracle.dyn_tiers(A, lim_s=4, seg=100)
+    assert list(m1) == [1, 2] and list(m2) == [3, 4]
+    assert list(lr) == [5, 7] and list(sc) == [2, 3]
+
+
+def test_dyn_tiers_partition_the_rows():
+    A = synth.zipf_rows(5000, 5000, 1.4, 3000, seed=3)
+    lens = np.diff(A.rowptr.numpy().astype(np.int64))
+    m1, m2, lr, sc = oracle.dyn_tiers(A, lim_s=16, seg=512)
+    assert np.array_equal(m1, np.flatnonzero((lens > 16) & (lens <= 64)))
+    assert np.array_equal(m2, np.flatnonzero((lens > 64) & (lens <= 512)))
+    assert np.array_equal(lr, np.flatnonzero(lens > 512))
+    assert np.array_equal(sc, -(-lens[lr] // 512))
+
+
 def test_row_blocks_cover_rows_by_window():
     A = synth.zipf_rows(2000, 2000, 1.6, 700, seed=4)
     rp = A.rowptr.numpy().astype(np.int64)
