@@ -294,10 +294,32 @@ typedef enum {
                                      and in padding, column-major like SLICE_COL   */
     SPMV_EXPORT_SLICE_PANEL_LO = 16,   /* SLICED, index_coding 2: uint16 [slice_ptr[S]]
                                      column mod 65536, 0 in padding                */
-    SPMV_EXPORT_SLICE_PANEL_STEP = 17  /* SLICED, index_coding 2: uint8 [slice_ptr[S]]
+    SPMV_EXPORT_SLICE_PANEL_STEP = 17, /* SLICED, index_coding 2: uint8 [slice_ptr[S]]
                                      panel (column / 65536) minus the previous
                                      element's panel (0 before a row's first
                                      element), 0 in padding                        */
+    SPMV_EXPORT_DYN_M1 = 18,      /* DYNAMIC: int32 [n_m1] rows with lim_s < len <= 64,
+                                     lim_s = min(16 threads_per_row, block_nnz), in
+                                     the order a prepare found them (atomics: the
+                                     set is fixed, the order is not)               */
+    SPMV_EXPORT_DYN_M2 = 19,      /* DYNAMIC: int32 [n_m2] rows with 64 < len <= block_nnz */
+    SPMV_EXPORT_DYN_LONG = 20,    /* DYNAMIC: int32 [n_long] rows with len > block_nnz  */
+    SPMV_EXPORT_DYN_SEG_OFF = 21, /* DYNAMIC: int32 [n_long + 1] first segment of each
+                                     long row (in DYN_LONG's order): the running sum of
+                                     ceil(len / block_nnz)                         */
+    SPMV_EXPORT_SLICE_LONG = 22,  /* SLICED: int32 [n_long_rows] rows above the cap,
+                                     ascending                                     */
+    SPMV_EXPORT_SLICE_SEG_OFF = 23,    /* SLICED: int32 [n_long_rows + 1] first segment
+                                     of each long row (segments of 2048 nonzeros)  */
+    SPMV_EXPORT_SLICE_SEG_BOUNDS = 24, /* SLICED: int64 [2 n_seg] CSR begin and end of
+                                     each segment                                  */
+    SPMV_EXPORT_SLICE_SEG_ROW = 25,    /* SLICED: int32 [n_seg] the segment's row when it
+                                     is its row's only segment, else -1            */
+    SPMV_EXPORT_SLICE_FIX = 26,   /* SLICED: int32 [n_fix] long-row list indices of the
+                                     rows with several segments                    */
+    SPMV_EXPORT_SLICE_SEG_FIX = 27     /* SLICED, FP64 values: int32 [n_seg] index in
+                                     SLICE_FIX of the segment's row, -1 for a row's
+                                     only segment                                  */
 } spmv_export;
 
 /* ---- status ---------------------------------------------------------- */
@@ -527,7 +549,10 @@ spmv_status spmv_host_async(spmv_prepared_t *P, const double *x_host, double *y_
 spmv_status spmv_prepared_info(const spmv_prepared_t *P, spmv_prepared_info_t *info);
 
 /* Copies one owned array of P (see spmv_export) into host memory dst of
- * `bytes` bytes (must equal the array's size).  Synchronizes `stream`. */
+ * `bytes` bytes (must equal the array's size; a mismatch fails with
+ * SPMV_ERR_INVALID_ARG and a message giving the size).  An empty array is
+ * exported with bytes = 0, and dst may then be NULL.  Synchronizes
+ * `stream`. */
 spmv_status spmv_prepared_export(const spmv_prepared_t *P, int32_t which, void *dst,
                                  int64_t bytes, spmv_stream_t stream);
 

@@ -20,6 +20,9 @@ from ._abi import (  # noqa: F401  (re-exported)
     EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
     EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE, EXPORT_SLICE_DIAG,
     EXPORT_SLICE_DELTA, EXPORT_SLICE_PANEL_LO, EXPORT_SLICE_PANEL_STEP,
+    EXPORT_DYN_M1, EXPORT_DYN_M2, EXPORT_DYN_LONG, EXPORT_DYN_SEG_OFF, EXPORT_SLICE_LONG,
+    EXPORT_SLICE_SEG_OFF, EXPORT_SLICE_SEG_BOUNDS, EXPORT_SLICE_SEG_ROW, EXPORT_SLICE_FIX,
+    EXPORT_SLICE_SEG_FIX,
     declare,
 )
 

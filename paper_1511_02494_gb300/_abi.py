@@ -14,7 +14,10 @@ VAL_F64, VAL_F32, VAL_BF16 = 0, 1, 2
 (EXPORT_ROW_BLOCKS, EXPORT_MERGE_ROWS, EXPORT_MERGE_NZ, EXPORT_ROWBASE, EXPORT_OFFSETS,
  EXPORT_VALUES, EXPORT_SLICE_PERM, EXPORT_SLICE_ROWLEN, EXPORT_SLICE_LEN, EXPORT_SLICE_PTR,
  EXPORT_SLICE_COL, EXPORT_SLICE_VAL, EXPORT_SLICE_OFF16, EXPORT_SLICE_ROWBASE,
- EXPORT_SLICE_DIAG, EXPORT_SLICE_DELTA, EXPORT_SLICE_PANEL_LO, EXPORT_SLICE_PANEL_STEP) = range(18)
+ EXPORT_SLICE_DIAG, EXPORT_SLICE_DELTA, EXPORT_SLICE_PANEL_LO, EXPORT_SLICE_PANEL_STEP,
+ EXPORT_DYN_M1, EXPORT_DYN_M2, EXPORT_DYN_LONG, EXPORT_DYN_SEG_OFF, EXPORT_SLICE_LONG,
+ EXPORT_SLICE_SEG_OFF, EXPORT_SLICE_SEG_BOUNDS, EXPORT_SLICE_SEG_ROW, EXPORT_SLICE_FIX,
+ EXPORT_SLICE_SEG_FIX) = range(28)
 
 
 class CSR(C.Structure):

@@ -641,7 +641,7 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
                                  int64_t bytes, spmv_stream_t stream)
 {
     clear_error();
-    if (!P || !dst) return fail(SPMV_ERR_INVALID_ARG, "spmv_prepared_export: NULL argument");
+    if (!P || (!dst && bytes != 0)) return fail(SPMV_ERR_INVALID_ARG, "spmv_prepared_export: NULL argument");
     const void* src = nullptr;
     int64_t size = 0;
     const int v = P->c.variant;
@@ -709,6 +709,42 @@ spmv_status spmv_prepared_export(const spmv_prepared_t* P, int32_t which, void* 
             break;
         case SPMV_EXPORT_SLICE_PANEL_STEP:
             if (v == SPMV_V7_SLICED && P->sl.coding == 2) { src = P->sl.step; size = P->sl.tot; }
+            break;
+        case SPMV_EXPORT_DYN_M1:
+            if (v == SPMV_V4_DYNAMIC) { src = P->dyn.m1; size = 4 * (int64_t)P->dyn.n_m1; }
+            break;
+        case SPMV_EXPORT_DYN_M2:
+            if (v == SPMV_V4_DYNAMIC) { src = P->dyn.m2; size = 4 * (int64_t)P->dyn.n_m2; }
+            break;
+        case SPMV_EXPORT_DYN_LONG:
+            if (v == SPMV_V4_DYNAMIC) { src = P->dyn.lrow; size = 4 * (int64_t)P->dyn.n_long; }
+            break;
+        case SPMV_EXPORT_DYN_SEG_OFF:
+            if (v == SPMV_V4_DYNAMIC && P->dyn.n_long > 0) {
+                src = P->dyn.seg_off;
+                size = 4 * ((int64_t)P->dyn.n_long + 1);
+            }
+            break;
+        case SPMV_EXPORT_SLICE_LONG:
+            if (v == SPMV_V7_SLICED) { src = P->sl.long_rows; size = 4 * (int64_t)P->sl.n_long; }
+            break;
+        case SPMV_EXPORT_SLICE_SEG_OFF:
+            if (v == SPMV_V7_SLICED && P->sl.n_long > 0) {
+                src = P->sl.seg_off;
+                size = 4 * ((int64_t)P->sl.n_long + 1);
+            }
+            break;
+        case SPMV_EXPORT_SLICE_SEG_BOUNDS:
+            if (v == SPMV_V7_SLICED) { src = P->sl.seg_be; size = 16 * (int64_t)P->sl.n_seg; }
+            break;
+        case SPMV_EXPORT_SLICE_SEG_ROW:
+            if (v == SPMV_V7_SLICED) { src = P->sl.seg_row; size = 4 * (int64_t)P->sl.n_seg; }
+            break;
+        case SPMV_EXPORT_SLICE_FIX:
+            if (v == SPMV_V7_SLICED) { src = P->sl.fix; size = 4 * (int64_t)P->sl.n_fix; }
+            break;
+        case SPMV_EXPORT_SLICE_SEG_FIX:
+            if (v == SPMV_V7_SLICED) { src = P->sl.seg_fix; size = 4 * (int64_t)P->sl.n_seg; }
             break;
         case SPMV_EXPORT_SLICE_DIAG:
             if (v == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 && P->sl.cbytes < 4 &&
