@@ -526,7 +526,12 @@ spmv_status spmv_prepare(const spmv_csr_t *A, const spmv_choice_t *c, int32_t tr
 
 /* y = A x (Algorithm 1, FP64 accumulation).  x: device [n_cols], y: device
  * [n_rows]; x and y must not overlap.  Asynchronous on `stream`; does not
- * allocate. */
+ * allocate.  A prepared object holds per-call device state (STREAM and
+ * MERGE carries, DYNAMIC's work counter and partial sums, SLICED's long-row
+ * partials and per-row tickets, FP32 copies of x), so calls on one object
+ * must not overlap on the GPU (same stream, or ordered by events); calls on
+ * different objects may run concurrently.  The tickets return to 0 at the
+ * end of every call that completes. */
 spmv_status spmv(const spmv_prepared_t *P, const double *x, double *y, spmv_stream_t stream);
 
 /* End-to-end form of spmv for host vectors: copies x_host [n_cols] to the
