@@ -418,8 +418,18 @@ spmv_status spmv_classify_profile(const spmv_profile_t *p, const spmv_thresholds
 /* Variant that tackles a class (see spmv_variant). */
 int32_t spmv_class_variant(int32_t cls);
 
+/* The whole choice for a class (Table 2 on GB300): the class's variant and
+ * the launch configuration calibrated for the class (source 1, cls set).
+ * All four classes take SLICED.  CML and CMP take its structural rules, MB
+ * rows in order with one slice per warp, and IMB a length sort in windows
+ * of 4096 with a row cap of 32.  The table was calibrated on the training
+ * matrices, among the second level's configurations and delta-coded
+ * layouts.  spmv_select and the fallback of spmv_select_model return this
+ * choice.  SPMV_ERR_INVALID_ARG for an unknown class. */
+spmv_status spmv_class_choice(int32_t cls, spmv_choice_t *out);
+
 /* Chooses a variant.  With a profile (p != NULL) and no model, the profile
- * rule decides.  Host-only; does not touch the GPU.  f may be NULL when p is
+ * rule decides (spmv_class_choice of the rule's class).  Host-only; does not touch the GPU.  f may be NULL when p is
  * given.  SPMV_ERR_INVALID_ARG when p holds a NaN or non-positive speedup. */
 spmv_status spmv_select(const spmv_features_t *f, const spmv_profile_t *p,
                         const spmv_thresholds_t *th, spmv_choice_t *out);
@@ -466,8 +476,8 @@ spmv_status spmv_model_logits(const spmv_model_t *m, const float *vec16, float *
  * output), margin = best - second logit; when m carries launch parameters
  * (spmv_model_set_launch) the choice takes the chosen output's.  When
  * margin < min_margin and a profile p is given, the profiling rule decides
- * instead (used_fallback = 1, source = 1, no launch parameters); otherwise
- * source = 2.  Host-only; th may be NULL. */
+ * instead (used_fallback = 1, source = 1, the class's choice from
+ * spmv_class_choice); otherwise source = 2.  Host-only; th may be NULL. */
 spmv_status spmv_select_model(const spmv_features_t *f, const spmv_model_t *m,
                               const spmv_profile_t *p, const spmv_thresholds_t *th,
                               spmv_choice_t *out);
@@ -477,7 +487,8 @@ spmv_status spmv_select_model(const spmv_features_t *f, const spmv_model_t *m,
  * chosen, sub's forward on the same features picks that variant's launch
  * parameters (threads_per_row, block_nnz, items_per_warp of the choice).
  * sub may be NULL (first level only).  A choice from a model with launch
- * parameters carries them; a profile fallback carries none.  Host-only. */
+ * parameters carries them; a profile fallback keeps its class's choice
+ * (spmv_class_choice) and is not refined.  Host-only. */
 spmv_status spmv_select_model_refined(const spmv_features_t *f, const spmv_model_t *m,
                                       const spmv_model_t *sub, const spmv_profile_t *p,
                                       const spmv_thresholds_t *th, spmv_choice_t *out);

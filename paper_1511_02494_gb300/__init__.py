@@ -169,6 +169,13 @@ def spmv_class_variant(cls: int) -> int:
     return int(lib().spmv_class_variant(cls))
 
 
+def spmv_class_choice(cls: int) -> Choice:
+    """The class's calibrated choice (variant and launch configuration)."""
+    out = Choice()
+    _check(lib().spmv_class_choice(int(cls), C.byref(out)))
+    return out
+
+
 def spmv_select(features: Features | None = None, profile: Profile | None = None,
                 thresholds: Thresholds | None = None) -> Choice:
     out = Choice()

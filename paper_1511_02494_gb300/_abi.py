@@ -101,6 +101,7 @@ def declare(lib):
         "spmv_default_thresholds": (Thresholds, []),
         "spmv_classify_profile": (I32, [C.POINTER(Profile), C.POINTER(Thresholds), C.POINTER(I32)]),
         "spmv_class_variant": (I32, [I32]),
+        "spmv_class_choice": (I32, [I32, C.POINTER(Choice)]),
         "spmv_select": (I32, [C.POINTER(Features), C.POINTER(Profile), C.POINTER(Thresholds),
                               C.POINTER(Choice)]),
         "spmv_prepare": (I32, [C.POINTER(CSR), C.POINTER(Choice), I32, C.POINTER(P), P]),

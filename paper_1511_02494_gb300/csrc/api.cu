@@ -479,16 +479,45 @@ int32_t spmv_class_variant(int32_t cls)
     switch (cls) {
         // calibrated on GB300: per class, the variant with the lowest
         // geometric-mean slowdown against the exhaustive best on the training
-        // matrices (CML 1.04, MB 1.00, IMB 1.13, CMP 1.05).  SLICED wins every
+        // matrices (CML 1.03, MB 1.00, IMB 1.01, CMP 1.03).  SLICED wins every
         // class because its prepare step adapts the layout to the row lengths
         // (length sort and row cap for imbalance, four slices per warp for
-        // short rows); DYNAMIC is next for IMB (1.28)
+        // short rows); DYNAMIC is next for IMB (1.52)
         case SPMV_CLASS_CML: return SPMV_V7_SLICED;
         case SPMV_CLASS_MB: return SPMV_V7_SLICED;
         case SPMV_CLASS_IMB: return SPMV_V7_SLICED;
         case SPMV_CLASS_CMP: return SPMV_V7_SLICED;
         default: return -1;
     }
+}
+
+spmv_status spmv_class_choice(int32_t cls, spmv_choice_t* out)
+{
+    clear_error();
+    if (!out) return fail(SPMV_ERR_INVALID_ARG, "spmv_class_choice: NULL output");
+    if (cls < 0 || cls > 3) return fail(SPMV_ERR_INVALID_ARG, "spmv_class_choice: unknown class");
+    // calibrated on GB300 like the variant table: per class, the SLICED form
+    // (among the second level's launch configurations and delta-coded
+    // layouts) with the lowest geometric-mean slowdown on the training
+    // matrices the rule puts in that class.  {slices per warp, sort window,
+    // row cap, index coding}; 0 = the prepare step's structural rule.
+    static const int32_t form[4][4] = {
+        {0, 0, 0, 0},      // CML: the structural rules (1.052)
+        {1, 1, 1024, 0},   // MB: rows in order, one slice per warp (1.022)
+        {1, 4096, 32, 0},  // IMB: length sort in windows of 4096, cap 32 (1.011)
+        {0, 0, 0, 0},      // CMP: the structural rules (1.053)
+    };
+    spmv_choice_t c = {};
+    c.cls = cls;
+    c.variant = spmv_class_variant(cls);
+    c.threads_per_row = form[cls][0];
+    c.block_nnz = form[cls][1];
+    c.items_per_warp = form[cls][2];
+    c.index_coding = form[cls][3];
+    c.value_type = SPMV_VAL_F64;
+    c.source = 1;
+    *out = c;
+    return SPMV_OK;
 }
 
 spmv_status spmv_select(const spmv_features_t* f, const spmv_profile_t* p,
@@ -503,13 +532,7 @@ spmv_status spmv_select(const spmv_features_t* f, const spmv_profile_t* p,
     int32_t cls = -1;
     spmv_status st = spmv_classify_profile(p, th, &cls);
     if (st != SPMV_OK) return st;
-    spmv_choice_t c = {};
-    c.cls = cls;
-    c.variant = spmv_class_variant(cls);
-    c.value_type = SPMV_VAL_F64;
-    c.source = 1;
-    *out = c;
-    return SPMV_OK;
+    return spmv_class_choice(cls, out);
 }
 
 spmv_status spmv_prepare(const spmv_csr_t* A, const spmv_choice_t* c, int32_t trusted,

@@ -469,11 +469,10 @@ spmv_status spmv_select_model(const spmv_features_t* f, const spmv_model_t* m,
         int32_t cls = -1;
         spmv_status st = spmv_classify_profile(p, th, &cls);
         if (st != SPMV_OK) return st;
-        c.cls = cls;
-        c.variant = spmv_class_variant(cls);
-        c.threads_per_row = c.block_nnz = c.items_per_warp = 0;
+        const float margin = c.margin;
+        if ((st = spmv_class_choice(cls, &c)) != SPMV_OK) return st;
+        c.margin = margin;
         c.used_fallback = 1;
-        c.source = 1;
     }
     *out = c;
     return SPMV_OK;
@@ -484,7 +483,7 @@ spmv_status spmv_select_model_refined(const spmv_features_t* f, const spmv_model
                                       const spmv_thresholds_t* th, spmv_choice_t* out)
 {
     spmv_status st = spmv_select_model(f, m, p, th, out);
-    if (st != SPMV_OK || !sub || sub->launch.empty()) return st;
+    if (st != SPMV_OK || !sub || sub->launch.empty() || out->used_fallback) return st;
     for (int o = 0; o < sub->k; ++o)
         if (sub->variants[o] != out->variant) return SPMV_OK;  // another variant: first level only
     spmv_choice_t c2;

@@ -450,6 +450,82 @@ def train_second_level(args, d, first):
     print(json.dumps(rep["test"], indent=1))
 
 
+# SLICED forms beyond the second level's launch configurations that the
+# class table may assign: (threads_per_row, block_nnz, items_per_warp,
+# index_coding) -- Table 2's delta coding in the two base layouts
+CLASS_EXTRA = (
+    (1, 1, 1024, 1),   # rows in order, delta-coded columns
+    (1, 4096, 32, 1),  # sorted, cap 32, delta-coded columns
+)
+
+
+def class_table(args, d):
+    """The profiling rule's class -> choice table (Table 2 on GB300): for each
+    class the rule names on the training split, the SLICED form -- one of the
+    second level's launch configurations or CLASS_EXTRA -- with the lowest
+    geometric-mean slowdown against the best form; written with its held-out
+    evaluation to class_table.json (CLASS_EXTRA timings in class_dataset.npz)."""
+    tcfg = sliced_dataset(d, os.path.join(args.out, "sliced_dataset.npz"))
+    path = os.path.join(args.out, "class_dataset.npz")
+    extra = None
+    if os.path.exists(path):
+        s = np.load(path)
+        if np.array_equal(s["seed"], d["seed"]) and s["times"].shape[1] == len(CLASS_EXTRA):
+            extra = s["times"]
+    if extra is None:
+        extra = np.empty((len(d["seed"]), len(CLASS_EXTRA)))
+        t0 = time.time()
+        for row, i in enumerate(d["seed"]):
+            family, n_rows = matrix_spec(int(i))
+            A = synth.family_matrix(family, n_rows, seed=int(i), device="cuda")
+            dA = sp.DeviceCSR(A.n_rows, A.n_cols, A.rowptr.contiguous(), A.colind.contiguous(),
+                              A.val.contiguous())
+            x = synth.uniform_vector(A.n_cols, int(i), device="cuda")
+            y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+            for j, (r, sigma, cap, code) in enumerate(CLASS_EXTRA):
+                ch = sp.make_choice("sliced", threads_per_row=r, block_nnz=sigma, items_per_warp=cap,
+                                    index_coding=code)
+                extra[row, j] = time_choice(dA, ch, x, y)
+            del dA, A, x, y
+            if (row + 1) % 500 == 0:
+                torch.cuda.empty_cache()
+                print(f"{row + 1}/{len(d['seed'])} matrices, {time.time() - t0:.0f} s", flush=True)
+        np.savez(path, seed=d["seed"], times=extra, forms=np.array(CLASS_EXTRA, np.int32))
+    forms = [tuple(c) + (0,) for c in SLICED_CONFIGS] + list(CLASS_EXTRA)
+    t_all = np.concatenate([tcfg, extra], 1)
+    th = sp.spmv_default_thresholds()
+    cls = np.array([_rule_class(p, th) for p in d["prof"]])
+    seeds = d["seed"]
+    tr, te = np.where(seeds % 5 != 0)[0], np.where(seeds % 5 == 0)[0]
+    best = t_all.min(1)
+    table, per_class = [], {}
+    for c in range(4):
+        m = tr[cls[tr] == c]
+        slow = [geomean(t_all[m, j] / best[m]) if len(m) else math.inf for j in range(len(forms))]
+        j = int(np.argmin(slow)) if len(m) else 0
+        table.append([sp.VARIANT_IDS["sliced"], *forms[j]])
+        per_class[sp.CLASSES[c]] = {"train_matrices": int(len(m)), "form": list(forms[j]),
+                                    "train_slowdown_each_form": slow}
+    pick = np.array([table[c][1:] for c in cls])
+    idx = [forms.index(tuple(p)) for p in pick]
+    t_rule = t_all[np.arange(len(seeds)), idx]
+    overall = np.minimum(d["times"].min(1), t_all.min(1))
+    rep = {"forms": [list(f) for f in forms], "table": table, "classes": per_class,
+           "test": {"matrices": int(len(te)),
+                    "rule_with_class_forms_vs_best_overall": geomean(t_rule[te] / overall[te]),
+                    "rule_with_sliced_rules_vs_best_overall": geomean(tcfg[te, 0] / overall[te]),
+                    "rule_with_class_forms_vs_best_variant": geomean(t_rule[te] / d["times"][te].min(1))}}
+    with open(os.path.join(args.out, "class_table.json"), "w") as f:
+        json.dump(rep, f, indent=1)
+    print(json.dumps(rep["test"], indent=1))
+
+
+def _rule_class(prof_row, th) -> int:
+    p = sp.Profile()
+    p.s_noxmiss, p.s_inflate, p.s_balance = (float(v) for v in prof_row)
+    return sp.spmv_classify_profile(p, th)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -461,6 +537,8 @@ def main():
                     help="variants whose kernels changed: time them again on every stored matrix")
     ap.add_argument("--second-level", action="store_true",
                     help="also time SLICED's launch configurations and train the second-level network")
+    ap.add_argument("--class-table", action="store_true",
+                    help="only build the profiling rule's class -> SLICED form table from the stored data")
     ap.add_argument("--retime-configs", action="store_true",
                     help="with --second-level: time every SLICED launch configuration again")
     args = ap.parse_args()
@@ -469,6 +547,8 @@ def main():
     build()
     ds_path = os.path.join(args.out, "selector_dataset.npz")
     d = build_dataset(args.n, ds_path, resume=not args.no_resume)
+    if args.class_table:
+        return class_table(args, d)
     if args.retime:
         times = d["times"].astype(np.float64)
         if times.shape[1] < N_VAR:

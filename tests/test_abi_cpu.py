@@ -118,6 +118,21 @@ def test_profile_rule_random_profiles_bit_exact(lib):
         assert sp.spmv_classify_profile(p) == oracle.profile_class(*row, tau=tau)
 
 
+def test_rule_selection_returns_the_class_choice(lib):
+    for c in range(4):
+        ch = sp.spmv_class_choice(c)
+        assert ch.variant == sp.spmv_class_variant(c) and ch.cls == c and ch.source == 1
+        assert ch.value_type == sp.VAL_F64 and ch.used_fallback == 0
+    # a profile whose rule names IMB (balance probe far above its threshold)
+    p = _abi.Profile()
+    p.s_noxmiss, p.s_inflate, p.s_balance = 1.0, 1.0, 50.0
+    got = sp.spmv_select(profile=p)
+    want = sp.spmv_class_choice(_abi.CLASSES.index("IMB"))
+    assert got.as_dict() == want.as_dict()
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_class_choice(4)
+
+
 def test_class_variant_table(lib):
     # the library's table is calibrated (its values are pinned against the
     # committed training data in test_selector_gain); here: one valid variant
