@@ -592,8 +592,13 @@ spmv_status spmv_batch_create(const spmv_csr_t *mats, int32_t count,
                               spmv_batch_t **out, spmv_stream_t stream);
 /* A batch of prepared matrices (borrowed; they must outlive the batch), each
  * run in the persistent form of its own variant inside the one launch: a
- * SLICED matrix with FP64 values as work items of 4 slices (its long rows
- * one item each); a MERGE or DYNAMIC matrix (imbalance class), or a SLICED
+ * SLICED matrix with FP64 values as work items of 4 slices, and its long
+ * rows as one item per segment of 2048 nonzeros (the segments of rows that
+ * span several queued first, then per matrix its slices and its rows of one
+ * segment; a row of several segments is summed by the warp
+ * that finishes its last one, with the prepared object's per-row tickets,
+ * so a batch run must not overlap spmv calls on the same prepared
+ * objects); a MERGE or DYNAMIC matrix (imbalance class), or a SLICED
  * one with FP32/BF16 values (the batch sums FP64), as the sliced form with
  * the automatic layout, which the batch prepares and owns (CSR rows would
  * make a warp run as many DFMAs as its longest row); any other variant as

@@ -40,11 +40,21 @@ struct BatchMat {
     const double* sval;
     const int* long_rows;
     int32_t scb;       // bytes per stored column (4, 2 or 1)
+    // long rows' segment table of the sliced form (see SlicedPlan)
+    const int64_t* seg_be;
+    const int* seg_row;
+    const int* seg_fix;
+    const int* fix;
+    const int* seg_off;
+    unsigned* ticket;
+    double* partial;
 };
 
 // lg 0..5: rows [r0, r1) with 2^lg lanes per row; kSliceItem: slices
-// [r0, r1) of a sliced matrix; kLongItem: entries [r0, r1) of its long-row list
-constexpr int32_t kSliceItem = 8, kLongItem = 9;
+// [r0, r1) of a sliced matrix; kSegItem: segment r0 of its long rows
+// (at most 2048 nonzeros; a row of several segments is summed by the warp
+// that finishes its last one, as in the single-matrix kernel)
+constexpr int32_t kSliceItem = 8, kSegItem = 10;
 struct BatchItem {
     int32_t m, r0, r1, lg;
 };
@@ -112,14 +122,31 @@ k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, 
                                            static_cast<const int*>(M.scol), M.sval, M.x, M.y);
                 }
                 break;
-            case kLongItem:
-                for (int q = I.r0; q < I.r1; ++q) {
-                    const int r = M.long_rows[q];
-                    const double s = group_sum(
-                        row_partial<32, 8>(M.rp[r], M.rp[r + 1], lane, ColPlain<int>{M.ci}, M.v, M.x), 32);
-                    if (lane == 0) M.y[r] = s;
+            case kSegItem: {
+                const int j = I.r0;
+                const int64_t b = M.seg_be[2 * (int64_t)j], e = M.seg_be[2 * (int64_t)j + 1];
+                const double sum = group_sum(row_partial<32, 8>(b, e, lane, ColPlain<int>{M.ci}, M.v, M.x), 32);
+                if (lane == 0) {
+                    const int r1 = M.seg_row[j];
+                    if (r1 >= 0) {
+                        M.y[r1] = sum;
+                    } else {
+                        M.partial[j] = sum;
+                        __threadfence();
+                        const int t = M.seg_fix[j];
+                        const int q = M.fix[t];
+                        const int sb = M.seg_off[q], se = M.seg_off[q + 1];
+                        if (atomicAdd(M.ticket + t, 1u) == (unsigned)(se - sb - 1)) {
+                            __threadfence();
+                            double s = 0.0;
+                            for (int i = sb; i < se; ++i) s += __ldcg(M.partial + i);
+                            M.y[M.long_rows[q]] = s;
+                            M.ticket[t] = 0u;
+                        }
+                    }
                 }
                 break;
+            }
             case 0: batch_rows<1>(M, I.r0, I.r1, lane); break;
             case 1: batch_rows<2>(M, I.r0, I.r1, lane); break;
             case 2: batch_rows<4>(M, I.r0, I.r1, lane); break;
@@ -148,14 +175,22 @@ std::vector<BatchItem> make_items(const spmv_batch* B, const std::vector<int32_t
                                   const std::vector<int32_t>& rpi)
 {
     std::vector<BatchItem> items;
+    // the segments of rows that span several (the longest work, a row of
+    // up to 2^31 nonzeros) of every sliced matrix first; then per matrix its
+    // slices or row chunks, and the rows of a single segment
+    for (size_t m = 0; m < B->mats.size(); ++m)
+        if (const spmv_prepared* P = B->preps[m])
+            for (int j = 0; j < P->sl.n_seg; ++j)
+                if (P->sl.seg_several[j]) items.push_back({(int32_t)m, j, j + 1, kSegItem});
     for (size_t m = 0; m < B->mats.size(); ++m) {
         const spmv_prepared* P = B->preps[m];
         if (P) {
-            // rows per item / 32 slices per item, then one item per long row
+            // rows per item / 32 slices per item
             const int ns = (int)P->sl.n_slices;
             const int k = std::max(1, rpi[m] / 32);
             for (int s0 = 0; s0 < ns; s0 += k) items.push_back({(int32_t)m, s0, std::min(ns, s0 + k), kSliceItem});
-            for (int q = 0; q < P->sl.n_long; ++q) items.push_back({(int32_t)m, q, q + 1, kLongItem});
+            for (int j = 0; j < P->sl.n_seg; ++j)
+                if (!P->sl.seg_several[j]) items.push_back({(int32_t)m, j, j + 1, kSegItem});
             continue;
         }
         const int n = (int)B->mats[m].n_rows;
@@ -344,7 +379,8 @@ spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* con
     for (size_t m = 0; m < B->mats.size(); ++m) {
         const spmv_csr_t& A = B->mats[m];
         h[m] = {A.rowptr, A.colind, A.val, x[m], y[m], A.n_rows,
-                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 4};
+                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 4,
+                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         if (const spmv_prepared* P = B->preps[m]) {
             const SlicedPlan& d = P->sl;
             h[m].rowlen = d.rowlen;
@@ -355,6 +391,13 @@ spmv_status spmv_batch_bind(spmv_batch_t* B, const double* const* x, double* con
             h[m].scb = d.cbytes;
             h[m].sval = d.val;
             h[m].long_rows = d.long_rows;
+            h[m].seg_be = d.seg_be;
+            h[m].seg_row = d.seg_row;
+            h[m].seg_fix = d.seg_fix;
+            h[m].fix = d.fix;
+            h[m].seg_off = d.seg_off;
+            h[m].ticket = d.ticket;
+            h[m].partial = d.partial;
         }
         B->xs[m] = x[m];
         B->ys[m] = y[m];

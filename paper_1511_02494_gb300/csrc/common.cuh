@@ -84,6 +84,7 @@ struct SlicedPlan {
     int* fix = nullptr;          // [n_fix] long rows (list indices) with several segments
     int* seg_fix = nullptr;      // [n_seg] index in fix of the segment's row, -1 for a single segment
     unsigned* ticket = nullptr;  // [n_fix] segments of the row finished in this call (0 between calls)
+    std::vector<uint8_t> seg_several;  // host, [n_seg]: 1 when the segment's row has several
     int n_fix = 0;
     int n_seg = 0;
     // low-precision values (FP32 / BF16), optionally 16-bit column offsets

@@ -751,8 +751,12 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
         d.n_fix = (int)fix.size();
         // per segment the index of its row in the fix list (-1: the row's only segment)
         std::vector<int> seg_fix((size_t)d.n_seg, -1);
+        d.seg_several.assign((size_t)d.n_seg, 0);
         for (int t = 0; t < d.n_fix; ++t)
-            for (int j = off[fix[t]]; j < off[fix[t] + 1]; ++j) seg_fix[j] = t;
+            for (int j = off[fix[t]]; j < off[fix[t] + 1]; ++j) {
+                seg_fix[j] = t;
+                d.seg_several[j] = 1;
+            }
         if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)d.n_seg)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_be), 16 * (int64_t)d.n_seg)) != SPMV_OK ||
             (st = prepared_alloc(P, reinterpret_cast<void**>(&d.seg_row), 4 * (int64_t)d.n_seg)) != SPMV_OK ||

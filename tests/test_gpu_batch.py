@@ -132,3 +132,39 @@ def test_batch_of_prepared_matrices(batch_case):
         torch.cuda.synchronize()
         _check(mats, xs, ys)
         B.free()
+
+
+@pytest.mark.parametrize("form", ["prepared", "sliced"])
+def test_batch_with_rows_of_many_segments(form):
+    # a row of 120,000 nonzeros (59 segments) and other long rows beside
+    # small matrices: one work item per segment, each row of several
+    # segments summed by the warp that finishes its last one; integer values
+    # give exact sums, and repeated runs (tickets back at 0) the same bits,
+    # equal to the single-matrix SLICED kernel's
+    g = np.random.default_rng(4)
+    Z = synth.zipf_rows(30_000, 200_000, 1.3, 120_000, seed=5)
+    Z.val = torch.from_numpy(g.integers(-3, 4, Z.nnz).astype(np.float64))
+    mats = [Z, synth.laplacian_2d_5pt(40, 40), synth.zipf_rows(5000, 5000, 1.5, 4000, seed=6)]
+    dev = [sp.DeviceCSR.from_host(A) for A in mats]
+    preps = [sp.spmv_prepare(dev[0], sp.make_choice("sliced", block_nnz=4096, items_per_warp=32)),
+             sp.spmv_prepare(dev[1], sp.make_choice("subwarp")),
+             sp.spmv_prepare(dev[2], sp.make_choice("sliced"))]
+    assert preps[0].info().n_long_rows > 0
+    xs = [torch.from_numpy(g.integers(-2, 3, mats[0].n_cols).astype(np.float64)).cuda()] + \
+        [synth.uniform_vector(A.n_cols, 3 + i).cuda() for i, A in enumerate(mats[1:])]
+    ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats]
+    B = sp.spmv_batch_create_prepared(preps) if form == "prepared" else sp.spmv_batch_create_sliced(preps)
+    sp.spmv_batch_bind(B, xs, ys)
+    y_single = torch.empty_like(ys[0])
+    sp.spmv(preps[0], xs[0], y_single)
+    for use_graph in (False, False, True, True):
+        for y in ys:
+            y.fill_(float("nan"))
+        sp.spmv_batch_run(B, use_graph=use_graph)
+        torch.cuda.synchronize()
+        assert np.array_equal(ys[0].cpu().numpy(), oracle.spmv(mats[0], xs[0].cpu()))
+        assert torch.equal(ys[0], y_single)
+        _check(mats, xs, ys)
+    B.free()
+    for P in preps:
+        P.free()
