@@ -368,6 +368,14 @@ def run_ours(args):
         P = sp.spmv_prepare(dA, ch)
         rec["prepare_ms"] = (time.perf_counter() - t0) * 1e3
         rec["selected_min_bytes"] = P.info().min_bytes
+        # the profiling rule's own choice (its class's variant and launch
+        # configuration), timed alone like the variants below
+        Pr = sp.spmv_prepare(dA, ch_rule)
+        ir = Pr.info()
+        rec["rule_launch"] = {"threads_per_row": ir.threads_per_row, "block_nnz": ir.block_nnz,
+                              "items_per_warp": ir.items_per_warp}
+        rec["rule_ms"] = time_spmv(Pr, x, y, reps=10)
+        Pr.free()
         inf = P.info()
         rec["launch"] = {"threads_per_row": inf.threads_per_row, "block_nnz": inf.block_nnz,
                          "items_per_warp": inf.items_per_warp}
@@ -513,7 +521,8 @@ def run_ours(args):
     for r, km, s in zip(per, kern_ms, speedups):
         matrices.append({
             "matrix": r["matrix"], "class": r["class"], "variant": r["variant"], "launch": r["launch"],
-            "variant_rule": r["variant_rule"],
+            "variant_rule": r["variant_rule"], "rule_launch": r["rule_launch"],
+            "rule_ms": round(r["rule_ms"], 5),
             "best_variant": r["best_variant"], "ms": round(km, 5),
             "gbs": round(r["min_bytes"] / (km * 1e-3) / 1e9, 1),
             "gflops": round(2 * r["nnz"] / (km * 1e-3) / 1e9, 1),
@@ -546,6 +555,8 @@ def run_ours(args):
         "plain_csr_gbs": round(step_bytes / (plain_total * 1e-3) / 1e9, 2),
         "speedup_vs_plain_csr": round(plain_total / sel_total, 3),
         "speedup_geomean": round(math.exp(sum(map(math.log, speedups)) / len(speedups)), 3),
+        "speedup_geomean_profile_rule": round(math.exp(sum(math.log(r["plain_ms"] / r["rule_ms"]) for r in per)
+                                                       / len(per)), 3),
         "selector_cost_spmvs": {
             "features_and_model": round(sum(r["features_ms"] / r["plain_ms"] for r in per) / len(per), 2),
             "profile_and_rule": round(sum(r["profile_select_ms"] / r["plain_ms"] for r in per) / len(per), 1),
