@@ -141,11 +141,9 @@ int32_t launches_of(const spmv_prepared_t* P)
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
         case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
         case SPMV_V7_SLICED:
-            // FP64 values: slices and long rows in one launch.  FP32/BF16:
-            // + x to FP32, + long-row segments, + fix-up of rows with several
-            if (P->sl.value_type == SPMV_VAL_F64) return 1;
-            return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0) + (P->sl.n_long > 0 ? 1 : 0) +
-                   (P->sl.n_fix > 0 ? 1 : 0);
+            // slices and long rows in one launch; with FP32 accumulation the
+            // conversion of x to FP32 before it
+            return 1 + (P->sl.acc32 && P->A.n_cols > 0 ? 1 : 0);
         case SPMV_V6_COMPRESSED: return P->c.accumulate == 2 && P->A.n_cols > 0 ? 2 : 1;  // + x to FP32
         default: return 1;
     }

@@ -313,19 +313,34 @@ __device__ __forceinline__ longlong2 segment_bounds(const int64_t* seg_be, int w
 
 // A segment's warp writes its sum to y when it is its row's only segment,
 // else to partial; the partials of a row with several segments are summed
-// in segment order (k_sliced_fixup for FP32/BF16 values, the ticket in
-// k_sliced_long for FP64).
-// fix[t]: index in the long-row list of the t-th row with several segments
-__global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int* __restrict__ list,
-                               const int* __restrict__ seg_off, const double* __restrict__ partial,
-                               double* __restrict__ y)
+// in segment order by the warp finishing the row's last one (finish_segment).
+// Lane 0 of segment w's warp, with the segment's sum: y of the row when it
+// is the row's only segment; else the partial, and when the atomic ticket
+// shows this was the row's last segment to finish, the row's sum of
+// partials in segment order, after which the ticket is reset for the next
+// call.  Nothing waits.
+__device__ __forceinline__ void finish_segment(int w, double sum, const int* __restrict__ seg_row,
+                                               const int* __restrict__ seg_fix, const int* __restrict__ fix,
+                                               const int* __restrict__ list, const int* __restrict__ seg_off,
+                                               unsigned* __restrict__ ticket, double* __restrict__ partial,
+                                               double* __restrict__ y)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_fix) return;
+    const int r1 = seg_row[w];
+    if (r1 >= 0) {
+        y[r1] = sum;
+        return;
+    }
+    partial[w] = sum;
+    __threadfence();
+    const int t = seg_fix[w];
     const int q = fix[t];
-    double sum = 0.0;
-    for (int i = seg_off[q]; i < seg_off[q + 1]; ++i) sum += partial[i];
-    y[list[q]] = sum;
+    const int b = seg_off[q], e = seg_off[q + 1];
+    if (atomicAdd(ticket + t, 1u) != (unsigned)(e - b - 1)) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = b; i < e; ++i) s += __ldcg(partial + i);
+    y[list[q]] = s;
+    ticket[t] = 0u;
 }
 
 // Slices and long-row segments in one launch (FP64 values, rows above the
@@ -336,8 +351,8 @@ __global__ void k_sliced_fixup(int n_fix, const int* __restrict__ fix, const int
 // instead of running as a separate launch after them.  A row with several
 // segments has no fix-up launch either: each of its segments stores its
 // partial, and the warp that finishes the row's last one (an atomic ticket
-// per row) sums the partials in segment order, as k_sliced_fixup does, and
-// resets the ticket for the next call.  Nothing waits on another warp.
+// per row) sums the partials in segment order (finish_segment) and resets
+// the ticket for the next call.  Nothing waits on another warp.
 template <int U, int R, int B, typename CT, int MODE = 0, typename DT = uint8_t>
 __global__ void __launch_bounds__(kSB, B)
 k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
@@ -358,23 +373,7 @@ k_sliced_long(int n_seg, unsigned seg_blocks, int64_t n_slices,
         if (w >= n_seg) return;  // whole warps only
         const longlong2 be = segment_bounds(seg_be, w);
         const double sum = group_sum(row_partial<32, 4>(be.x, be.y, lane, ColPlain<int>{ci}, v, x), 32);
-        if (lane != 0) return;
-        const int r1 = seg_row[w];
-        if (r1 >= 0) {
-            y[r1] = sum;
-            return;
-        }
-        partial[w] = sum;
-        __threadfence();
-        const int t = seg_fix[w];
-        const int q = fix[t];
-        const int b = seg_off[q], e = seg_off[q + 1];
-        if (atomicAdd(ticket + t, 1u) != (unsigned)(e - b - 1)) return;
-        __threadfence();
-        double s = 0.0;
-        for (int i = b; i < e; ++i) s += __ldcg(partial + i);
-        y[list[q]] = s;
-        ticket[t] = 0u;
+        if (lane == 0) finish_segment(w, sum, seg_row, seg_fix, fix, list, seg_off, ticket, partial, y);
         return;
     }
     const int64_t s0 = ((int64_t)(blockIdx.x - seg_blocks) * kSB + threadIdx.x) >> 5;
@@ -466,39 +465,50 @@ k_sliced_lp(int64_t n_slices, const int* __restrict__ rowlen, const int* __restr
     if (row >= 0) y[row] = v;
 }
 
-// long-row segments with the values rounded as the slices' (same arithmetic
-// per element; the segment's lanes are combined by a shuffle tree)
-template <typename VT, bool ACC32>
-__global__ void __launch_bounds__(kSB)
-k_sliced_segments_lp(int n_seg, const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
-                     const int* __restrict__ ci, const double* __restrict__ v,
-                     const double* __restrict__ x, const float* __restrict__ x32,
-                     double* __restrict__ partial, double* __restrict__ y)
+// FP32/BF16 values with rows above the cap: slices and long-row segments in
+// one launch, as k_sliced_long.  A segment is computed from the CSR arrays
+// with each value rounded as the slices' (the same arithmetic per element);
+// its lanes are combined by a shuffle tree, in FP32 (ACC32) or FP64.
+template <typename VT, bool OFF16, bool ACC32>
+__global__ void __launch_bounds__(kSB, 8)
+k_sliced_long_lp(int n_seg, unsigned seg_blocks, int64_t n_slices,
+                 const int64_t* __restrict__ seg_be, const int* __restrict__ seg_row,
+                 const int* __restrict__ seg_fix, const int* __restrict__ fix,
+                 const int* __restrict__ list, const int* __restrict__ seg_off,
+                 unsigned* __restrict__ ticket, double* __restrict__ partial,
+                 const int* __restrict__ ci, const double* __restrict__ v,
+                 const int* __restrict__ rowlen, const int* __restrict__ slice_len,
+                 const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
+                 const int* __restrict__ col, const uint16_t* __restrict__ off,
+                 const int* __restrict__ rowbase, const VT* __restrict__ val,
+                 const double* __restrict__ x, const float* __restrict__ x32, double* __restrict__ y)
 {
-    const int w = (int)(((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5);
-    if (w >= n_seg) return;
     const int lane = threadIdx.x & 31;
-    const longlong2 be = segment_bounds(seg_be, w);
-    const int64_t b = be.x, e = be.y;
-    if (ACC32) {
-        float acc = 0.f;
-        for (int64_t j = b + lane; j < e; j += 32)
-            acc = fmaf(widen32(round_to(__ldcs(v + j), (VT*)nullptr)), __ldg(x32 + __ldcs(ci + j)), acc);
-        acc = group_sum32(acc, 32);
-        if (lane == 0) {
-            const int r1 = seg_row[w];
-            if (r1 >= 0) y[r1] = (double)acc; else partial[w] = (double)acc;
+    if (blockIdx.x < seg_blocks) {
+        const int w = (int)(blockIdx.x * (kSB / 32) + (threadIdx.x >> 5));
+        if (w >= n_seg) return;  // whole warps only
+        const longlong2 be = segment_bounds(seg_be, w);
+        double sum;
+        if (ACC32) {
+            float acc = 0.f;
+            for (int64_t j = be.x + lane; j < be.y; j += 32)
+                acc = fmaf(widen32(round_to(__ldcs(v + j), (VT*)nullptr)), __ldg(x32 + __ldcs(ci + j)), acc);
+            sum = (double)group_sum32(acc, 32);
+        } else {
+            double acc = 0.0;
+            for (int64_t j = be.x + lane; j < be.y; j += 32)
+                acc = fma(widen_f32(widen32(round_to(__ldcs(v + j), (VT*)nullptr))), ldx(x + __ldcs(ci + j)), acc);
+            sum = group_sum(acc, 32);
         }
-    } else {
-        double acc = 0.0;
-        for (int64_t j = b + lane; j < e; j += 32)
-            acc = fma(widen_f32(widen32(round_to(__ldcs(v + j), (VT*)nullptr))), ldx(x + __ldcs(ci + j)), acc);
-        acc = group_sum(acc, 32);
-        if (lane == 0) {
-            const int r1 = seg_row[w];
-            if (r1 >= 0) y[r1] = acc; else partial[w] = acc;
-        }
+        if (lane == 0) finish_segment(w, sum, seg_row, seg_fix, fix, list, seg_off, ticket, partial, y);
+        return;
     }
+    const int64_t s = ((int64_t)(blockIdx.x - seg_blocks) * kSB + threadIdx.x) >> 5;
+    if (s >= n_slices) return;
+    int row;
+    const double r = slice_value_lp<OFF16 ? 2 : 1, VT, OFF16, ACC32>(s, lane, rowlen, slice_len, slice_ptr,
+                                                                    perm, col, off, rowbase, val, x, x32, &row);
+    if (row >= 0) y[row] = r;
 }
 
 unsigned grid_of(int64_t threads, int64_t cap_blocks)
@@ -850,6 +860,21 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
         else { SPMV_SL_CT(int) }
 #undef SPMV_SL_CT
 #undef SPMV_SL_M
+    } else if (d.n_long > 0) {
+        // FP32/BF16 values with long rows: slices and segments in one launch
+        const unsigned seg_blocks = (unsigned)((d.n_seg + kSB / 32 - 1) / (kSB / 32));
+        const unsigned blocks = seg_blocks + (unsigned)((d.n_slices + kSB / 32 - 1) / (kSB / 32));
+#define SPMV_SL_LONG_LP(VT, O16, A32)                                                                 \
+    k_sliced_long_lp<VT, O16, A32><<<blocks, kSB, 0, s>>>(                                          \
+        d.n_seg, seg_blocks, d.n_slices, d.seg_be, d.seg_row, d.seg_fix, d.fix, d.long_rows,         \
+        d.seg_off, d.ticket, d.partial, A.colind, A.val, d.rowlen, d.slice_len, d.slice_ptr, perm,    \
+        d.col, d.off, d.rowbase, static_cast<const VT*>(d.lowval), x, d.x32, y)
+#define SPMV_SL_LONG_LP_VT(VT)                                                                         \
+    if (d.off16) { if (d.acc32) SPMV_SL_LONG_LP(VT, true, true); else SPMV_SL_LONG_LP(VT, true, false); } \
+    else { if (d.acc32) SPMV_SL_LONG_LP(VT, false, true); else SPMV_SL_LONG_LP(VT, false, false); }
+        if (d.value_type == SPMV_VAL_F32) { SPMV_SL_LONG_LP_VT(float) } else { SPMV_SL_LONG_LP_VT(__nv_bfloat16) }
+#undef SPMV_SL_LONG_LP_VT
+#undef SPMV_SL_LONG_LP
     } else {
 #define SPMV_SL_LP(VT, O16, A32)                                                                   \
     k_sliced_lp<4, VT, O16, A32><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len,          \
@@ -862,23 +887,6 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
 #undef SPMV_SL_LP_VT
 #undef SPMV_SL_LP
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess || d.n_long == 0) return e;
-    // FP32/BF16 values (FP64 values with long rows took k_sliced_long above)
-    const unsigned sgrid = grid_of(32 * (int64_t)d.n_seg, INT32_MAX);
-#define SPMV_SL_SEG(VT, A32)                                                                        \
-    k_sliced_segments_lp<VT, A32><<<sgrid, kSB, 0, s>>>(d.n_seg, d.seg_be, d.seg_row, A.colind, A.val, x, \
-                                                        d.x32, d.partial, y)
-    if (d.value_type == SPMV_VAL_F32) {
-        if (d.acc32) SPMV_SL_SEG(float, true); else SPMV_SL_SEG(float, false);
-    } else {
-        if (d.acc32) SPMV_SL_SEG(__nv_bfloat16, true); else SPMV_SL_SEG(__nv_bfloat16, false);
-    }
-#undef SPMV_SL_SEG
-    e = cudaGetLastError();
-    if (e != cudaSuccess || d.n_fix == 0) return e;
-    k_sliced_fixup<<<(unsigned)((d.n_fix + 255) / 256), 256, 0, s>>>(d.n_fix, d.fix, d.long_rows, d.seg_off,
-                                                                     d.partial, y);
     return cudaGetLastError();
 }
 
