@@ -376,6 +376,7 @@ def run_ours(args):
                               "items_per_warp": ir.items_per_warp}
         rec["rule_ms"] = time_spmv(Pr, x, y, reps=10)
         Pr.free()
+        rec["selected_alone_ms"] = time_spmv(P, x, y, reps=10)
         inf = P.info()
         rec["launch"] = {"threads_per_row": inf.threads_per_row, "block_nnz": inf.block_nnz,
                          "items_per_warp": inf.items_per_warp}
@@ -522,7 +523,7 @@ def run_ours(args):
         matrices.append({
             "matrix": r["matrix"], "class": r["class"], "variant": r["variant"], "launch": r["launch"],
             "variant_rule": r["variant_rule"], "rule_launch": r["rule_launch"],
-            "rule_ms": round(r["rule_ms"], 5),
+            "rule_ms": round(r["rule_ms"], 5), "selected_alone_ms": round(r["selected_alone_ms"], 5),
             "best_variant": r["best_variant"], "ms": round(km, 5),
             "gbs": round(r["min_bytes"] / (km * 1e-3) / 1e9, 1),
             "gflops": round(2 * r["nnz"] / (km * 1e-3) / 1e9, 1),
@@ -555,8 +556,12 @@ def run_ours(args):
         "plain_csr_gbs": round(step_bytes / (plain_total * 1e-3) / 1e9, 2),
         "speedup_vs_plain_csr": round(plain_total / sel_total, 3),
         "speedup_geomean": round(math.exp(sum(map(math.log, speedups)) / len(speedups)), 3),
-        "speedup_geomean_profile_rule": round(math.exp(sum(math.log(r["plain_ms"] / r["rule_ms"]) for r in per)
-                                                       / len(per)), 3),
+        "speedup_geomean_alone": {
+            "learned_selector": round(math.exp(sum(math.log(r["plain_ms"] / r["selected_alone_ms"]) for r in per)
+                                               / len(per)), 3),
+            "profile_rule": round(math.exp(sum(math.log(r["plain_ms"] / r["rule_ms"]) for r in per)
+                                           / len(per)), 3),
+            "note": "each matrix's choice timed alone, as plain CSR is"},
         "selector_cost_spmvs": {
             "features_and_model": round(sum(r["features_ms"] / r["plain_ms"] for r in per) / len(per), 2),
             "profile_and_rule": round(sum(r["profile_select_ms"] / r["plain_ms"] for r in per) / len(per), 1),

@@ -139,7 +139,7 @@ int32_t launches_of(const spmv_prepared_t* P)
     switch (P->c.variant) {
         case SPMV_V2_STREAM: return P->bulk ? 2 : 1;               // windows + carry fix-up
         case SPMV_V3_MERGE: return 2;                              // tiles + carry fix-up
-        case SPMV_V4_DYNAMIC: return P->dyn.n_long > 0 ? 2 : 1;    // + long-row fix-up
+        case SPMV_V4_DYNAMIC: return 1;                            // long rows summed by their last warp
         case SPMV_V7_SLICED:
             // slices and long rows in one launch; with FP32 accumulation the
             // conversion of x to FP32 before it

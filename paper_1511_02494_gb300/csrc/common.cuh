@@ -54,6 +54,7 @@ struct DynPlan {
     int* lrow = nullptr;     // rows longer than seg
     int* seg_off = nullptr;  // first segment of each long row, [n_long + 1]
     double* partial = nullptr;  // one partial sum per segment
+    unsigned* ticket = nullptr; // [n_long] segments of the row finished in this call (0 between calls)
 };
 
 // SLICED (V7): rows longer than the plan's cap (kSlicedCap unless chosen)

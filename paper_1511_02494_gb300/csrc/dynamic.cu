@@ -4,8 +4,9 @@
 //   M1 lim_s < len <= 64       compact list, 8 lanes per row
 //   M2 64 < len <= seg         compact list, a warp per row
 //   L  len > seg               split into segments of `seg` nonzeros, a warp
-//                              per segment, partial sums fixed up per row in
-//                              segment order (deterministic)
+//                              per segment; the warp that finishes a row's
+//                              last segment (an atomic ticket per row) sums
+//                              its partials in segment order (deterministic)
 // Persistent warps take items from one atomic counter, longest work first
 // (L segments, M2, M1, then S chunks); the last warp to finish resets the
 // counter.  Every tier spends one DFMA per nonzero plus log2(lanes) shuffle
@@ -92,6 +93,7 @@ struct DynArgs {
     int n_m1, n_m2, n_long, n_seg, seg, lim_s, chunk_rows;
     double* partial;
     unsigned* counter;
+    unsigned* ticket;
 };
 
 template <int TS>
@@ -120,7 +122,20 @@ __global__ void __launch_bounds__(kDB) k_dyn(DynArgs a)
             const int64_t b = (int64_t)a.rp[r] + (int64_t)((int)it - a.seg_off[lo]) * a.seg;
             const int64_t e = min((int64_t)a.rp[r + 1], b + a.seg);
             const double s = group_sum(row_partial<32, 8>(b, e, lane, col, a.v, a.x), 32);
-            if (lane == 0) a.partial[it] = s;
+            if (lane == 0) {
+                // the row's last segment to finish sums its partials in
+                // segment order and resets the row's ticket (nothing waits)
+                a.partial[it] = s;
+                __threadfence();
+                const int sb = a.seg_off[lo], se = a.seg_off[lo + 1];
+                if (atomicAdd(a.ticket + lo, 1u) == (unsigned)(se - sb - 1)) {
+                    __threadfence();
+                    double t = 0.0;
+                    for (int i = sb; i < se; ++i) t += __ldcg(a.partial + i);
+                    a.y[r] = t;
+                    a.ticket[lo] = 0u;
+                }
+            }
         } else if ((int64_t)it < i_m1) {
             const int r = a.m2[it - i_m2];
             const double s = group_sum(row_partial<32, 4>(a.rp[r], a.rp[r + 1], lane, col, a.v, a.x), 32);
@@ -158,17 +173,6 @@ __global__ void __launch_bounds__(kDB) k_dyn(DynArgs a)
             a.counter[1] = 0u;
         }
     }
-}
-
-// y of each long row = its segment partials summed in segment order
-__global__ void k_dyn_fixup(int n_long, const int* __restrict__ lrow, const int* __restrict__ seg_off,
-                            const double* __restrict__ partial, double* __restrict__ y)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_long) return;
-    double s = 0.0;
-    for (int i = seg_off[p]; i < seg_off[p + 1]; ++i) s += partial[i];
-    y[lrow[p]] = s;
 }
 
 template <int TS>
@@ -251,8 +255,10 @@ spmv_status dyn_prepare(spmv_prepared* P, cudaStream_t s)
         SPMV_CUDA_TRY(cudaMemcpyAsync(&ns, d.seg_off + d.n_long, 4, cudaMemcpyDeviceToHost, s));
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));
         d.n_seg = ns;
-        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)ns)) != SPMV_OK)
+        if ((st = prepared_alloc(P, reinterpret_cast<void**>(&d.partial), 8 * (int64_t)ns)) != SPMV_OK ||
+            (st = prepared_alloc(P, reinterpret_cast<void**>(&d.ticket), 4 * (int64_t)d.n_long)) != SPMV_OK)
             return st;
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.ticket, 0, 4 * (size_t)d.n_long, s));
     }
     P->n_blocks = d.n_seg + d.n_m2 + (d.n_m1 + 3) / 4 + (A.n_rows + d.chunk_rows - 1) / d.chunk_rows;
     return SPMV_OK;
@@ -264,7 +270,8 @@ cudaError_t launch_dyn(const spmv_prepared* P, const double* x, double* y, cudaS
     if (A.n_rows == 0) return cudaSuccess;
     const DynPlan& d = P->dyn;
     DynArgs a{A.n_rows, A.rowptr, A.colind, A.val, x, y, d.m1, d.m2, d.lrow, d.seg_off,
-              d.n_m1, d.n_m2, d.n_long, d.n_seg, d.seg, d.lim_s, d.chunk_rows, d.partial, P->counter};
+              d.n_m1, d.n_m2, d.n_long, d.n_seg, d.seg, d.lim_s, d.chunk_rows, d.partial, P->counter,
+              d.ticket};
     cudaError_t e;
     switch (P->c.threads_per_row) {
         case 1: e = launch_dyn_t<1>(a, P->sm_count, s); break;
@@ -275,10 +282,7 @@ cudaError_t launch_dyn(const spmv_prepared* P, const double* x, double* y, cudaS
         case 32: e = launch_dyn_t<32>(a, P->sm_count, s); break;
         default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess || d.n_long == 0) return e;
-    k_dyn_fixup<<<(unsigned)((d.n_long + 255) / 256), 256, 0, s>>>(d.n_long, d.lrow, d.seg_off,
-                                                                   d.partial, y);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace spmvlib

@@ -617,7 +617,7 @@ def test_gather_probe_sum_and_launch_counts():
     Z = synth.zipf_rows(20_000, 20_000, 1.5, 10_000, seed=1)
     dZ = sp.DeviceCSR.from_host(Z)
     P = sp.spmv_prepare(dZ, sp.make_choice("dynamic", block_nnz=256))
-    assert P.info().launches == 2
+    assert P.info().launches == 1  # long rows summed by the warp finishing their last segment
 
 
 # ----------------------------------------------------------------- profile + select
