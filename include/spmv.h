@@ -207,13 +207,15 @@ typedef struct {
     int32_t accumulate;  /* COMPRESSED: 0 by value type (FP64 values -> FP64,
                             FP32/BF16 values -> FP32), 1 FP64, 2 FP32 */
     int32_t index_bytes; /* SLICED with FP64 values: narrowest stored column
-                            allowed -- 0 or 4: 32-bit columns; 2 or 1: the
+                            allowed -- 4: 32-bit columns; 2 or 1: the
                             column minus the row index in int16 or int8 when
                             every row in the slices stays that close to its
-                            diagonal (else the next wider form).  Measured on
-                            GB300 the 32-bit form is as fast or faster (the
-                            narrower index stream does not shorten the
-                            FP64-issue-bound kernel), hence the default. */
+                            diagonal (else the next wider form); 0: as 1 when
+                            every row has the same length and the rows stay
+                            in order (no slice header is read there, and the
+                            narrower index stream shortens the launch), else
+                            as 4 (with a header to read, the 32-bit form is
+                            as fast or faster on GB300). */
     int32_t index_coding; /* SLICED with FP64 values: 0 = as index_bytes says;
                             1 = Table 2's delta coding (Section 3.3): each
                             column stored as its difference from the
@@ -690,7 +692,11 @@ spmv_status spmv_stream_noalloc(const spmv_csr_t *A, const double *x, double *y,
  * nothing.  The next spmv_stream_noalloc call clears the word. */
 spmv_status spmv_stream_noalloc_status(spmv_stream_t stream);
 
-/* Releases everything P owns (device sync first).  NULL is ignored. */
+/* Releases everything P owns (device sync first).  NULL is ignored.  A
+ * LATENCY object whose x exceeds half the L2 raised this process's
+ * persisting-L2 carve-out when it was prepared; freeing the last such object
+ * on the device releases the persisting lines and puts the carve-out back, so
+ * that the kernels that run afterwards have the whole L2 again. */
 void spmv_prepared_free(spmv_prepared_t *P);
 
 #ifdef __cplusplus

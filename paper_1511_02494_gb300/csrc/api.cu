@@ -16,6 +16,47 @@ thread_local std::string t_last_error;
 constexpr int kMaxDevices = 64;
 DeviceInfo g_dev[kMaxDevices];
 std::mutex g_dev_mu;
+
+// LATENCY's persisting-L2 carve-out (cudaLimitPersistingL2CacheSize, a limit
+// of this process's context): raised by the first prepared object that keeps
+// x persisting, and put back, with every persisting line released, when the
+// last such object on the device is freed.  Persisting lines left behind
+// shrink the L2 of every kernel that runs afterwards (measured: SLICED and
+// DYNAMIC 6-20 % slower on matrices of over 10^6 rows timed after LATENCY
+// had run on a large one).
+std::mutex g_persist_mu;
+int g_persist_users[kMaxDevices] = {};
+size_t g_persist_saved[kMaxDevices] = {};
+
+// Raises the carve-out of device d (current) to at least want bytes and
+// counts a user; false (nothing changed) where the limit cannot be set.
+bool persist_acquire(int d, int64_t want)
+{
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
+        ((int64_t)cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)want) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    if (g_persist_users[d]++ == 0) g_persist_saved[d] = cur;
+    return true;
+}
+
+// One user of device d fewer; the last one releases the persisting lines and
+// puts the carve-out back (with no kernel of the object in flight).
+void persist_release(int d)
+{
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    if (g_persist_users[d] == 0 || --g_persist_users[d] > 0) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return; }
+    if (cur != d && cudaSetDevice(d) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_persist_saved[d]);
+    cudaGetLastError();
+    if (cur != d) cudaSetDevice(cur);
+}
 }  // namespace
 
 void set_error(const std::string& msg) { t_last_error = msg; }
@@ -131,6 +172,10 @@ void release(spmv_prepared_t* P)
     for (void* p : P->owned)
         if (p) cudaFree(p);
     P->owned.clear();
+    if (P->persist_held) {
+        persist_release(P->device);
+        P->persist_held = false;
+    }
 }
 
 int32_t launches_of(const spmv_prepared_t* P)
@@ -235,16 +280,12 @@ spmv_status prepare_impl(spmv_prepared_t* P, cudaStream_t s)
             int64_t want = xbytes < dev.max_persist_l2 ? xbytes : dev.max_persist_l2;
             if (2 * xbytes <= (int64_t)dev.l2_bytes) want = 0;
             if (want > dev.max_window) want = dev.max_window;
-            // the persisting-L2 carve-out is a limit of this process's context;
-            // where it cannot be set the variant runs without the window
+            // the persisting-L2 carve-out is a limit of this process's context,
+            // held while the object lives; where it cannot be set the variant
+            // runs without the window
             if (want > 0) {
-                size_t cur = 0;
-                if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
-                    ((int64_t)cur < want &&
-                     cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)want) != cudaSuccess)) {
-                    cudaGetLastError();
-                    want = 0;
-                }
+                if (persist_acquire(dev.device, want)) P->persist_held = true;
+                else want = 0;
             }
             P->l2_window_bytes = (int)(want > 0 ? want : 0);
             return SPMV_OK;

@@ -66,6 +66,7 @@ constexpr int kSlicedSeg = 2048;
 struct SlicedPlan {
     int64_t n_slices = 0, tot = 0;
     int sigma = 1, n_long = 0;
+    int uniform_len = -1;        // >= 0: every row has this many nonzeros, rows in order, none long
     int* rowlen = nullptr;       // [32 n_slices] row length per position, -1: long or absent
     int* slice_len = nullptr;    // [n_slices]
     int64_t* slice_ptr = nullptr;  // [n_slices + 1] element offset of each slice
@@ -118,6 +119,7 @@ struct spmv_prepared {
     int64_t owned_bytes = 0;
     int sm_count = 0;
     int l2_window_bytes = 0;       // LATENCY: bytes of x kept persisting in L2
+    bool persist_held = false;     // LATENCY: counted among the persisting-L2 users
     int tile_items = 0;            // MERGE: path items per tile (CTA or warp)
     bool bulk = false;             // STREAM / MERGE: pipelined bulk-copy kernel in use
     unsigned* status = nullptr;    // device status word (bounded-wait timeouts)

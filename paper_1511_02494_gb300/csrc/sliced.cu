@@ -212,6 +212,18 @@ __global__ void k_sl_fill_coded(int64_t n_slices, const int* __restrict__ rp, co
     }
 }
 
+// the shortest row length over the positions holding rows (min into *out,
+// which starts at INT_MAX)
+__global__ void k_sl_min_len(int64_t n_rows, const int* __restrict__ rowlen, int* __restrict__ out)
+{
+    int m = 0x7fffffff;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_rows;
+         p += (int64_t)gridDim.x * blockDim.x)
+        m = min(m, rowlen[p]);
+    m = __reduce_min_sync(FULL, m);
+    if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
 // rows longer than cap, appended with one atomic per warp
 __global__ void k_sl_long_list(int64_t n_rows, const int* __restrict__ rp, int cap,
                                int* __restrict__ list, unsigned* __restrict__ count)
@@ -262,6 +274,58 @@ k_sliced_coded(int64_t n_slices, const int* __restrict__ rowlen, const int* __re
     const double v = slice_value_coded<U, MODE, DT>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm,
                                                     cs, step, rowbase, val, x, &row);
     if (row >= 0) y[row] = v;
+}
+
+// Every row of length L in order, none long (an ELLPACK matrix): slice s
+// starts at slot 32 L s and holds rows 32 s .. 32 s + 31, so no slice header
+// (row lengths, slice length and start) is read -- one dependent memory
+// round trip less per slice, which matters where a lane has only a few
+// elements.  R slices per warp, U elements of each row in flight; each row
+// is the same DFMA chain as in slice_rows / slice_rows_multi.
+template <int U, int R, int B, typename CT>
+__global__ void __launch_bounds__(kSB, B)
+k_sliced_uniform(int64_t n_rows, int64_t n_slices, int L, const CT* __restrict__ col,
+                 const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s0 = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
+    if (s0 >= n_slices) return;  // whole warps only
+    int64_t q0[R];
+    int row[R];
+    bool in[R];
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t p = (s0 + r) * 32 + lane;
+        in[r] = s0 + r < n_slices && p < n_rows;
+        row[r] = in[r] ? (int)p : 0;
+        q0[r] = (s0 + r) * 32 * (int64_t)L + lane;
+        acc[r] = 0.0;
+    }
+    for (int k = 0; k < L; k += U) {
+        int c[R][U];
+        double a[R][U], xv[R][U];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = in[r] && k + u < L;
+                c[r][u] = ok ? column_of(__ldcs(col + q0[r] + (int64_t)(k + u) * 32), row[r]) : 0;
+                a[r][u] = ok ? __ldcs(val + q0[r] + (int64_t)(k + u) * 32) : 0.0;
+            }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[r][u] = in[r] && k + u < L ? ldx(x + c[r][u]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (in[r] && k + u < L) acc[r] = fma(a[r][u], xv[r][u], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (in[r]) y[row[r]] = acc[r];
 }
 
 // R consecutive slices per warp (slice_rows_multi), for short slices whose
@@ -603,6 +667,18 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
     }
     d.n_long = (int)n_long;
     d.tot = sptr[d.n_slices];
+    // rows all of one length, in order, none long: the slice header is implied
+    d.uniform_len = -1;
+    if (sigma == 1 && n_long == 0 && A.n_rows > 0) {
+        int shortest = 0x7fffffff;
+        SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0x7f, 4, s));
+        k_sl_min_len<<<rows_grid, kSB, 0, s>>>(A.n_rows, d.rowlen, reinterpret_cast<int*>(d.count));
+        SPMV_CUDA_TRY(cudaGetLastError());
+        SPMV_CUDA_TRY(cudaMemcpyAsync(&shortest, d.count, 4, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        const int longest = *std::max_element(slen.begin(), slen.begin() + d.n_slices);
+        if (shortest == longest) d.uniform_len = longest;
+    }
     SPMV_CUDA_TRY(cudaMemcpyAsync(d.slice_ptr, sptr.data(), 8 * (d.n_slices + 1), cudaMemcpyHostToDevice, s));
     const int64_t tot1 = std::max<int64_t>(d.tot, 1);
     const int* permp = sigma > 1 ? d.perm : nullptr;
@@ -639,7 +715,12 @@ spmv_status sliced_prepare(spmv_prepared* P, cudaStream_t s)
                 if (r <= 255) { d.coding = 2; d.cbytes = 3; }
             }
         }
-        const int allowed = d.coding != 0 ? 4 : (P->c.index_bytes == 0 ? 4 : P->c.index_bytes);
+        // index_bytes 0: the narrowest form that fits when the rows are all of
+        // one length and in order (k_sliced_uniform, where the narrower column
+        // stream shortens the launch), else 32-bit columns
+        const int allowed = d.coding != 0 ? 4
+                            : P->c.index_bytes != 0 ? P->c.index_bytes
+                            : d.uniform_len >= 0 ? 1 : 4;
         unsigned reach = 0;
         if (d.n_slices > 0 && allowed < 4) {
             SPMV_CUDA_TRY(cudaMemsetAsync(d.count, 0, 4, s));
@@ -839,6 +920,23 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
         else if (d.coding == 1) SPMV_SL_CODED(1, uint16_t);
         else SPMV_SL_CODED(2, uint16_t);
 #undef SPMV_SL_CODED
+        return cudaGetLastError();
+    }
+    if (d.value_type == SPMV_VAL_F64 && d.uniform_len >= 0) {
+        // rows of one length: no slice header (k_sliced_uniform)
+        const int R = P->c.threads_per_row == 2 || P->c.threads_per_row == 4 ? P->c.threads_per_row : 1;
+        const unsigned ugrid = grid_of(32 * ((d.n_slices + R - 1) / R), INT32_MAX);
+#define SPMV_SL_U(U, RR, B, CT)                                                                    \
+    k_sliced_uniform<U, RR, B, CT><<<ugrid, kSB, 0, s>>>(A.n_rows, d.n_slices, d.uniform_len,      \
+                                                         static_cast<const CT*>(d.scol), d.val, x, y)
+#define SPMV_SL_U_CT(CT)                                                                           \
+        if (R == 4) SPMV_SL_U(1, 4, 4, CT); else if (R == 2) SPMV_SL_U(2, 2, 6, CT);               \
+        else SPMV_SL_U(4, 1, 8, CT);
+        if (d.cbytes == 1) { SPMV_SL_U_CT(int8_t) }
+        else if (d.cbytes == 2) { SPMV_SL_U_CT(int16_t) }
+        else { SPMV_SL_U_CT(int) }
+#undef SPMV_SL_U_CT
+#undef SPMV_SL_U
         return cudaGetLastError();
     }
     if (d.value_type == SPMV_VAL_F64) {

@@ -58,8 +58,12 @@ def matrix_spec(i: int):
     return family, n_rows
 
 
-def time_variant(dA, v: int, x, y, budget_ms: float = 25.0):
-    P = sp.spmv_prepare(dA, sp.make_choice(v), trusted=True)
+def time_prepared(P, x, y, budget_ms: float = 25.0, window_ms: float = 0.5):
+    """Milliseconds per SpMV of a prepared matrix, as in a solver's loop:
+    after a warm-up, one launch is timed; unless it took budget_ms or more,
+    the median of three runs of back-to-back launches, each about window_ms
+    long (so that the few microseconds of launch and event overhead do not
+    decide between variants of small matrices)."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sp.spmv(P, x, y)  # warm-up
     e0.record()
@@ -67,16 +71,25 @@ def time_variant(dA, v: int, x, y, budget_ms: float = 25.0):
     e1.record()
     e1.synchronize()
     first = e0.elapsed_time(e1)
-    ts = [first]
-    if first < budget_ms:
-        for _ in range(3):
-            e0.record()
+    if first >= budget_ms:
+        return float(first)
+    reps = int(min(200, max(1, window_ms / max(first, 1e-3))))
+    ts = []
+    for _ in range(3):
+        e0.record()
+        for _ in range(reps):
             sp.spmv(P, x, y)
-            e1.record()
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-    P.free()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / reps)
     return float(np.median(ts))
+
+
+def time_variant(dA, v: int, x, y, budget_ms: float = 25.0):
+    P = sp.spmv_prepare(dA, sp.make_choice(v), trusted=True)
+    t = time_prepared(P, x, y, budget_ms)
+    P.free()
+    return t
 
 
 def build_dataset(n: int, out_path: str, resume: bool = True, log=print):
@@ -341,19 +354,9 @@ SLICED_CONFIGS = (
 
 def time_choice(dA, ch, x, y, budget_ms: float = 25.0):
     P = sp.spmv_prepare(dA, ch, trusted=True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sp.spmv(P, x, y)  # warm-up
-    ts = []
-    for _ in range(4):
-        e0.record()
-        sp.spmv(P, x, y)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-        if ts[0] >= budget_ms:
-            break
+    t = time_prepared(P, x, y, budget_ms)
     P.free()
-    return float(np.median(ts))
+    return t
 
 
 def sliced_dataset(d, out_path: str, retime: bool = False, log=print):

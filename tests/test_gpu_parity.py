@@ -304,7 +304,7 @@ def test_sliced_layout_bit_exact(sigma, cap, name, A):
     """The SLICED prepared arrays equal the oracle's sliced layout, for the
     default row-length cap (1024) and chosen ones."""
     dA = sp.DeviceCSR.from_host(A)
-    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma,
+    P = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, index_bytes=4,
                                            items_per_warp=0 if cap == 1024 else cap))
     perm, rowlen, slen, sptr, n_long = oracle.sliced_layout(A, sigma, cap)
     S = (A.n_rows + 31) // 32
@@ -336,6 +336,13 @@ def test_sliced_layout_bit_exact(sigma, cap, name, A):
     Q = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, index_bytes=1,
                                            items_per_warp=0 if cap == 1024 else cap))
     assert Q.info().index_bytes == nb
+    # by default the narrowest form only where every row has one length and
+    # the rows stay in order (no slice header), else 32-bit columns
+    lens = np.diff(A.rowptr.numpy())
+    uniform = A.n_rows > 0 and sigma == 1 and n_long == 0 and lens.min() == lens.max()
+    D = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma,
+                                           items_per_warp=0 if cap == 1024 else cap))
+    assert D.info().index_bytes == (nb if uniform else 4)
     if tot and nb < 4:
         got = _export(Q, sp.EXPORT_SLICE_DIAG, tot, torch.int8 if nb == 1 else torch.int16)
         assert np.array_equal(got.astype(np.int32), d)
@@ -427,6 +434,34 @@ def test_sliced_index_width_at_its_boundaries(reach, nb):
         y = torch.empty(n, dtype=torch.float64, device="cuda")
         sp.spmv(P, x.cuda(), y)
         assert np.array_equal(y.cpu().numpy(), oracle.spmv(A, x))
+
+
+UNIFORM = [("random_cols_16", synth.random_columns(70_001, 70_001, 16, seed=11)),
+           ("random_cols_37", synth.random_columns(2049, 5000, 37, seed=14)),
+           ("random_cols_1", synth.random_columns(3000, 50, 1, seed=13)),
+           ("short_rows", synth.short_rows(50_001, 8, seed=12)),
+           ("all_empty", synth.random_csr(777, 100, 0, seed=8))]
+
+
+@pytest.mark.parametrize("tpr", [0, 1, 2, 4])
+@pytest.mark.parametrize("nb", [4, 1])
+@pytest.mark.parametrize("name,A", UNIFORM, ids=[m[0] for m in UNIFORM])
+def test_sliced_uniform_rows_bit_exact(name, A, nb, tpr):
+    """Rows all of one length, kept in order: the slice starts are implied
+    by the length and no header is read.  The same rows laid out in sorted
+    windows of 32 (read through the slice header) give the same bits, y is
+    within the bound of the oracle's, and bit-exact with it on integer data."""
+    x = synth.uniform_vector(A.n_cols, 3)
+    ys = [_run(A, sp.make_choice("sliced", block_nnz=sigma, index_bytes=nb, threads_per_row=tpr), x)[0]
+          for sigma in (1, 32)]
+    assert torch.equal(ys[0], ys[1])
+    _assert_close(ys[0], A, x)
+    g = np.random.default_rng(A.nnz)
+    vi = torch.from_numpy(g.integers(-9, 10, A.nnz).astype(np.float64))
+    Ai = synth.HostCSR(A.n_rows, A.n_cols, A.rowptr, A.colind, vi, A.name)
+    xi = torch.from_numpy(g.integers(-20, 21, A.n_cols).astype(np.float64))
+    y, _ = _run(Ai, sp.make_choice("sliced", block_nnz=1, index_bytes=nb, threads_per_row=tpr), xi)
+    assert np.array_equal(y.cpu().numpy(), oracle.spmv(Ai, xi))
 
 
 def test_sliced_auto_window_and_long_rows():
@@ -675,6 +710,39 @@ def test_spmv_host_async_on_several_streams():
 @pytest.fixture(scope="module")
 def four_class():
     return synth.four_class_set()
+
+
+def test_latency_persisting_carve_out_released():
+    """LATENCY with an x over half the L2 raises the persisting-L2 carve-out
+    while an object needs it; freeing the last such object puts it back, so
+    that later kernels get the whole L2 (stale persisting lines measured
+    6-20 % slower SLICED and DYNAMIC launches)."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+
+    def limit():
+        v = ctypes.c_size_t()
+        assert cu.cuCtxGetLimit(ctypes.byref(v), 6) == 0  # CU_LIMIT_PERSISTING_L2_CACHE_SIZE
+        return v.value
+
+    torch.cuda.synchronize()
+    before = limit()
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20)
+    A = synth.random_columns(4096, l2 // 8 + 4096, 8, seed=21)  # x of more than the whole L2
+    dA = sp.DeviceCSR.from_host(A)
+    P = sp.spmv_prepare(dA, sp.make_choice("latency"))
+    raised = limit()
+    assert raised >= before
+    x = synth.uniform_vector(A.n_cols, 4)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    sp.spmv(P, x.cuda(), y)
+    torch.cuda.synchronize()
+    _assert_close(y, A, x)
+    Q = sp.spmv_prepare(dA, sp.make_choice("latency"))  # a second user
+    P.free()
+    assert limit() == raised
+    Q.free()
+    assert limit() == before
 
 
 def _sample_rows(A, k=3000, seed=0):
