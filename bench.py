@@ -736,7 +736,7 @@ def run_coding(args):
         y0 = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
         y = torch.empty_like(y0)
         base = None
-        for form, kw in (("int32", {}), ("row_offset", {"index_bytes": 1}),
+        for form, kw in (("int32", {"index_bytes": 4}), ("row_offset", {"index_bytes": 1}),
                          ("delta", {"index_coding": 1}), ("panel", {"index_coding": 2})):
             P = sp.spmv_prepare(dA, sp.make_choice("sliced", **kw))
             info = P.info()

@@ -609,7 +609,7 @@ int64_t orc_sliced_delta(int64_t n_rows, const int32_t *rowptr, const int32_t *c
     return largest;
 }
 
-/* "8- or 16-bit deltas wherever possible, but never both" (Section 3.3), per
+/* Section 3.3's delta width, one width only (8 or 16 bits, not a mix), per
  * matrix: 1 byte when every delta is at most 255, 2 when at most 65535, 0
  * when some delta needs more (the delta coding does not apply).               */
 int32_t orc_delta_bytes(int64_t largest_delta)
