@@ -367,6 +367,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         P = sp.spmv_prepare(dA, ch)
         rec["prepare_ms"] = (time.perf_counter() - t0) * 1e3
+        rec["choice"] = ch
         rec["selected_min_bytes"] = P.info().min_bytes
         # the profiling rule's own choice (its class's variant and launch
         # configuration), timed alone like the variants below
@@ -482,35 +483,46 @@ def run_ours(args):
     # every step uploads each matrix's x from pinned memory, runs its SpMV
     # and downloads y (spmv_host_async, one stream per matrix so that one
     # matrix's copies overlap another's SpMV).  The steps are pipelined: the
-    # host waits for the streams once, after the last step, so a step's
-    # uploads overlap the previous step's downloads on the link (each
-    # matrix's own steps stay in order on its stream).  The same with a wait
-    # after every step is reported beside it.
+    # host waits for the streams once, after the last step, and each matrix
+    # has a second prepared object (its own staging buffers) on a second
+    # stream, used on alternate steps, so that one step's uploads and
+    # downloads overlap the next step's SpMVs.  The same with one object
+    # per matrix and a wait after every step is reported beside it, and the
+    # bound the host link sets (the step's copies at the link's measured
+    # rate, both directions at once).
     hx = [x.cpu().pin_memory() for x in xs]
-    hy = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for A in mats]
-    streams = [torch.cuda.Stream() for _ in mats]
+    hy = [[torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for A in mats] for _ in range(2)]
+    streams = [[torch.cuda.Stream() for _ in mats] for _ in range(2)]
+    twin = [sp.spmv_prepare(dA, r["choice"]) for dA, r in zip(dev, per)]
+    objs = [[r["P"] for r in per], twin]
 
-    def e2e_step(wait):
-        for r, a, b, st in zip(per, hx, hy, streams):
-            sp.spmv_host_async(r["P"], a, b, stream=st)
+    def e2e_step(k, wait):
+        b = 0 if wait else k % 2
+        for P, a, hb, st in zip(objs[b], hx, hy[b], streams[b]):
+            sp.spmv_host_async(P, a, hb, stream=st)
         if wait:
-            for st in streams:
+            for st in streams[b]:
                 st.synchronize()
-    e2e_step(True)
+    for k in range(2):
+        e2e_step(k, False)
     torch.cuda.synchronize()
     e2e_s = {}
     for wait in (False, True):
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step(wait)
-        for st in streams:
-            st.synchronize()
+        for k in range(args.steps):
+            e2e_step(k, wait)
+        torch.cuda.synchronize()
         e2e_s[wait] = time.perf_counter() - t0
+    for P in twin:
+        P.free()
+    h2d_b, d2h_b = sum(8 * A.n_cols for A in mats), sum(8 * A.n_rows for A in mats)
+    link = _link_gbs(torch, max(h2d_b, d2h_b) // 4)
     e2e = {"value": step_bytes * args.steps / e2e_s[False] / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": sum(8 * A.n_cols for A in mats),
-           "d2h_bytes_per_step": sum(8 * A.n_rows for A in mats),
-           "pipelined_steps": True,
-           "value_waiting_every_step": step_bytes * args.steps / e2e_s[True] / 1e9}
+           "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+           "pipelined_steps": True, "prepared_objects_per_matrix": 2,
+           "value_waiting_every_step": step_bytes * args.steps / e2e_s[True] / 1e9,
+           "link_gbs": {k: round(v, 1) for k, v in link.items()},
+           "link_bound": round(step_bytes / ((h2d_b + d2h_b) / (link["both_directions"] * 1e9)) / 1e9, 1)}
 
     # ---------------- report
     dom = int(np.argmax(kern_ms))
@@ -619,6 +631,35 @@ def run_single(args):
     sp.spmv_prepared_status(P)
     print(json.dumps({"single": args.single, "matrix": A.name, "info": P.info().as_dict()}))
     return 0
+
+
+def _link_gbs(torch, nbytes: int) -> dict:
+    """Host link rates (GB/s) of pinned-memory copies of nbytes: each
+    direction alone, and both directions at once (aggregate)."""
+    n = max(1, nbytes // 8)
+    h1 = torch.ones(n, dtype=torch.float64).pin_memory()
+    h2 = torch.empty(n, dtype=torch.float64).pin_memory()
+    d1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    d2 = torch.ones(n, dtype=torch.float64, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def rate(fn, moved, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return moved * reps / (time.perf_counter() - t0) / 1e9
+
+    def both():
+        with torch.cuda.stream(s1):
+            d1.copy_(h1, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+    return {"h2d": rate(lambda: d1.copy_(h1, non_blocking=True), 8 * n),
+            "d2h": rate(lambda: h2.copy_(d2, non_blocking=True), 8 * n),
+            "both_directions": rate(both, 16 * n)}
 
 
 def _events():
