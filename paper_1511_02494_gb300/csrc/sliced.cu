@@ -276,12 +276,9 @@ k_sliced_coded(int64_t n_slices, const int* __restrict__ rowlen, const int* __re
     if (row >= 0) y[row] = v;
 }
 
-// Every row of length L in order, none long (an ELLPACK matrix): slice s
-// starts at slot 32 L s and holds rows 32 s .. 32 s + 31, so no slice header
-// (row lengths, slice length and start) is read -- one dependent memory
-// round trip less per slice, which matters where a lane has only a few
-// elements.  R slices per warp, U elements of each row in flight; each row
-// is the same DFMA chain as in slice_rows / slice_rows_multi.
+// Every row of length L in order, none long (an ELLPACK matrix): R slices
+// per warp with no slice header read (uniform_rows); each row is the same
+// DFMA chain as in slice_rows / slice_rows_multi.
 template <int U, int R, int B, typename CT>
 __global__ void __launch_bounds__(kSB, B)
 k_sliced_uniform(int64_t n_rows, int64_t n_slices, int L, const CT* __restrict__ col,
@@ -290,42 +287,7 @@ k_sliced_uniform(int64_t n_rows, int64_t n_slices, int L, const CT* __restrict__
     const int lane = threadIdx.x & 31;
     const int64_t s0 = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
     if (s0 >= n_slices) return;  // whole warps only
-    int64_t q0[R];
-    int row[R];
-    bool in[R];
-    double acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int64_t p = (s0 + r) * 32 + lane;
-        in[r] = s0 + r < n_slices && p < n_rows;
-        row[r] = in[r] ? (int)p : 0;
-        q0[r] = (s0 + r) * 32 * (int64_t)L + lane;
-        acc[r] = 0.0;
-    }
-    for (int k = 0; k < L; k += U) {
-        int c[R][U];
-        double a[R][U], xv[R][U];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = in[r] && k + u < L;
-                c[r][u] = ok ? column_of(__ldcs(col + q0[r] + (int64_t)(k + u) * 32), row[r]) : 0;
-                a[r][u] = ok ? __ldcs(val + q0[r] + (int64_t)(k + u) * 32) : 0.0;
-            }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int u = 0; u < U; ++u) xv[r][u] = in[r] && k + u < L ? ldx(x + c[r][u]) : 0.0;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (in[r] && k + u < L) acc[r] = fma(a[r][u], xv[r][u], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (in[r]) y[row[r]] = acc[r];
+    uniform_rows<U, R, CT>(s0, n_slices, n_rows, L, lane, col, val, x, y);
 }
 
 // R consecutive slices per warp (slice_rows_multi), for short slices whose

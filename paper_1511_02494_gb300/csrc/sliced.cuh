@@ -134,6 +134,56 @@ __device__ __forceinline__ void slice_rows_multi(int64_t s0, int64_t n_slices, i
         if (row[r] >= 0) y[row[r]] = acc[r];
 }
 
+// Slices s0 .. s0 + R - 1 of a layout whose rows all have length L, in
+// order, none long (an ELLPACK matrix): slice s starts at 32 L s and holds
+// rows 32 s .. 32 s + 31, so no slice header (row lengths, slice length and
+// start) is read -- one dependent round trip less per slice.  The lane sums
+// one row of each slice with the same FMA chain as slice_value, U elements
+// of every row in flight; slices at or past s_end and rows at or past n_rows
+// are skipped.
+template <int U, int R, typename CT = int>
+__device__ __forceinline__ void uniform_rows(int64_t s0, int64_t s_end, int64_t n_rows, int L, int lane,
+                                             const CT* __restrict__ col, const double* __restrict__ val,
+                                             const double* __restrict__ x, double* __restrict__ y)
+{
+    int64_t q0[R];
+    int row[R];
+    bool in[R];
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t p = (s0 + r) * 32 + lane;
+        in[r] = s0 + r < s_end && p < n_rows;
+        row[r] = in[r] ? (int)p : 0;
+        q0[r] = (s0 + r) * 32 * (int64_t)L + lane;
+        acc[r] = 0.0;
+    }
+    for (int k = 0; k < L; k += U) {
+        int c[R][U];
+        double a[R][U], xv[R][U];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = in[r] && k + u < L;
+                c[r][u] = ok ? column_of(__ldcs(col + q0[r] + (int64_t)(k + u) * 32), row[r]) : 0;
+                a[r][u] = ok ? __ldcs(val + q0[r] + (int64_t)(k + u) * 32) : 0.0;
+            }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[r][u] = in[r] && k + u < L ? ldx(x + c[r][u]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (in[r] && k + u < L) acc[r] = fma(a[r][u], xv[r][u], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (in[r]) y[row[r]] = acc[r];
+}
+
 // FP64 values with coded columns.  A lane walks its row in order, so a
 // column is decoded from the one before it with integer operations:
 //   MODE 1, Table 2's delta coding: cs (DT = uint8_t or uint16_t) holds the
