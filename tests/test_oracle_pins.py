@@ -846,3 +846,58 @@ def test_cg_refinement_converges_to_the_fp64_solution():
         np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-12)
     xn, _ = oracle.cg(A, b, np.zeros(A.n_rows), 200, vkind=2, lowval=low, refine=0)
     assert np.max(np.abs(xn - xs)) > 1e-5 * np.max(np.abs(xs))
+
+
+# ----------------------------------------------------------------- Adam
+def _adam_run(p0, grads, lr, b1, b2, eps, wd):
+    """Steps of the oracle's Adam from m = v = 0 with the bias corrections
+    c1 = 1 - b1^t, c2 = 1 - b2^t of step t."""
+    p = np.asarray(p0, np.float32)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t, g in enumerate(grads, 1):
+        p, m, v = oracle.adam_f32(p, np.asarray(g, np.float32), m, v, lr, b1, b2, eps, wd,
+                                  np.float32(1 - b1 ** t), np.float32(1 - b2 ** t))
+    return p, m, v
+
+
+def test_adam_first_step_is_lr_whatever_the_gradient_scale():
+    """With bias correction, the first step divides m_hat = g by
+    sqrt(v_hat) = |g|: every coordinate moves by lr against the sign of its
+    gradient, whatever the gradient's size (eps small against |g|)."""
+    g = np.array([1e-3, -0.5, 2.0, -7e2, 3e4], np.float32)
+    p0 = np.zeros(g.size, np.float32)
+    p1, _, _ = _adam_run(p0, [g], lr=1e-2, b1=0.9, b2=0.999, eps=1e-12, wd=0.0)
+    np.testing.assert_allclose(p0 - p1, 1e-2 * np.sign(g), rtol=1e-5)
+
+
+def test_adam_constant_gradient_moves_lr_every_step():
+    """A constant gradient keeps m_hat = g and v_hat = g^2 at every step t
+    (the bias corrections undo the zero start), so t steps move t * lr;
+    a wrong correction would shrink or grow the early steps."""
+    g = np.array([0.25, -3.0], np.float32)
+    p0 = np.zeros(2, np.float32)
+    p, _, _ = _adam_run(p0, [g] * 10, lr=1e-3, b1=0.9, b2=0.999, eps=1e-12, wd=0.0)
+    np.testing.assert_allclose(p0 - p, 10 * 1e-3 * np.sign(g), rtol=1e-4)
+
+
+def test_adam_is_scale_invariant_bit_for_bit():
+    """With eps = 0, scaling every gradient by a power of two scales m by it
+    and v by its square exactly, so sqrt(v) scales back and the parameters
+    follow the same trajectory bit for bit."""
+    rng = np.random.default_rng(5)
+    grads = [rng.standard_normal(16).astype(np.float32) for _ in range(6)]
+    p0 = rng.standard_normal(16).astype(np.float32)
+    a, _, _ = _adam_run(p0, grads, 3e-3, 0.9, 0.999, 0.0, 1e-2)
+    b, _, _ = _adam_run(p0, [np.float32(64.0) * g for g in grads], 3e-3, 0.9, 0.999, 0.0, 1e-2)
+    assert np.array_equal(a, b)
+
+
+def test_adam_weight_decay_is_decoupled():
+    """A zero gradient leaves m = v = 0 and the update is the decay alone:
+    p <- p - lr * wd * p (decoupled from the gradient; an L2 term added to
+    the gradient would instead be normalised to a step of about lr)."""
+    p0 = np.array([2.0, -0.5, 8.0], np.float32)
+    p1, m, v = _adam_run(p0, [np.zeros(3, np.float32)], lr=0.1, b1=0.9, b2=0.999, eps=1e-8, wd=0.05)
+    assert not m.any() and not v.any()
+    np.testing.assert_allclose(p1, p0 * (1 - 0.1 * 0.05), rtol=1e-6)
