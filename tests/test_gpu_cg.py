@@ -51,6 +51,45 @@ def test_cg_fp64_matches_oracle(variant, graph):
     assert r[-1] < 1e-6 * r[0]
 
 
+def _periodic_laplacian(n: int, shift: float, seed: int):
+    """2-D five-point operator on an n x n torus with a diagonal of 4 + shift
+    and random off-diagonal weights in [-1, -0.5], symmetrised: SPD, and
+    every row has five nonzeros (the uniform sliced layout)."""
+    g = np.random.default_rng(seed)
+    N = n * n
+    idx = lambda i, j: (i % n) * n + (j % n)
+    w_right = -g.uniform(0.5, 1.0, N)
+    w_down = -g.uniform(0.5, 1.0, N)
+    rows = []
+    for i in range(n):
+        for j in range(n):
+            r = idx(i, j)
+            e = {r: 4.0 + shift,
+                 idx(i, j + 1): w_right[r], idx(i, j - 1): w_right[idx(i, j - 1)],
+                 idx(i + 1, j): w_down[r], idx(i - 1, j): w_down[idx(i - 1, j)]}
+            rows.append(sorted(e.items()))
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.array([c for r in rows for c, _ in r], np.int32)
+    va = np.array([v for r in rows for _, v in r], np.float64)
+    return synth.HostCSR(N, N, torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(va),
+                         f"torus_{n}")
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_cg_rows_of_one_length(graph):
+    """Every row of the torus operator has five nonzeros: SLICED's default
+    form stores its columns as int16 offsets from the row, and the CG loop
+    (fused SpMV and dot) runs on that form; it agrees with the oracle."""
+    A = _periodic_laplacian(24, 0.5, seed=7)
+    P = sp.spmv_prepare(sp.DeviceCSR.from_host(A), sp.make_choice("sliced"))
+    assert P.info().index_bytes == 2 and P.info().block_nnz == 1
+    b = synth.uniform_vector(A.n_rows, 5)
+    x, r = _run(A, b, 40, sp.make_choice("sliced"), graph=graph)
+    xo, ro = oracle.cg(A, b, np.zeros(A.n_rows), 40)
+    _close(x, r, xo, ro)
+    assert r[-1] < 1e-6 * r[0]
+
+
 @pytest.mark.parametrize("vt,vkind", [(sp.VAL_F32, 1), (sp.VAL_BF16, 2)])
 @pytest.mark.parametrize("refine", [0, 10])
 def test_cg_low_precision_inner_matches_oracle(vt, vkind, refine):
