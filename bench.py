@@ -380,7 +380,8 @@ def run_ours(args):
         rec["selected_alone_ms"] = time_spmv(P, x, y, reps=10)
         inf = P.info()
         rec["launch"] = {"threads_per_row": inf.threads_per_row, "block_nnz": inf.block_nnz,
-                         "items_per_warp": inf.items_per_warp}
+                         "items_per_warp": inf.items_per_warp, "index_bytes": inf.index_bytes,
+                         "uniform_len": inf.uniform_len}
         # every variant, for the "best possible" comparison
         times = {}
         for v, kw in ([] if args.no_variant_sweep else candidates):

@@ -259,6 +259,10 @@ typedef struct {
     int32_t index_coding;  /* SLICED with FP64 values: the column coding in
                               use, 0, 1 (deltas) or 2 (panels), as in
                               spmv_choice_t; 0 for the other variants         */
+    int32_t uniform_len;   /* SLICED with FP64 values and uncoded columns: the
+                              length every row has, when they all have one,
+                              the rows stay in order and none is long (the
+                              kernel then reads no slice header); else -1    */
 } spmv_prepared_info_t;
 
 /* Arrays a prepared object can export (spmv_prepared_export). */

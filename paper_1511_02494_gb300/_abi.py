@@ -78,7 +78,7 @@ class PreparedInfo(C.Structure):
                                   "owned_bytes", "min_bytes")] + \
         [("tile_items", C.c_int32), ("bulk_copy", C.c_int32), ("accumulate", C.c_int32),
          ("launches", C.c_int32), ("index_bytes", C.c_int32), ("n_long_rows", C.c_int64),
-         ("index_coding", C.c_int32)]
+         ("index_coding", C.c_int32), ("uniform_len", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

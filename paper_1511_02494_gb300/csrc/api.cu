@@ -695,6 +695,8 @@ spmv_status spmv_prepared_info(const spmv_prepared_t* P, spmv_prepared_info_t* i
     i.index_bytes = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.cbytes : 4;
     i.n_long_rows = P->c.variant == SPMV_V7_SLICED ? P->sl.n_long : 0;
     i.index_coding = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 ? P->sl.coding : 0;
+    i.uniform_len = P->c.variant == SPMV_V7_SLICED && P->sl.value_type == SPMV_VAL_F64 && P->sl.coding == 0
+                        ? P->sl.uniform_len : -1;
     *info = i;
     return SPMV_OK;
 }

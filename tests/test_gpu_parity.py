@@ -452,6 +452,12 @@ def test_sliced_uniform_rows_bit_exact(name, A, nb, tpr):
     windows of 32 (read through the slice header) give the same bits, y is
     within the bound of the oracle's, and bit-exact with it on integer data."""
     x = synth.uniform_vector(A.n_cols, 3)
+    lens = np.diff(A.rowptr.numpy())
+    dA = sp.DeviceCSR.from_host(A)
+    for sigma, want in ((1, int(lens[0])), (32, -1)):
+        info = sp.spmv_prepare(dA, sp.make_choice("sliced", block_nnz=sigma, index_bytes=nb,
+                                                  threads_per_row=tpr)).info()
+        assert info.uniform_len == want
     ys = [_run(A, sp.make_choice("sliced", block_nnz=sigma, index_bytes=nb, threads_per_row=tpr), x)[0]
           for sigma in (1, 32)]
     assert torch.equal(ys[0], ys[1])
