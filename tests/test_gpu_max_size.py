@@ -6,7 +6,8 @@ Row i < N - 1 holds columns {i, i + 1}; the last row holds {0, N - 1}.
   aggregate of this matrix follows from the two row kinds, so the GPU's
   exact integer sums (64- and 128-bit) are checked bit for bit.
 * y of the plain CSR kernel and of SLICED (whose slice storage here holds
-  2^31 slots, so slot indices pass 32 bits) on sampled rows -- the first,
+  2^31 slots, so slot indices pass 32 bits; every row has two nonzeros, so
+  it is the header-free kernel) on sampled rows -- the first,
   the last and 4096 random ones -- against the oracle's product of those rows,
   within 1e-12 * sum_j |a_ij x_j|.
 About 80 GB of device memory; the arrays are built on the device in chunks.
@@ -91,7 +92,11 @@ def test_spmv_at_the_size_limit(big, variant):
     P = sp.spmv_prepare(A, sp.make_choice(variant))
     info = P.info()
     if variant == "sliced":
+        # every row has two nonzeros: the header-free kernel, whose slot
+        # index 64 s + 32 k + lane passes 2^31; the last row's reach keeps
+        # 32-bit columns
         assert info.n_blocks == (N + 31) // 32 and info.n_long_rows == 0
+        assert info.uniform_len == 2 and info.index_bytes == 4
     y = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
     sp.spmv(P, x, y)
     torch.cuda.synchronize()
