@@ -285,9 +285,18 @@ k_sliced_uniform(int64_t n_rows, int64_t n_slices, int L, const CT* __restrict__
                  const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t s0 = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
-    if (s0 >= n_slices) return;  // whole warps only
-    uniform_rows<U, R, CT>(s0, n_slices, n_rows, L, lane, col, val, x, y);
+    const int64_t first = (((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5) * R;
+    if constexpr (R == 4) {
+        // four slices per warp (64 registers, 4 blocks per SM): one resident
+        // grid whose warps stride over the slices, instead of many short
+        // blocks waiting for an SM slot
+        const int64_t step = (int64_t)gridDim.x * (kSB / 32) * R;
+        for (int64_t s0 = first; s0 < n_slices; s0 += step)
+            uniform_rows<U, R, CT>(s0, n_slices, n_rows, L, lane, col, val, x, y);
+    } else {
+        if (first >= n_slices) return;  // whole warps only
+        uniform_rows<U, R, CT>(first, n_slices, n_rows, L, lane, col, val, x, y);
+    }
 }
 
 // R consecutive slices per warp (slice_rows_multi), for short slices whose
@@ -892,7 +901,7 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
     if (d.value_type == SPMV_VAL_F64 && d.uniform_len >= 0) {
         // rows of one length: no slice header (k_sliced_uniform)
         const int R = P->c.threads_per_row == 2 || P->c.threads_per_row == 4 ? P->c.threads_per_row : 1;
-        const unsigned ugrid = grid_of(32 * ((d.n_slices + R - 1) / R), INT32_MAX);
+        const unsigned ugrid = grid_of(32 * ((d.n_slices + R - 1) / R), R == 4 ? (int64_t)P->sm_count * 4 : INT32_MAX);
 #define SPMV_SL_U(U, RR, B, CT)                                                                    \
     k_sliced_uniform<U, RR, B, CT><<<ugrid, kSB, 0, s>>>(A.n_rows, d.n_slices, d.uniform_len,      \
                                                          static_cast<const CT*>(d.scol), d.val, x, y)
