@@ -522,7 +522,7 @@ def run_ours(args):
     for P in twin:
         P.free()
     h2d_b, d2h_b = sum(8 * A.n_cols for A in mats), sum(8 * A.n_rows for A in mats)
-    link = _link_gbs(torch, max(h2d_b, d2h_b) // 4)
+    link = _link_gbs(torch, max(h2d_b, d2h_b))
     e2e = {"value": step_bytes * args.steps / e2e_s[False] / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
            "pipelined_steps": True, "prepared_objects_per_matrix": 2,
