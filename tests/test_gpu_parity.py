@@ -173,6 +173,24 @@ def test_empty_matrix_all_variants():
         P.free()
 
 
+def test_rows_without_columns_all_variants():
+    """n_cols = 0: every row is empty, so y = 0 for every variant and
+    launch shape (the SLICED layout is uniform with rows of length 0)."""
+    A = synth.HostCSR(100, 0, torch.zeros(101, dtype=torch.int32), torch.zeros(0, dtype=torch.int32),
+                      torch.zeros(0, dtype=torch.float64), "no_columns")
+    dA = sp.DeviceCSR.from_host(A)
+    x = torch.zeros(1, dtype=torch.float64, device="cuda")  # a valid pointer, never read
+    for v, params in CHOICES:
+        P = sp.spmv_prepare(dA, sp.make_choice(v, **params))
+        y = torch.full((100,), float("nan"), dtype=torch.float64, device="cuda")
+        sp.spmv(P, x, y)
+        torch.cuda.synchronize()
+        assert torch.equal(y, torch.zeros_like(y)), (v, params)
+        if v == "sliced" and not params:
+            assert P.info().uniform_len == 0
+        P.free()
+
+
 # ----------------------------------------------------------------- features
 def _features_match(A, line_bytes=128):
     dA = sp.DeviceCSR.from_host(A)
