@@ -70,26 +70,31 @@ __device__ __forceinline__ u64 warp_max_u64(u64 v) {
 constexpr int kFields = 16;  // FeatAcc words reduced per block (err excluded)
 
 // floor(a 2^32 / b) for 0 <= a <= b < 2^31, exactly, without a 64-bit
-// integer division: an FP32 estimate of the quotient, then the integer
-// remainder a 2^32 - q b corrected into [0, b).  The estimate is within about
-// 800 of the quotient and the remainder's own FP32 correction within one, so
-// the final steps run at most once (capped at four).  Arguments outside that
-// range come only from rows the pass flags as invalid (columns not strictly
-// increasing or out of range), whose results are discarded: they give 0.
+// integer division and without 64-bit conversions (which run on the FP64
+// pipe): an FP32 estimate of the quotient (a / b < 1, so it fits 32 bits),
+// then the integer remainder a 2^32 - q b, converted to FP32 from two 32-bit
+// halves, gives a correction, and the remainder is brought into [0, b).  The
+// first estimate is within about 2^9 of the quotient, so |remainder| < 2^41
+// and the second within one; the final steps run at most once (capped at
+// four).  Arguments outside that range come only from rows the pass flags as
+// invalid (columns not strictly increasing or out of range), whose results
+// are discarded: they give 0.
 __device__ __forceinline__ u64 fixq32(u64 a, u64 b)
 {
     if (a == 0 || b == 0 || b >= (1ull << 31) || a > b) return 0;
     if (a == b) return 1ull << 32;
-    const float rb = __frcp_rn((float)b);
-    const u64 num = a << 32;
-    u64 q = (u64)__fmul_rn(__fmul_rn((float)a, rb), 4294967296.0f);
-    int64_t rem = (int64_t)(num - q * b);
-    const int64_t c = (int64_t)floorf(__fmul_rn((float)rem, rb));
-    q += (u64)c;
-    rem -= c * (int64_t)b;
-    for (int i = 0; i < 4 && rem < 0; ++i) { --q; rem += (int64_t)b; }
-    for (int i = 0; i < 4 && rem >= (int64_t)b; ++i) { ++q; rem -= (int64_t)b; }
-    return q;
+    const unsigned a32 = (unsigned)a, b32 = (unsigned)b;
+    const float rb = __frcp_rn(__uint2float_rn(b32));
+    int64_t q = (int64_t)__float2uint_rz(__fmul_rn(__fmul_rn(__uint2float_rn(a32), rb), 4294967296.0f));
+    int64_t rem = (int64_t)(((u64)a32 << 32) - (u64)q * b32);
+    const float rf = __fmaf_rn(__int2float_rn((int)(rem >> 20)), 1048576.0f,
+                               __uint2float_rn((unsigned)(rem & 0xFFFFF)));
+    const int c = __float2int_rd(__fmul_rn(rf, rb));
+    q += c;
+    rem -= (int64_t)c * b32;
+    for (int i = 0; i < 4 && rem < 0; ++i) { --q; rem += b32; }
+    for (int i = 0; i < 4 && rem >= (int64_t)b32; ++i) { ++q; rem -= b32; }
+    return (u64)q;
 }
 
 // Per-thread partial aggregates of the rows a thread finalizes.
@@ -189,36 +194,51 @@ __device__ void flush_block(RowAgg& r, u64 err, u64 (*s_red)[kFields], u64* s_er
     }
 }
 
+// The per-element tests in 32-bit integers.  Columns of a valid matrix lie
+// in [0, n_cols) with n_cols < 2^31, so the unsigned compare (unsigned)c >=
+// n_cols is c < 0 || c >= n_cols, and the difference of two columns, taken
+// modulo 2^32, is exact; a row with an invalid column or order sets an error
+// bit and the call returns an error, so its counts are never used.  A gap d
+// moves more than a line of line_bytes when 8 d > line_bytes, that is when
+// d > floor(line_bytes / 8) (d an integer).
+struct ColTest {
+    unsigned n_cols;
+    int lb8;  // floor(line_bytes / 8)
+};
+
 // Elements [j0, e) of a row starting at b, every `step`-th one, U at a time:
 // ng counts columns that do not follow their predecessor by one, ms those
 // more than a line away from it; bad collects CSR violations.
 template <int U>
 __device__ __forceinline__ void count_elements(int64_t b, int64_t j0, int64_t e, int step,
-                                               const int* __restrict__ ci, int64_t n_cols,
-                                               int64_t line_bytes, u64& ng, u64& ms, u64& bad)
+                                               const int* __restrict__ ci, ColTest t, u64& ng, u64& ms,
+                                               u64& bad)
 {
+    unsigned g = 0, m = 0;  // at most kChunk / 32 elements a lane per call
     for (; j0 < e; j0 += (int64_t)U * step) {
-        int64_t c[U], cp[U];
+        int c[U], cp[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u * step;
-            c[u] = j < e ? (int64_t)ci[j] : 0;
-            cp[u] = (j < e && j > b) ? (int64_t)ci[j - 1] : 0;
+            c[u] = j < e ? ci[j] : 0;
+            cp[u] = (j < e && j > b) ? ci[j - 1] : 0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u * step;
             if (j < e) {
-                if (c[u] < 0 || c[u] >= n_cols) bad |= 8;
+                if ((unsigned)c[u] >= t.n_cols) bad |= 8;
                 if (j > b) {
-                    const int64_t d = c[u] - cp[u];
+                    const int d = (int)((unsigned)c[u] - (unsigned)cp[u]);
                     if (d <= 0) bad |= 16;
-                    ng += (d != 1);
-                    ms += (8 * d > line_bytes);
+                    g += (d != 1);
+                    m += (d > t.lb8);
                 }
             }
         }
     }
+    ng += g;
+    ms += m;
 }
 
 // Rows of at most kShortCap nonzeros: a lane per row, warps taking tiles of
@@ -226,12 +246,14 @@ __device__ __forceinline__ void count_elements(int64_t b, int64_t j0, int64_t e,
 // flight, keeping the previous column in a register, so every element is
 // loaded once and the per-row arithmetic (two 64-bit divisions, 128-bit
 // squares) runs on all 32 lanes.  Longer rows are listed for the chunked
-// kernels below.
+// kernels below.  Held to 64 registers (4 blocks of 256 per SM; a few bytes
+// of the per-row aggregates spill): 0.126 ms on the 27-point stencil
+// against 0.148 ms at 80 registers and 3 blocks.
 constexpr int64_t kShortCap = 64;
 constexpr int64_t kChunk = 4096;
 
 template <bool FEATURES>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restrict__ rp,
                const int* __restrict__ ci, int64_t line_bytes, int* __restrict__ long_rows,
                int64_t max_long, FeatAcc* __restrict__ acc)
@@ -249,6 +271,7 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
     }
     const int64_t n_tiles = (n_rows + 31) / 32;
     const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const ColTest t{(unsigned)n_cols, (int)(line_bytes >> 3)};
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; tile < n_tiles;
          tile += n_warps) {
         const int64_t row = tile * 32 + lane;
@@ -261,24 +284,25 @@ k_feature_pass(int64_t n_rows, int64_t n_cols, int64_t nnz, const int* __restric
             else if (e - b > kShortCap) is_long = true;
             else { nz = e - b; row_ok = true; }
         }
-        u64 ng = 0, ms = 0;
-        int64_t first = 0, prev = 0;
-        if (nz > 0) {
+        unsigned ng = 0, ms = 0;
+        int first = 0, prev = 0;
+        const int nzi = (int)nz;  // at most kShortCap
+        if (nzi > 0) {
             first = prev = ci[b];
-            if (first < 0 || first >= n_cols) err |= 8;
+            if ((unsigned)first >= t.n_cols) err |= 8;
         }
-        for (int64_t k = 1; k < nz; k += U) {
-            int64_t c[U];
+        for (int k = 1; k < nzi; k += U) {
+            int c[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) c[u] = k + u < nz ? (int64_t)ci[b + k + u] : 0;
+            for (int u = 0; u < U; ++u) c[u] = k + u < nzi ? ci[b + k + u] : 0;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (k + u < nz) {
-                    if (c[u] < 0 || c[u] >= n_cols) err |= 8;
-                    const int64_t d = c[u] - prev;
+                if (k + u < nzi) {
+                    if ((unsigned)c[u] >= t.n_cols) err |= 8;
+                    const int d = (int)((unsigned)c[u] - (unsigned)prev);
                     if (d <= 0) err |= 16;
                     ng += (d != 1);
-                    ms += (8 * d > line_bytes);
+                    ms += (d > t.lb8);
                     prev = c[u];
                 }
             }
@@ -380,6 +404,7 @@ k_feature_chunks(const int* __restrict__ long_rows, int64_t max_long, const int*
     const int total = n_mid + (n_huge > 0 ? chunk_off[n_huge] : 0);
     RowAgg r;
     u64 bad = 0;
+    const ColTest t{(unsigned)n_cols, (int)(line_bytes >> 3)};
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(w.next, 1u);
@@ -390,7 +415,7 @@ k_feature_chunks(const int* __restrict__ long_rows, int64_t max_long, const int*
             const int row = long_rows[it];
             const int64_t b = rp[row], e = rp[row + 1];
             u64 ng = 0, ms = 0;
-            count_elements<4>(b, b + lane, e, 32, ci, n_cols, line_bytes, ng, ms, bad);
+            count_elements<4>(b, b + lane, e, 32, ci, t, ng, ms, bad);
             ng = warp_sum_u64(ng);
             ms = warp_sum_u64(ms);
             if (FEATURES && lane == 0) r.add((u64)(e - b), (int64_t)ci[b], (int64_t)ci[e - 1], ng, ms);
@@ -407,7 +432,7 @@ k_feature_chunks(const int* __restrict__ long_rows, int64_t max_long, const int*
         const int64_t c0 = b + (int64_t)(ic - chunk_off[lo]) * kChunk;
         const int64_t c1 = min(e, c0 + kChunk);
         u64 ng = 0, ms = 0;
-        count_elements<4>(b, c0 + lane, c1, 32, ci, n_cols, line_bytes, ng, ms, bad);
+        count_elements<4>(b, c0 + lane, c1, 32, ci, t, ng, ms, bad);
         ng = warp_sum_u64(ng);
         ms = warp_sum_u64(ms);
         if (lane == 0) {
