@@ -247,14 +247,18 @@ __global__ void k_sl_long_list(int64_t n_rows, const int* __restrict__ rp, int c
 // form on all three regular test matrices (random columns 0.249 against
 // 0.258 ms, stencil 0.115 against 0.136 ms, 2-nonzero rows 0.080 against
 // 0.093 ms).
+// Blocks of two warps (32 per SM), as for k_sliced_long: a block frees its
+// slot when its two slices are done (27-point stencil 0.113 against 0.115
+// ms with eight-warp blocks, 7-point Laplacian 0.035 against 0.037)
+constexpr int kOB = 64;
 template <int U, typename CT>
-__global__ void __launch_bounds__(kSB, 8)
+__global__ void __launch_bounds__(kOB, 32)
 k_sliced(int64_t n_slices, const int* __restrict__ rowlen, const int* __restrict__ slice_len,
          const int64_t* __restrict__ slice_ptr, const int* __restrict__ perm,
          const CT* __restrict__ col, const double* __restrict__ val,
          const double* __restrict__ x, double* __restrict__ y)
 {
-    const int64_t s = ((int64_t)blockIdx.x * kSB + threadIdx.x) >> 5;
+    const int64_t s = ((int64_t)blockIdx.x * kOB + threadIdx.x) >> 5;
     if (s >= n_slices) return;  // whole warps only
     slice_rows<U, CT>(s, threadIdx.x & 31, rowlen, slice_len, slice_ptr, perm, col, val, x, y);
 }
@@ -926,7 +930,8 @@ cudaError_t launch_sliced(const spmv_prepared* P, const double* x, double* y, cu
             case 2: SPMV_SL_M(2, 2, 6, CT); break;                                                 \
             case 4: SPMV_SL_M(1, 4, 4, CT); break;                                                 \
             default:                                                                               \
-                k_sliced<4, CT><<<grid, kSB, 0, s>>>(d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, \
+                k_sliced<4, CT><<<(unsigned)((d.n_slices + kOB / 32 - 1) / (kOB / 32)), kOB, 0, s>>>( \
+                    d.n_slices, d.rowlen, d.slice_len, d.slice_ptr, \
                                                      perm, static_cast<const CT*>(d.scol), d.val, x, y); \
         }
         if (d.cbytes == 1) { SPMV_SL_CT(int8_t) }
